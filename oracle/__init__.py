@@ -1,0 +1,185 @@
+"""Python access to the FP64 CPU oracle (``sph_oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the CPU-baseline arm
+of ``bench.py`` are the only users.  The product path (the CUDA library and its
+binding) never imports this module, and this module imports nothing from it.
+
+The shared library is compiled on first use with g++ (-O2 -ffp-contract=off) into
+``oracle/_build/``; ``build()`` does the same explicitly.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.cpp")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libsphoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CXXFLAGS = ["-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-pthread"]
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", *CXXFLAGS, "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            P = ctypes.c_void_p
+            L.orc_hilbert_cells.argtypes = [i64, P, P, P, i32, P]
+            L.orc_hilbert_keys.argtypes = [i64, P, P, P, P]
+            L.orc_stable_order.argtypes = [i64, P, P]
+            L.orc_kernel.argtypes = [i64, P, P, P, P, P]
+            L.orc_kernel.restype = None
+            L.orc_pair_r2.argtypes = [i64, P, P, P, i64, P, P, P]
+            L.orc_pair_r2.restype = None
+            L.orc_ngb_sets.argtypes = [i64, P, P, P, P, i32, i64, P, i32, P, P]
+            L.orc_density.argtypes = [i64, P, P, P, P, P, i64, P, i32, P, P, P, P, P]
+            L.orc_density_iterate.argtypes = [i64, P, P, P, P, P, i64, P, dbl, dbl, i32, i32,
+                                              P, P, P, P, P, P]
+            L.orc_density_iterate.restype = i64
+            L.orc_hydro.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, dbl, dbl, dbl,
+                                    dbl, i32, P, P, P, P, P]
+            L.orc_threads.argtypes = []
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _xyz(pos):
+    pos = np.asarray(pos, dtype=np.float64)
+    return _f64(pos[:, 0]), _f64(pos[:, 1]), _f64(pos[:, 2])
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
+
+
+def hilbert_cells(cells: np.ndarray, bits: int) -> np.ndarray:
+    c = np.ascontiguousarray(cells, dtype=np.uint32)
+    cx, cy, cz = (np.ascontiguousarray(c[:, a]) for a in range(3))
+    out = np.empty(len(c), dtype=np.uint64)
+    rc = lib().orc_hilbert_cells(len(c), _p(cx), _p(cy), _p(cz), bits, _p(out))
+    if rc != 0:
+        raise ValueError("bits out of range")
+    return out
+
+
+def hilbert_keys(pos: np.ndarray) -> np.ndarray:
+    x, y, z = _xyz(pos)
+    out = np.empty(len(x), dtype=np.uint64)
+    if lib().orc_hilbert_keys(len(x), _p(x), _p(y), _p(z), _p(out)) != 0:
+        raise ValueError("positions must lie in [0, 1)")
+    return out
+
+
+def stable_order(keys: np.ndarray) -> np.ndarray:
+    k = np.ascontiguousarray(keys, dtype=np.uint64)
+    perm = np.empty(len(k), dtype=np.int32)
+    lib().orc_stable_order(len(k), _p(k), _p(perm))
+    return perm
+
+
+def kernel(r, h):
+    r = _f64(np.atleast_1d(r))
+    h = _f64(np.broadcast_to(h, r.shape))
+    w, dwdr, dwdh = (np.empty_like(r) for _ in range(3))
+    lib().orc_kernel(len(r), _p(r), _p(h), _p(w), _p(dwdr), _p(dwdh))
+    return w, dwdr, dwdh
+
+
+def pair_r2(pos, pi, pj):
+    x, y, z = _xyz(pos)
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    pj = np.ascontiguousarray(pj, dtype=np.int32)
+    out = np.empty(len(pi))
+    lib().orc_pair_r2(len(x), _p(x), _p(y), _p(z), len(pi), _p(pi), _p(pj), _p(out))
+    return out
+
+
+DENSITY, HYDRO = 0, 1
+
+
+def ngb_sets(pos, h, targets=None, kind=DENSITY, use_tree=True):
+    """CSR (offsets, idx) of neighbour sets; idx ascending particle indices per target."""
+    x, y, z = _xyz(pos)
+    n = len(x)
+    h = _f64(h)
+    t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    off = np.zeros(len(t) + 1, dtype=np.int64)
+    L = lib()
+    L.orc_ngb_sets(n, _p(x), _p(y), _p(z), _p(h), kind, len(t), _p(t), int(use_tree), _p(off), None)
+    idx = np.empty(int(off[-1]), dtype=np.int32)
+    L.orc_ngb_sets(n, _p(x), _p(y), _p(z), _p(h), kind, len(t), _p(t), int(use_tree), _p(off), _p(idx))
+    return off, idx
+
+
+def density(pos, m, h, targets=None, use_tree=True):
+    x, y, z = _xyz(pos)
+    n = len(x)
+    m, h = _f64(m), _f64(h)
+    t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    nt = len(t)
+    rho, drhodh, f, neff = (np.empty(nt) for _ in range(4))
+    nngb = np.empty(nt, dtype=np.int32)
+    lib().orc_density(n, _p(x), _p(y), _p(z), _p(m), _p(h), nt, _p(t), int(use_tree), _p(rho),
+                      _p(drhodh), _p(f), _p(neff), _p(nngb))
+    return {"rho": rho, "drhodh": drhodh, "f": f, "neff": neff, "nngb": nngb}
+
+
+def density_iterate(pos, m, h_init, targets=None, nngb=64.0, dn=2.0, max_iter=100, use_tree=True):
+    """Iterates h of the targets; returns (h (all particles), dict of per-target outputs)."""
+    x, y, z = _xyz(pos)
+    n = len(x)
+    m = _f64(m)
+    h = _f64(np.array(h_init, dtype=np.float64, copy=True))
+    t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    nt = len(t)
+    rho, drhodh, f, neff = (np.empty(nt) for _ in range(4))
+    nn = np.empty(nt, dtype=np.int32)
+    iters = np.empty(nt, dtype=np.int32)
+    failed = lib().orc_density_iterate(n, _p(x), _p(y), _p(z), _p(m), _p(h), nt, _p(t), nngb, dn,
+                                       max_iter, int(use_tree), _p(rho), _p(drhodh), _p(f),
+                                       _p(neff), _p(nn), _p(iters))
+    return h, {"rho": rho, "drhodh": drhodh, "f": f, "neff": neff, "nngb": nn, "iters": iters,
+               "failed": int(failed)}
+
+
+def hydro(pos, vel, m, h, rho, f, u, targets=None, gamma=5.0 / 3.0, alpha=1.0, beta=2.0,
+          eps=0.01, use_tree=True):
+    x, y, z = _xyz(pos)
+    vx, vy, vz = _xyz(vel)
+    n = len(x)
+    m, h, rho, f, u = (_f64(a) for a in (m, h, rho, f, u))
+    t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    nt = len(t)
+    ax, ay, az, dudt = (np.empty(nt) for _ in range(4))
+    nn = np.empty(nt, dtype=np.int32)
+    lib().orc_hydro(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), _p(h), _p(rho), _p(f),
+                    _p(u), nt, _p(t), gamma, alpha, beta, eps, int(use_tree), _p(ax), _p(ay),
+                    _p(az), _p(dudt), _p(nn))
+    return {"acc": np.stack([ax, ay, az], axis=1), "dudt": dudt, "nngb": nn}
