@@ -1,0 +1,188 @@
+/*
+ * sphgrp.h -- C ABI of the GB300 SPH neighbour-search library.
+ *
+ * The library computes the hot path of "Exploiting the Space Filling Curve Ordering of
+ * Particles in the Neighbour Search of Gadget3" (Ragagnin et al., arXiv:1810.09898):
+ * Peano-Hilbert ordering of the particles, an octree over that order, the neighbour
+ * search in its two forms -- one tree walk per active particle (Sec. 2.1, "standard
+ * method", Fig. 1 left) and Neighbour Recycling (Sec. 3 and 3.1, Fig. 1 right: active
+ * particles consecutive along the curve form a group, the group makes one walk for a
+ * common superset of candidates, and each member filters the superset down to its own
+ * neighbours) -- and the SPH density (with the smoothing-length iteration to a fixed
+ * effective neighbour number, Sec. 3.2) and hydro-force loops that consume it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns an int status: SPHGRP_OK (0) or a negative SPHGRP_E* code.
+ *    sphgrp_last_error() returns a text describing the most recent failure of the
+ *    calling thread (never NULL).
+ *  - Positions are in units of the box side; the box is the periodic unit cube
+ *    [0,1)^3 and every coordinate must lie in [0,1).  Distances use the minimum image.
+ *    Smoothing lengths must satisfy 0 < h < 0.5 so that the minimum image is unique.
+ *  - Arrays named "device" are device pointers in the caller's memory; the caller
+ *    owns them, keeps them alive until the stream has passed the call, and the
+ *    library never frees them.  Particle arrays are indexed by the caller's particle
+ *    index ("original order"); the library keeps its own copies in key order.
+ *  - pos and vel are row-major n x 3 arrays (x0 y0 z0 x1 ...).
+ *  - Work is issued on the given stream.  Calls that report a count or a device-side
+ *    error (every call that returns a status derived from device work) synchronise
+ *    that stream before returning.
+ *  - The context owns its device workspace (key-ordered particle copies, the octree,
+ *    group and iteration state).  A context is used by one host thread at a time.
+ */
+#ifndef SPHGRP_H
+#define SPHGRP_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SPHGRP_OK = 0,
+    SPHGRP_EINVAL = -1,    /* bad argument: NaN or out-of-box position, h outside (0, 0.5), n = 0 ... */
+    SPHGRP_ENOMEM = -2,    /* device allocation failed */
+    SPHGRP_ENOCONV = -3,   /* smoothing-length iteration did not converge within max_iter */
+    SPHGRP_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    SPHGRP_EOVERFLOW = -5, /* an internal capacity was exceeded (results invalid) */
+    SPHGRP_ECUDA = -6,     /* a CUDA runtime call failed */
+    SPHGRP_ESTATE = -7     /* calls made out of order (e.g. a search before a tree) */
+};
+
+/* Neighbour-search forms. */
+enum {
+    SPHGRP_INDIVIDUAL = 0, /* one walk per active particle with radius h_i (Sec. 2.1) */
+    SPHGRP_GROUPED = 1     /* Neighbour Recycling: one walk per group of group_size
+                              consecutive active particles in key order (Sec. 3.1) */
+};
+
+/* Neighbour definitions (Sec. 2.1, last paragraph). */
+enum {
+    SPHGRP_DENSITY = 0, /* j is a neighbour of i iff |r_ij| < h_i (i itself included) */
+    SPHGRP_HYDRO = 1    /* j != i is a neighbour of i iff |r_ij| < max(h_i, h_j) */
+};
+
+typedef struct sphgrp_params {
+    double nngb;      /* target effective neighbour number 4 pi rho h^3 / (3 m), e.g. 64 */
+    double nngb_tol;  /* iteration stops when |N_eff - nngb| <= nngb_tol, e.g. 2 */
+    int max_iter;     /* smoothing-length passes before SPHGRP_ENOCONV, e.g. 100 */
+    int leaf_size;    /* octree leaf bucket size B (nodes with more particles split), e.g. 16 */
+    double gamma;     /* adiabatic index, P = (gamma - 1) rho u, e.g. 5/3 */
+    double alpha;     /* Monaghan viscosity alpha, e.g. 1 */
+    double beta;      /* Monaghan viscosity beta, e.g. 2 */
+    double eps;       /* viscosity softening (mu denominator r^2 + eps hbar^2), e.g. 0.01 */
+} sphgrp_params;
+
+/* Fills p with the defaults quoted above. */
+void sphgrp_default_params(sphgrp_params* p);
+
+typedef struct sphgrp_stats {
+    int64_t walks;          /* tree walks started (groups, or particles in the individual form) */
+    int64_t nodes_tested;   /* node-overlap tests */
+    int64_t candidates;     /* candidate particles taken from opened leaves (summed over walks) */
+    int64_t pair_tests;     /* member x candidate distance tests */
+    int64_t pairs;          /* neighbour pairs found */
+    int64_t fp64_retests;   /* pairs re-decided from FP64 positions (within the FP32 error band) */
+    int64_t iterations;     /* smoothing-length passes made by the last density call */
+    int64_t max_stack;      /* deepest walk stack seen */
+} sphgrp_stats;
+
+typedef struct sphgrp_ctx sphgrp_ctx;
+
+/* Creates a context for up to n_max particles.  p may be NULL (defaults).  Device
+ * memory for n_max particles is allocated here; the octree grows on demand. */
+int sphgrp_ctx_create(sphgrp_ctx** ctx, const sphgrp_params* p, int64_t n_max);
+int sphgrp_ctx_destroy(sphgrp_ctx* ctx);
+const char* sphgrp_last_error(void);
+
+/* a1 + a2 (Sec. 2.2: particles ordered along the Hilbert curve).
+ * keys: 63-bit Peano-Hilbert key of every particle -- coordinates mapped to a 2^21
+ * grid per axis, i = floor(x * 2^21), and the cell's Hilbert index by Skilling's
+ * construction (axis order x, y, z, most significant level first) -- sorted
+ * ascending by a stable device radix sort.
+ * pos:      device, n x 3 FP64, in [0,1).
+ * keys_out: device, n uint64, the sorted keys (may be NULL).
+ * perm_out: device, n int32, perm_out[r] = original index of the particle of rank r
+ *           (may be NULL).
+ * The context keeps the order for the following calls.  Errors: EINVAL for n < 1,
+ * n > n_max or a coordinate outside [0,1) (including NaN). */
+int sphgrp_sfc_keys_sort(sphgrp_ctx* ctx, int64_t n, const double* pos, uint64_t* keys_out,
+                         int32_t* perm_out, cudaStream_t stream);
+
+/* a3 (Sec. 2.2: octree over the curve-ordered particles).  Gathers pos and m into key
+ * order and builds the linear octree: a node with more than leaf_size particles is
+ * split into its non-empty octants (the next 3 key bits), down to the 2^21 grid.
+ * Each node keeps its tight bounding box, its particle range and the largest h of
+ * its particles (set by the density and hydro calls).
+ * pos: device n x 3 FP64 (the same positions as the last sfc_keys_sort);
+ * m:   device n FP32 masses.  Errors: ESTATE without a preceding sort of n particles. */
+int sphgrp_tree_build(sphgrp_ctx* ctx, int64_t n, const double* pos, const float* m,
+                      cudaStream_t stream);
+
+/* a4 + a5 (Sec. 2.1 and 3.1): neighbour sets of the active particles, exported as
+ * CSR for inspection.  The hot path never materialises pair lists; this call exists
+ * so that sets can be compared.
+ * active:  device, n_act distinct original indices (any order).
+ * h:       device, n FP64 smoothing lengths (all particles; hydro reads h_j too).
+ * kind:    SPHGRP_DENSITY or SPHGRP_HYDRO.   mode: SPHGRP_INDIVIDUAL or SPHGRP_GROUPED.
+ * group_size: members per group for the grouped form (1..256).
+ * offsets: device, n_act + 1 int64; offsets[k]..offsets[k+1] index the neighbours of
+ *          active[k] in idx (original indices, in no particular order).
+ * idx:     device, cap int32, or NULL to count only.
+ * n_pairs: host, receives the total number of pairs.
+ * Errors: EOVERFLOW if the total exceeds cap (offsets still valid). */
+int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                      int kind, int mode, int group_size, int64_t cap, int64_t* offsets,
+                      int32_t* idx, int64_t* n_pairs, cudaStream_t stream);
+
+/* The candidate superset of every group of the grouped form (Sec. 3.1), for
+ * inspection.  Groups are group_size consecutive active particles in key order.
+ * group_offsets: device, n_groups + 1 int64 over cand (n_groups = ceil(n_act/group_size));
+ * members:       device, n_act int32: the active original indices in group order;
+ * cand:          device, cap int32 original indices, or NULL to count only;
+ * n_cand:        host, total candidates.  kind selects the density or hydro radius. */
+int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
+                           const double* h, int kind, int group_size, int64_t cap,
+                           int64_t* group_offsets, int32_t* members, int32_t* cand,
+                           int64_t* n_cand, cudaStream_t stream);
+
+/* a6 + a7: SPH density of the active particles,
+ *   rho_i = sum_{j in N_i} m_j W(r_ij, h_i),   dRho_i/dh_i,
+ *   f_i = 1 / (1 + h_i / (3 rho_i) dRho_i/dh_i),  n_i = |N_i|,
+ * with W the M4 cubic spline of support h.  With iterate != 0, h_i is iterated per
+ * particle until |4 pi rho_i h_i^3 / (3 m_i) - nngb| <= nngb_tol (Sec. 3.2 relation
+ * N_ngb = 4 pi rho h^3 / 3): Newton steps on that function inside a bracket, with a
+ * volume bisection when a step leaves the bracket; each pass re-walks only the
+ * unconverged particles, regrouped.
+ * h:      device, n FP64; read for every particle, overwritten for active ones.
+ * rho, drhodh, fgrad: device n FP32; nngb, iters: device n int32 (iters may be NULL).
+ * Only entries of active particles are written.  Errors: ENOCONV if a particle did
+ * not converge within max_iter passes (its last values are still written). */
+int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h,
+                   int iterate, int mode, int group_size, float* rho, float* drhodh,
+                   float* fgrad, int32_t* nngb, int32_t* iters, cudaStream_t stream);
+
+/* a8: SPH hydro accelerations and du/dt of the active particles (Sec. 2.1 hydro
+ * neighbour definition).  For j in the hydro set of i:
+ *   a_i  -= m_j [ A_i dW(h_i) + A_j dW(h_j) + Pi_ij (dW(h_i) + dW(h_j))/2 ] r_ij / r
+ *   du_i += m_j [ A_i dW(h_i) + Pi_ij (dW(h_i) + dW(h_j))/4 ] v_ij . r_ij / r
+ * A_k = f_k P_k / rho_k^2, P = (gamma - 1) rho u, dW = dW/dr, Pi_ij the Monaghan
+ * viscosity (alpha, beta, eps; zero for receding pairs).
+ * h: device n FP64; rho, fgrad, u: device n FP32; vel: device n x 3 FP32 -- all
+ * particles (neighbours may be inactive).  acc: device n x 3 FP32, dudt: device n FP32,
+ * nngb: device n int32 (may be NULL); only active entries are written. */
+int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
+                       const double* h, const float* rho, const float* fgrad,
+                       const float* vel, const float* u, int mode, int group_size,
+                       float* acc, float* dudt, int32_t* nngb, cudaStream_t stream);
+
+/* Counters of the most recent search, density or hydro call. */
+int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPHGRP_H */

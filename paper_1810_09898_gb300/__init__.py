@@ -1,0 +1,18 @@
+"""GB300 SPH neighbour search with Neighbour Recycling (arXiv:1810.09898).
+
+The compute path is the CUDA library ``_build/libsphgrp.so`` (C ABI in
+``include/sphgrp.h``); this package only marshals arguments to it.  Nothing here falls
+back to a CPU implementation: if the library is missing or no GPU is present the
+calls raise.
+"""
+
+from .binding import (  # noqa: F401
+    DENSITY,
+    GROUPED,
+    HYDRO,
+    INDIVIDUAL,
+    SphgrpError,
+    Context,
+    library_path,
+    load_library,
+)

@@ -1,0 +1,199 @@
+"""ctypes binding of the C ABI in include/sphgrp.h (argument marshalling only).
+
+Every function of the C ABI is exposed under its own name on the loaded library;
+``Context`` wraps a ``sphgrp_ctx*`` and passes torch CUDA tensors as device pointers
+on the current torch stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "_build", "libsphgrp.so")
+
+INDIVIDUAL, GROUPED = 0, 1
+DENSITY, HYDRO = 0, 1
+
+EXPORTED = [
+    "sphgrp_default_params",
+    "sphgrp_last_error",
+    "sphgrp_ctx_create",
+    "sphgrp_ctx_destroy",
+    "sphgrp_sfc_keys_sort",
+    "sphgrp_tree_build",
+    "sphgrp_ngb_search",
+    "sphgrp_group_supersets",
+    "sphgrp_density",
+    "sphgrp_hydro_force",
+    "sphgrp_get_stats",
+]
+
+_ERRORS = {
+    -1: "SPHGRP_EINVAL",
+    -2: "SPHGRP_ENOMEM",
+    -3: "SPHGRP_ENOCONV",
+    -4: "SPHGRP_ETIMEOUT",
+    -5: "SPHGRP_EOVERFLOW",
+    -6: "SPHGRP_ECUDA",
+    -7: "SPHGRP_ESTATE",
+}
+
+
+class SphgrpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nngb", ctypes.c_double),
+        ("nngb_tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("leaf_size", ctypes.c_int),
+        ("gamma", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("eps", ctypes.c_double),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "walks", "nodes_tested", "candidates", "pair_tests", "pairs", "fp64_retests",
+        "iterations", "max_stack")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library():
+    """Loads libsphgrp.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"CUDA library not built: {_LIB_PATH} (run __graft_entry__.build())")
+    L = ctypes.CDLL(_LIB_PATH)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.sphgrp_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.sphgrp_default_params.restype = None
+    L.sphgrp_last_error.restype = ctypes.c_char_p
+    L.sphgrp_ctx_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Params), I64]
+    L.sphgrp_ctx_destroy.argtypes = [P]
+    L.sphgrp_sfc_keys_sort.argtypes = [P, I64, P, P, P, P]
+    L.sphgrp_tree_build.argtypes = [P, I64, P, P, P]
+    L.sphgrp_ngb_search.argtypes = [P, I64, P, P, I32, I32, I32, I64, P, P,
+                                    ctypes.POINTER(I64), P]
+    L.sphgrp_group_supersets.argtypes = [P, I64, P, P, I32, I32, I64, P, P, P,
+                                         ctypes.POINTER(I64), P]
+    L.sphgrp_density.argtypes = [P, I64, P, P, I32, I32, I32, P, P, P, P, P, P]
+    L.sphgrp_hydro_force.argtypes = [P, I64, P, P, P, P, P, P, I32, I32, P, P, P, P]
+    L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    for name in EXPORTED:
+        if name not in ("sphgrp_default_params", "sphgrp_last_error"):
+            getattr(L, name).restype = I32
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise SphgrpError(rc, load_library().sphgrp_last_error().decode())
+
+
+def default_params(**over) -> Params:
+    p = Params()
+    load_library().sphgrp_default_params(ctypes.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One sphgrp_ctx: device workspace for up to n_max particles."""
+
+    def __init__(self, n_max: int, **params):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("sphgrp needs a CUDA device")
+        self._L = load_library()
+        self.params = default_params(**params)
+        self._h = ctypes.c_void_p()
+        _check(self._L.sphgrp_ctx_create(ctypes.byref(self._h), ctypes.byref(self.params), int(n_max)))
+        self.n_max = int(n_max)
+
+    def close(self):
+        if self._h:
+            self._L.sphgrp_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- a1 + a2
+    def sfc_keys_sort(self, pos, keys_out=None, perm_out=None):
+        _check(self._L.sphgrp_sfc_keys_sort(self._h, pos.shape[0], _ptr(pos), _ptr(keys_out),
+                                            _ptr(perm_out), _stream()))
+
+    # -- a3
+    def tree_build(self, pos, m):
+        _check(self._L.sphgrp_tree_build(self._h, pos.shape[0], _ptr(pos), _ptr(m), _stream()))
+
+    # -- a4 + a5 export
+    def ngb_search(self, active, h, kind, mode, group_size, offsets, idx=None, cap=0) -> int:
+        n_pairs = ctypes.c_int64()
+        _check(self._L.sphgrp_ngb_search(self._h, active.shape[0], _ptr(active), _ptr(h), kind, mode,
+                                         group_size, int(cap), _ptr(offsets), _ptr(idx),
+                                         ctypes.byref(n_pairs), _stream()))
+        return int(n_pairs.value)
+
+    def group_supersets(self, active, h, kind, group_size, group_offsets, members=None, cand=None,
+                        cap=0) -> int:
+        n = ctypes.c_int64()
+        _check(self._L.sphgrp_group_supersets(self._h, active.shape[0], _ptr(active), _ptr(h), kind,
+                                              group_size, int(cap), _ptr(group_offsets), _ptr(members),
+                                              _ptr(cand), ctypes.byref(n), _stream()))
+        return int(n.value)
+
+    # -- a6 + a7
+    def density(self, active, h, iterate, mode, group_size, rho, drhodh, fgrad, nngb, iters=None):
+        _check(self._L.sphgrp_density(self._h, active.shape[0], _ptr(active), _ptr(h), int(iterate), mode,
+                                      group_size, _ptr(rho), _ptr(drhodh), _ptr(fgrad), _ptr(nngb),
+                                      _ptr(iters), _stream()))
+
+    # -- a8
+    def hydro_force(self, active, h, rho, fgrad, vel, u, mode, group_size, acc, dudt, nngb=None):
+        _check(self._L.sphgrp_hydro_force(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
+                                          _ptr(fgrad), _ptr(vel), _ptr(u), mode, group_size, _ptr(acc),
+                                          _ptr(dudt), _ptr(nngb), _stream()))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._L.sphgrp_get_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()

@@ -1,0 +1,533 @@
+// C ABI of the library (declared in include/sphgrp.h): context, argument checks and
+// the orchestration of the kernels of sort.cu, tree.cu and ngb.cu.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "search_args.cuh"
+
+namespace sphgrp {
+
+
+static thread_local std::string g_last_error = "no error";
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int check_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return SPHGRP_OK;
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SPHGRP_ENOMEM : SPHGRP_ECUDA;
+}
+
+}  // namespace sphgrp
+
+
+using namespace sphgrp;
+
+namespace {
+
+template <typename T>
+int dalloc(T** p, int64_t count) {
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), (size_t)count * sizeof(T));
+    if (e != cudaSuccess) return check_cuda(e, "cudaMalloc");
+    return SPHGRP_OK;
+}
+
+__global__ void k_mark_active(int64_t n_act, const int32_t* __restrict__ active, int64_t n,
+                              const int32_t* __restrict__ rank_of, int32_t* __restrict__ flag,
+                              unsigned* err) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_act) return;
+    int i = active[k];
+    if (i < 0 || i >= n) {
+        atomicOr(err, 32u);
+        return;
+    }
+    flag[rank_of[i]] = 1;
+}
+
+__global__ void k_compact_ranks(int64_t n, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                                int32_t* __restrict__ out) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n && flag[r]) out[pos[r]] = (int32_t)r;
+}
+
+__global__ void k_compact_list(int nu, const int32_t* __restrict__ keep, const int32_t* __restrict__ pos,
+                               const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < nu && keep[u]) out[pos[u]] = in[u];
+}
+
+__global__ void k_gather_h(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
+                           double* __restrict__ h64, uint4* __restrict__ pfix, unsigned* err) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double v = h[perm[r]];
+    if (!(v > 0.0 && v < 0.5)) atomicOr(err, kErrH);
+    h64[r] = v;
+    pfix[r].w = __float_as_uint((float)v);
+}
+
+__global__ void k_hydro_prep(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
+                             const float* __restrict__ rho, const float* __restrict__ fgrad,
+                             const float* __restrict__ vel, const float* __restrict__ u, float gamma,
+                             double* __restrict__ h64, uint4* __restrict__ pfix, float4* __restrict__ hyd0,
+                             float4* __restrict__ hyd1, unsigned* err) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int i = perm[r];
+    double hv = h[i];
+    if (!(hv > 0.0 && hv < 0.5)) atomicOr(err, kErrH);
+    h64[r] = hv;
+    float hf = (float)hv;
+    pfix[r].w = __float_as_uint(hf);
+    float rh = rho[i];
+    float P = (gamma - 1.0f) * rh * u[i];
+    float cs = sqrtf(gamma * P / rh);
+    float A = fgrad[i] * P / (rh * rh);
+    hyd0[r] = make_float4(vel[3 * (int64_t)i], vel[3 * (int64_t)i + 1], vel[3 * (int64_t)i + 2], cs);
+    const double kPi = 3.14159265358979323846;
+    float s = (float)(8.0 / (kPi * hv * hv * hv * hv));
+    hyd1[r] = make_float4(A, rh, 1.0f / hf, s);
+}
+
+__global__ void k_counts_by_caller(int64_t n_act, const int32_t* __restrict__ active,
+                                   const int64_t* __restrict__ cnt, int64_t* __restrict__ out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n_act) out[k] = cnt[active[k]];
+}
+
+__global__ void k_offsets_by_orig(int64_t n_act, const int32_t* __restrict__ active,
+                                  const int64_t* __restrict__ off, int64_t* __restrict__ out) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k < n_act) out[active[k]] = off[k];
+}
+
+__global__ void k_members(int nu, const int32_t* __restrict__ U, const int32_t* __restrict__ perm,
+                          int32_t* __restrict__ out) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < nu) out[u] = perm[U[u]];
+}
+
+int finish(Ctx* c, cudaStream_t s, int rc) {
+    if (rc) return rc;
+    unsigned err = 0;
+    rc = check_cuda(cudaMemcpyAsync(&c->host_small[1], c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                    "error flag copy");
+    if (rc) return rc;
+    DevCounters dc;
+    rc = check_cuda(cudaMemcpyAsync(reinterpret_cast<DevCounters*>(c->host_small + 8), c->ctr,
+                                    sizeof(DevCounters), cudaMemcpyDeviceToHost, s),
+                    "counter copy");
+    if (rc) return rc;
+    rc = check_cuda(cudaStreamSynchronize(s), "stream");
+    if (rc) return rc;
+    err = (unsigned)c->host_small[1];
+    std::memcpy(&dc, c->host_small + 8, sizeof(dc));
+    c->last.nodes_tested = (int64_t)dc.nodes;
+    c->last.candidates = (int64_t)dc.cands;
+    c->last.pair_tests = (int64_t)dc.tests;
+    c->last.pairs = (int64_t)dc.pairs;
+    c->last.fp64_retests = (int64_t)dc.retests;
+    c->last.max_stack = (int64_t)dc.max_stack;
+    if (err & kErrRange) return set_error(SPHGRP_EINVAL, "a position is outside [0,1) or not finite");
+    if (err & kErrH) return set_error(SPHGRP_EINVAL, "a smoothing length is outside (0, 0.5)");
+    if (err & 32u) return set_error(SPHGRP_EINVAL, "an active index is outside [0, n)");
+    if (err & kErrStack) return set_error(SPHGRP_EOVERFLOW, "walk stack overflow");
+    if (err & kErrNodes) return set_error(SPHGRP_EOVERFLOW, "octree capacity exceeded");
+    if (err & kErrCap) return set_error(SPHGRP_EOVERFLOW, "export capacity exceeded");
+    return SPHGRP_OK;
+}
+
+void reset_flags(Ctx* c, cudaStream_t s) {
+    cudaMemsetAsync(c->err, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s);
+    std::memset(&c->last, 0, sizeof(c->last));
+}
+
+// active original indices -> key-ordered ranks in c->act; returns the count
+int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s, int* nu) {
+    const int64_t n = c->n;
+    cudaMemsetAsync(c->flag, 0, n * sizeof(int32_t), s);
+    k_mark_active<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, n, c->rank_of, c->flag, c->err);
+    int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
+    int rc = exclusive_scan_i32(c, c->flag, c->scan, n, total, s);
+    if (rc) return rc;
+    k_compact_ranks<<<blocks_for(n, 256), 256, 0, s>>>(n, c->flag, c->scan, c->act);
+    cudaMemcpyAsync(c->host_small, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    rc = check_cuda(cudaStreamSynchronize(s), "active list");
+    if (rc) return rc;
+    *nu = c->host_small[0];
+    return SPHGRP_OK;
+}
+
+SearchArgs base_args(Ctx* c) {
+    SearchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.ncen = c->tree.ncen;
+    a.next = c->tree.next;
+    a.nlink = c->tree.nlink;
+    a.pfix = c->pfix;
+    a.poff = c->poff;
+    a.xd = c->xd;
+    a.yd = c->yd;
+    a.zd = c->zd;
+    a.h64 = c->h64;
+    a.hyd0 = c->hyd0;
+    a.hyd1 = c->hyd1;
+    a.perm = c->perm;
+    a.alpha = (float)c->p.alpha;
+    a.beta = (float)c->p.beta;
+    a.eps = (float)c->p.eps;
+    a.ctr = c->ctr;
+    a.err = c->err;
+    a.work = c->work;
+    return a;
+}
+
+int check_common(Ctx* c, int64_t n_act, const int32_t* active, int mode, int group_size) {
+    if (!c) return set_error(SPHGRP_EINVAL, "null context");
+    if (!c->built) return set_error(SPHGRP_ESTATE, "no octree: call sphgrp_tree_build first");
+    if (n_act < 0 || n_act > c->n) return set_error(SPHGRP_EINVAL, "n_act outside [0, n]");
+    if (n_act > 0 && !active) return set_error(SPHGRP_EINVAL, "null active list");
+    if (mode != SPHGRP_INDIVIDUAL && mode != SPHGRP_GROUPED) return set_error(SPHGRP_EINVAL, "bad mode");
+    if (mode == SPHGRP_GROUPED && (group_size < 1 || group_size > 128))
+        return set_error(SPHGRP_EINVAL, "group_size must be in [1, 128]");
+    return SPHGRP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sphgrp_default_params(sphgrp_params* p) {
+    if (!p) return;
+    p->nngb = 64.0;
+    p->nngb_tol = 2.0;
+    p->max_iter = 100;
+    p->leaf_size = 16;
+    p->gamma = 5.0 / 3.0;
+    p->alpha = 1.0;
+    p->beta = 2.0;
+    p->eps = 0.01;
+}
+
+const char* sphgrp_last_error(void) { return g_last_error.c_str(); }
+
+int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
+    if (!out) return set_error(SPHGRP_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (n_max < 1 || n_max > (int64_t)1 << 30) return set_error(SPHGRP_EINVAL, "n_max outside [1, 2^30]");
+    Ctx* c = new Ctx();
+    if (p) c->p = *p;
+    else sphgrp_default_params(&c->p);
+    if (c->p.leaf_size < 1 || c->p.leaf_size > 1024 || !(c->p.nngb > 0) || !(c->p.nngb_tol >= 0) ||
+        c->p.max_iter < 1) {
+        delete c;
+        return set_error(SPHGRP_EINVAL, "bad parameters");
+    }
+    c->n_max = n_max;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n = n_max;
+    int rc = 0;
+    rc |= dalloc(&c->keys, n);
+    rc |= dalloc(&c->keys_alt, n);
+    rc |= dalloc(&c->perm, n);
+    rc |= dalloc(&c->perm_alt, n);
+    rc |= dalloc(&c->rank_of, n);
+    c->hist_cap = 256 * ((n + 2047) / 2048) + 256;
+    rc |= dalloc(&c->hist, c->hist_cap);
+    rc |= dalloc(&c->xd, n);
+    rc |= dalloc(&c->yd, n);
+    rc |= dalloc(&c->zd, n);
+    rc |= dalloc(&c->pfix, n);
+    rc |= dalloc(&c->poff, n);
+    rc |= dalloc(&c->h64, n);
+    rc |= dalloc(&c->hyd0, n);
+    rc |= dalloc(&c->hyd1, n);
+    rc |= dalloc(&c->act, n);
+    rc |= dalloc(&c->act2, n);
+    rc |= dalloc(&c->flag, n);
+    rc |= dalloc(&c->scan, n);
+    c->scan_aux_cap = 2 * (n / 1024 + 4096);
+    rc |= dalloc(&c->scan_aux, c->scan_aux_cap);
+    rc |= dalloc(&c->lo, n);
+    rc |= dalloc(&c->hi, n);
+    rc |= dalloc(&c->acc_rho, n);
+    rc |= dalloc(&c->acc_drho, n);
+    rc |= dalloc(&c->acc_n, n);
+    rc |= dalloc(&c->cnt64, n + 1);
+    rc |= dalloc(&c->ctr, 1);
+    rc |= dalloc(&c->err, 1);
+    rc |= dalloc(&c->work, 64);
+    if (rc == 0 && cudaMallocHost(&c->host_small, 64 * sizeof(int)) != cudaSuccess) rc = SPHGRP_ENOMEM;
+    if (rc) {
+        sphgrp_ctx_destroy(reinterpret_cast<sphgrp_ctx*>(c));
+        return set_error(SPHGRP_ENOMEM, "device allocation failed for n_max = " + std::to_string(n_max));
+    }
+    *out = reinterpret_cast<sphgrp_ctx*>(c);
+    return SPHGRP_OK;
+}
+
+int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c) return SPHGRP_OK;
+    void* ptrs[] = {c->keys, c->keys_alt, c->perm, c->perm_alt, c->rank_of, c->hist, c->xd, c->yd,
+                    c->zd, c->pfix, c->poff, c->h64, c->hyd0, c->hyd1, c->act, c->act2, c->flag,
+                    c->scan, c->scan_aux, c->lo, c->hi, c->acc_rho, c->acc_drho, c->acc_n,
+                    c->cnt64, c->ctr, c->err, c->work, c->tree.ncen, c->tree.next, c->tree.nlink,
+                    c->tree.nlevel};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->host_small) cudaFreeHost(c->host_small);
+    delete c;
+    return SPHGRP_OK;
+}
+
+int sphgrp_sfc_keys_sort(sphgrp_ctx* ctx, int64_t n, const double* pos, uint64_t* keys_out,
+                         int32_t* perm_out, cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c) return set_error(SPHGRP_EINVAL, "null context");
+    if (n < 1 || n > c->n_max) return set_error(SPHGRP_EINVAL, "n outside [1, n_max]");
+    if (!pos) return set_error(SPHGRP_EINVAL, "null positions");
+    c->sorted = false;
+    c->built = false;
+    c->n = n;
+    reset_flags(c, s);
+    int rc = sort_keys(c, n, pos, s);
+    if (!rc && keys_out) rc = check_cuda(cudaMemcpyAsync(keys_out, c->keys, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s), "keys copy");
+    if (!rc && perm_out) rc = check_cuda(cudaMemcpyAsync(perm_out, c->perm, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s), "perm copy");
+    rc = finish(c, s, rc);
+    if (!rc) c->sorted = true;
+    return rc;
+}
+
+int sphgrp_tree_build(sphgrp_ctx* ctx, int64_t n, const double* pos, const float* m, cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c) return set_error(SPHGRP_EINVAL, "null context");
+    if (!c->sorted || n != c->n) return set_error(SPHGRP_ESTATE, "tree_build needs a preceding sfc_keys_sort of the same n");
+    if (!pos || !m) return set_error(SPHGRP_EINVAL, "null positions or masses");
+    c->built = false;
+    reset_flags(c, s);
+    int rc = gather_particles(c, pos, m, s);
+    if (!rc) rc = build_tree(c, s);
+    rc = finish(c, s, rc);
+    if (!rc) c->built = true;
+    return rc;
+}
+
+int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                      int kind, int mode, int group_size, int64_t cap, int64_t* offsets,
+                      int32_t* idx, int64_t* n_pairs, cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    int rc = check_common(c, n_act, active, mode, group_size);
+    if (rc) return rc;
+    if (kind != SPHGRP_DENSITY && kind != SPHGRP_HYDRO) return set_error(SPHGRP_EINVAL, "bad kind");
+    if (!h || !offsets || !n_pairs) return set_error(SPHGRP_EINVAL, "null h, offsets or n_pairs");
+    reset_flags(c, s);
+    k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    if (kind == SPHGRP_HYDRO) {
+        cudaMemsetAsync(c->hyd0, 0, c->n * sizeof(float4), s);
+        cudaMemsetAsync(c->hyd1, 0, c->n * sizeof(float4), s);
+        if ((rc = refresh_hmax(c, s))) return rc;
+    }
+    int nu = 0;
+    if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
+    const bool grouped = mode == SPHGRP_GROUPED;
+    SearchArgs a = base_args(c);
+    a.U = c->act;
+    a.nu = nu;
+    a.g = grouped ? group_size : 1;
+    a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
+    a.x_cnt = c->cnt64;
+    a.x_off = c->cnt64;
+    a.x_cap = cap;
+    cudaMemsetAsync(c->cnt64, 0, c->n * sizeof(int64_t), s);
+    if ((rc = launch_search(a, kind, kCount, grouped, c->sm_count, s))) return rc;
+    k_counts_by_caller<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->cnt64, offsets);
+    if ((rc = exclusive_scan_i64(c, offsets, offsets, n_act, offsets + n_act, s))) return rc;
+    if (n_act == 0) cudaMemsetAsync(offsets, 0, sizeof(int64_t), s);
+    int64_t total = 0;
+    cudaMemcpyAsync(c->host_small + 32, offsets + n_act, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "pair count"))) return rc;
+    std::memcpy(&total, c->host_small + 32, sizeof(int64_t));
+    *n_pairs = total;
+    if (idx) {
+        k_offsets_by_orig<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, offsets, c->cnt64);
+        if ((rc = launch_search(a, kind, kFill, grouped, c->sm_count, s))) return rc;
+        if (total > cap) {
+            finish(c, s, 0);
+            return set_error(SPHGRP_EOVERFLOW, "more pairs than cap");
+        }
+    }
+    c->last.walks = a.ngroups;
+    return finish(c, s, 0);
+}
+
+int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                           int kind, int group_size, int64_t cap, int64_t* group_offsets,
+                           int32_t* members, int32_t* cand, int64_t* n_cand, cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    int rc = check_common(c, n_act, active, SPHGRP_GROUPED, group_size);
+    if (rc) return rc;
+    if (kind != SPHGRP_DENSITY && kind != SPHGRP_HYDRO) return set_error(SPHGRP_EINVAL, "bad kind");
+    if (!h || !group_offsets || !n_cand) return set_error(SPHGRP_EINVAL, "null h, group_offsets or n_cand");
+    reset_flags(c, s);
+    k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    if (kind == SPHGRP_HYDRO) {
+        cudaMemsetAsync(c->hyd0, 0, c->n * sizeof(float4), s);
+        cudaMemsetAsync(c->hyd1, 0, c->n * sizeof(float4), s);
+        if ((rc = refresh_hmax(c, s))) return rc;
+    }
+    int nu = 0;
+    if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
+    SearchArgs a = base_args(c);
+    a.U = c->act;
+    a.nu = nu;
+    a.g = group_size;
+    a.ngroups = (nu + group_size - 1) / group_size;
+    a.x_cnt = c->cnt64;
+    a.x_cap = cap;
+    if ((rc = launch_search(a, kind, kSupCount, true, c->sm_count, s))) return rc;
+    int ng = a.ngroups;
+    if ((rc = exclusive_scan_i64(c, c->cnt64, group_offsets, ng, group_offsets + ng, s))) return rc;
+    if (ng == 0) cudaMemsetAsync(group_offsets, 0, sizeof(int64_t), s);
+    if (members) k_members<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->act, c->perm, members);
+    cudaMemcpyAsync(c->host_small + 32, group_offsets + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "superset count"))) return rc;
+    int64_t total = 0;
+    std::memcpy(&total, c->host_small + 32, sizeof(int64_t));
+    *n_cand = total;
+    if (cand) {
+        a.x_off = group_offsets;
+        a.x_idx = cand;
+        if ((rc = launch_search(a, kind, kSupFill, true, c->sm_count, s))) return rc;
+        if (total > cap) {
+            finish(c, s, 0);
+            return set_error(SPHGRP_EOVERFLOW, "more candidates than cap");
+        }
+    }
+    c->last.walks = ng;
+    return finish(c, s, 0);
+}
+
+int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h, int iterate,
+                   int mode, int group_size, float* rho, float* drhodh, float* fgrad, int32_t* nngb,
+                   int32_t* iters, cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    int rc = check_common(c, n_act, active, mode, group_size);
+    if (rc) return rc;
+    if (!h || !rho || !drhodh || !fgrad || !nngb) return set_error(SPHGRP_EINVAL, "null output array");
+    reset_flags(c, s);
+    k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    int nu = 0;
+    if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
+    const bool grouped = mode == SPHGRP_GROUPED;
+    int32_t* U = c->act;
+    int32_t* U2 = c->act2;
+    int* nfail = c->work + 8;
+    cudaMemsetAsync(nfail, 0, sizeof(int), s);
+    int64_t walks = 0;
+    int it = 1;
+    const int max_iter = iterate ? c->p.max_iter : 1;
+    for (it = 1; it <= max_iter && nu > 0; ++it) {
+        SearchArgs a = base_args(c);
+        a.U = U;
+        a.nu = nu;
+        a.g = grouped ? group_size : 1;
+        a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
+        a.o_s0 = c->acc_rho;
+        a.o_s1 = c->acc_drho;
+        a.o_n = c->acc_n;
+        walks += a.ngroups;
+        if ((rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s))) return rc;
+        UpdateArgs ua;
+        std::memset(&ua, 0, sizeof(ua));
+        ua.U = U;
+        ua.nu = nu;
+        ua.it = it;
+        ua.max_iter = max_iter;
+        ua.nngb = c->p.nngb;
+        ua.tol = c->p.nngb_tol;
+        ua.s0 = c->acc_rho;
+        ua.s1 = c->acc_drho;
+        ua.n = c->acc_n;
+        ua.poff = c->poff;
+        ua.h64 = c->h64;
+        ua.pfix = c->pfix;
+        ua.lo = c->lo;
+        ua.hi = c->hi;
+        ua.keep = c->flag;
+        ua.perm = c->perm;
+        ua.h_out = h;
+        ua.rho = rho;
+        ua.drhodh = drhodh;
+        ua.fgrad = fgrad;
+        ua.nngb_out = nngb;
+        ua.iters = iters;
+        ua.iterate = iterate;
+        ua.nfail = nfail;
+        if ((rc = launch_hsml_update(ua, s))) return rc;
+        if (!iterate) break;
+        int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
+        if ((rc = exclusive_scan_i32(c, c->flag, c->scan, nu, total, s))) return rc;
+        k_compact_list<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->flag, c->scan, U, U2);
+        cudaMemcpyAsync(c->host_small, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "iteration count"))) return rc;
+        nu = c->host_small[0];
+        std::swap(U, U2);
+    }
+    cudaMemcpyAsync(c->host_small + 2, nfail, sizeof(int), cudaMemcpyDeviceToHost, s);
+    rc = finish(c, s, 0);
+    c->last.walks = walks;
+    c->last.iterations = std::min(it, max_iter);
+    if (rc) return rc;
+    if (c->host_small[2] > 0)
+        return set_error(SPHGRP_ENOCONV, std::to_string(c->host_small[2]) + " particles did not converge");
+    return SPHGRP_OK;
+}
+
+int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                       const float* rho, const float* fgrad, const float* vel, const float* u,
+                       int mode, int group_size, float* acc, float* dudt, int32_t* nngb,
+                       cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    int rc = check_common(c, n_act, active, mode, group_size);
+    if (rc) return rc;
+    if (!h || !rho || !fgrad || !vel || !u || !acc || !dudt) return set_error(SPHGRP_EINVAL, "null array");
+    reset_flags(c, s);
+    k_hydro_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, rho, fgrad, vel, u,
+                                                      (float)c->p.gamma, c->h64, c->pfix, c->hyd0,
+                                                      c->hyd1, c->err);
+    if ((rc = refresh_hmax(c, s))) return rc;
+    int nu = 0;
+    if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
+    const bool grouped = mode == SPHGRP_GROUPED;
+    SearchArgs a = base_args(c);
+    a.U = c->act;
+    a.nu = nu;
+    a.g = grouped ? group_size : 1;
+    a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
+    a.o_acc = acc;
+    a.o_dudt = dudt;
+    a.o_nh = nngb;
+    if ((rc = launch_search(a, SPHGRP_HYDRO, kAcc, grouped, c->sm_count, s))) return rc;
+    c->last.walks = a.ngroups;
+    return finish(c, s, 0);
+}
+
+int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c || !out) return set_error(SPHGRP_EINVAL, "null argument");
+    *out = c->last;
+    return SPHGRP_OK;
+}
+
+}  // extern "C"

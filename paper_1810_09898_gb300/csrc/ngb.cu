@@ -1,0 +1,836 @@
+// Neighbour search and the SPH loops that consume it.
+//
+// Two forms (Sec. 2.1 standard search, Sec. 3.1 Neighbour Recycling):
+//  * individual: one thread per active particle walks the octree depth-first with
+//    skip pointers and radius h_i (hydro: max(h_i, node hmax)), testing the particles
+//    of every opened leaf;
+//  * grouped: one warp per group of consecutive active particles (key order).  The
+//    warp walks the octree cooperatively once for the group (32 nodes tested per
+//    step) with the radius that covers every member's sphere, streams the particles
+//    of the opened leaves (the common superset) through shared memory in tiles, and
+//    every member filters the tile down to its own neighbours.
+//
+// Pair decisions are taken in FP32 on coordinates relative to a fixed-point centre;
+// pairs whose FP32 r^2 falls inside the proven error band around the threshold are
+// re-decided from the FP64 positions with the oracle's exact arithmetic, so the
+// neighbour sets are those of the FP64 definition.  Sums are FP32 with compensated
+// (Kahan) accumulation.
+#include "search_args.cuh"
+
+namespace sphgrp {
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kStackCap = 512;
+constexpr int kRangeCap = 96;
+constexpr int kTileD = 256;   // density tile (candidates)
+constexpr int kTileH = 128;   // hydro tile
+
+struct LocalCounters {
+    unsigned long long nodes = 0, cands = 0, tests = 0, pairs = 0, retests = 0;
+    int max_stack = 0;
+};
+
+__device__ __forceinline__ void flush_counters(const SearchArgs& a, LocalCounters& lc, int lane) {
+    // warp-reduce then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        lc.nodes += __shfl_xor_sync(0xffffffffu, lc.nodes, o);
+        lc.cands += __shfl_xor_sync(0xffffffffu, lc.cands, o);
+        lc.tests += __shfl_xor_sync(0xffffffffu, lc.tests, o);
+        lc.pairs += __shfl_xor_sync(0xffffffffu, lc.pairs, o);
+        lc.retests += __shfl_xor_sync(0xffffffffu, lc.retests, o);
+        lc.max_stack = max(lc.max_stack, __shfl_xor_sync(0xffffffffu, lc.max_stack, o));
+    }
+    if (lane == 0) {
+        if (lc.nodes) atomicAdd(&a.ctr->nodes, lc.nodes);
+        if (lc.cands) atomicAdd(&a.ctr->cands, lc.cands);
+        if (lc.tests) atomicAdd(&a.ctr->tests, lc.tests);
+        if (lc.pairs) atomicAdd(&a.ctr->pairs, lc.pairs);
+        if (lc.retests) atomicAdd(&a.ctr->retests, lc.retests);
+        atomicMax(&a.ctr->max_stack, (unsigned long long)lc.max_stack);
+    }
+}
+
+// Squared distance, in fixed-point units^2 and rounded down, from the point C to a
+// node's box (conservative: never larger than the true distance).
+__device__ __forceinline__ float node_gap2(const uint4& cen, const float4& ext, uint32_t cx,
+                                           uint32_t cy, uint32_t cz) {
+    float dx = fabsf(__int2float_rz((int32_t)(cen.x - cx)));
+    float dy = fabsf(__int2float_rz((int32_t)(cen.y - cy)));
+    float dz = fabsf(__int2float_rz((int32_t)(cen.z - cz)));
+    float gx = fmaxf(__fsub_rd(dx, ext.x), 0.0f);
+    float gy = fmaxf(__fsub_rd(dy, ext.y), 0.0f);
+    float gz = fmaxf(__fsub_rd(dz, ext.z), 0.0f);
+    return __fadd_rd(__fadd_rd(__fmul_rd(gx, gx), __fmul_rd(gy, gy)), __fmul_rd(gz, gz));
+}
+
+// radius in box units -> squared radius in fixed-point units, rounded up, with a
+// relative margin for the FP32 error of the radius itself
+__device__ __forceinline__ float radius2_units(float r_box) {
+    float r = __fmul_ru(__fmul_ru(r_box, 1.0000010f), 4294967296.0f);
+    return __fmul_ru(r, r);
+}
+
+// ---------------------------------------------------------------------------------
+// Per-member state
+// ---------------------------------------------------------------------------------
+
+struct DMember {
+    float mx, my, mz;
+    float hinv;
+    float h2lo, h2hi;   // decided-inside below h2lo, candidate below h2hi
+    int rank;           // -1: slot empty
+    float s0, c0, s1, c1;
+    int n;
+    int64_t xpos;       // export write position
+};
+
+struct HMember {
+    float mx, my, mz;
+    float h, hinv, sk;  // sk = 8 / (pi h^4): dW/dr = sk * dw/dq
+    float h2, bk;       // h^2 (FP32 of the FP64 square), band offset 8 b |m|^2
+    float vx, vy, vz, cs, A, rho;
+    int rank;
+    float sx, cx_, sy, cy_, sz, cz_, su, cu;
+    int n;
+    int64_t xpos;
+};
+
+__device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, int rank, uint32_t cx,
+                                             uint32_t cy, uint32_t cz) {
+    M.rank = rank;
+    M.s0 = M.c0 = M.s1 = M.c1 = 0.0f;
+    M.n = 0;
+    M.xpos = 0;
+    if (rank < 0) {
+        M.mx = M.my = M.mz = 0.0f;
+        M.hinv = 0.0f;
+        M.h2lo = M.h2hi = -1.0f;
+        return;
+    }
+    uint4 P = a.pfix[rank];
+    float4 O = a.poff[rank];
+    M.mx = rel_coord(P.x, O.x, cx);
+    M.my = rel_coord(P.y, O.y, cy);
+    M.mz = rel_coord(P.z, O.z, cz);
+    double h = a.h64[rank];
+    float hf = (float)h;
+    M.hinv = 1.0f / hf;
+    float h2 = (float)(h * h);
+    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
+    float bk = 8.0f * kBandRel * m2;
+    M.h2hi = fmaf(h2, 1.0f + 3.0f * kBandRel, bk);
+    M.h2lo = fmaf(h2, 1.0f - 3.0f * kBandRel, -bk);
+}
+
+__device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, int rank, uint32_t cx,
+                                             uint32_t cy, uint32_t cz) {
+    M.rank = rank;
+    M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = M.su = M.cu = 0.0f;
+    M.n = 0;
+    M.xpos = 0;
+    if (rank < 0) {
+        M.mx = M.my = M.mz = 0.0f;
+        M.h = 0.0f; M.hinv = 0.0f; M.sk = 0.0f;
+        M.h2 = -1.0f; M.bk = -1.0f;
+        M.vx = M.vy = M.vz = M.cs = M.A = M.rho = 0.0f;
+        return;
+    }
+    uint4 P = a.pfix[rank];
+    float4 O = a.poff[rank];
+    M.mx = rel_coord(P.x, O.x, cx);
+    M.my = rel_coord(P.y, O.y, cy);
+    M.mz = rel_coord(P.z, O.z, cz);
+    double h = a.h64[rank];
+    M.h = (float)h;
+    float4 H0 = a.hyd0[rank];
+    float4 H1 = a.hyd1[rank];
+    M.hinv = H1.z;
+    M.sk = H1.w;
+    M.h2 = (float)(h * h);
+    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
+    M.bk = 8.0f * kBandRel * m2;
+    M.vx = H0.x; M.vy = H0.y; M.vz = H0.z; M.cs = H0.w;
+    M.A = H1.x;
+    M.rho = H1.y;
+}
+
+// ---------------------------------------------------------------------------------
+// Pair physics shared by both forms
+// ---------------------------------------------------------------------------------
+
+// density pair: cand = {dx, dy, dz, m_j} relative to the same centre as the member
+template <int MODE>
+__device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, float4 cand, int crank,
+                                             LocalCounters& lc) {
+    float dx = cand.x - M.mx, dy = cand.y - M.my, dz = cand.z - M.mz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    bool in = r2 < M.h2lo;
+    if (!in) {
+        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
+        double h = a.h64[M.rank];
+        in = e < __dmul_rn(h, h);
+        lc.retests++;
+    }
+    if (!in) return;
+    M.n++;
+    lc.pairs++;
+    if (MODE == kAcc) {
+        float q = sqrtf(r2) * M.hinv;
+        float w, dw;
+        m4_shape(q, w, dw);
+        kahan_add(M.s0, M.c0, cand.w * w);
+        kahan_add(M.s1, M.c1, cand.w * fmaf(q, dw, 3.0f * w));
+    } else if (MODE == kFill) {
+        int64_t p = M.xpos++;
+        if (p < a.x_cap) a.x_idx[p] = a.perm[crank];
+        else atomicOr(a.err, kErrCap);
+    }
+}
+
+// hydro pair: p = {dx, dy, dz, m_j}, hh = {h_j, hinv_j, s_j, A_j}, v = {vx, vy, vz, c_j}
+template <int MODE>
+__device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 hh,
+                                           float4 v, float rho_j, int crank, LocalCounters& lc) {
+    if (crank == M.rank) return;
+    float dx = p.x - M.mx, dy = p.y - M.my, dz = p.z - M.mz;
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float H2 = fmaxf(M.h2, hh.x * hh.x);
+    bool in = r2 < fmaf(H2, 1.0f - 3.0f * kBandRel, -M.bk);
+    if (!in) {
+        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
+        double hi = a.h64[M.rank], hj = a.h64[crank];
+        in = e < fmax(__dmul_rn(hi, hi), __dmul_rn(hj, hj));
+        lc.retests++;
+    }
+    if (!in) return;
+    M.n++;
+    lc.pairs++;
+    if (MODE == kFill) {
+        int64_t q = M.xpos++;
+        if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
+        else atomicOr(a.err, kErrCap);
+        return;
+    }
+    if (MODE != kAcc) return;
+    if (r2 == 0.0f) return;  // coincident: the kernel gradient vanishes
+    float r = sqrtf(r2);
+    float rinv = 1.0f / r;
+    float wi, dwi, wj, dwj;
+    m4_shape(r * M.hinv, wi, dwi);
+    m4_shape(r * hh.y, wj, dwj);
+    float dWi = M.sk * dwi;
+    float dWj = hh.z * dwj;
+    float rx = -dx, ry = -dy, rz = -dz;  // r_ij = x_i - x_j
+    float vx = M.vx - v.x, vy = M.vy - v.y, vz = M.vz - v.z;
+    float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+    float visc = 0.0f;
+    if (vr < 0.0f) {
+        float hb = 0.5f * (M.h + hh.x);
+        float mu = hb * vr / fmaf(a.eps * hb, hb, r2);
+        float cb = 0.5f * (M.cs + v.w);
+        float rb = 0.5f * (M.rho + rho_j);
+        visc = fmaf(-a.alpha * cb, mu, a.beta * mu * mu) / rb;
+    }
+    float gbar = 0.5f * (dWi + dWj);
+    float coef = p.w * fmaf(M.A, dWi, fmaf(hh.w, dWj, visc * gbar)) * rinv;
+    kahan_add(M.sx, M.cx_, -coef * rx);
+    kahan_add(M.sy, M.cy_, -coef * ry);
+    kahan_add(M.sz, M.cz_, -coef * rz);
+    kahan_add(M.su, M.cu, p.w * fmaf(M.A, dWi, 0.5f * visc * gbar) * vr * rinv);
+}
+
+// ---------------------------------------------------------------------------------
+// Grouped form: one warp per group
+// ---------------------------------------------------------------------------------
+
+struct WalkSmem {
+    uint32_t stack[kStackCap];   // node ranges: (first child << 3) | (count - 1)
+    int2 ranges[kRangeCap];      // pending leaf ranges (first rank, count)
+    int rpre[kRangeCap + 1];     // prefix of the pending counts
+    int nodes[32];
+};
+
+struct DensTile {
+    float4 p[kTileD];   // {dx, dy, dz, m}
+    int r[kTileD];
+};
+
+struct HydroTile {
+    float4 p[kTileH];   // {dx, dy, dz, m}
+    float4 h[kTileH];   // {h, hinv, s, A}
+    float4 v[kTileH];   // {vx, vy, vz, c}
+    float rho[kTileH];
+    int r[kTileH];
+};
+
+template <int KIND>
+struct TileOf { using T = DensTile; static constexpr int cap = kTileD; };
+template <>
+struct TileOf<1> { using T = HydroTile; static constexpr int cap = kTileH; };
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Member slot layout of a lane: with group size g <= 32 a power of two, the warp
+// holds S = 32 / g copies ("slices") of the g members and each slice filters a
+// different subset of the candidates; otherwise the lane holds M members, one slice.
+struct Layout {
+    int S;       // slices
+    int slice;   // this lane's slice
+    int gw;      // members per slice row (min(g, 32))
+};
+
+__device__ __forceinline__ Layout make_layout(int g, int lane, bool allow_slices) {
+    Layout L;
+    L.gw = g < 32 ? g : 32;
+    bool pow2 = (g & (g - 1)) == 0;
+    L.S = (allow_slices && g < 32 && pow2) ? 32 / g : 1;
+    L.slice = L.S > 1 ? lane / g : 0;
+    return L;
+}
+
+// member index (within the group) held by slot mm of this lane; -1 if none
+__device__ __forceinline__ int member_of(const Layout& L, int lane, int mm, int g) {
+    int k;
+    if (L.S > 1) k = lane % g;
+    else k = lane + 32 * mm;
+    return k < g ? k : -1;
+}
+
+template <int KIND, int MODE, int M>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_group(SearchArgs a) {
+    using Tile = typename TileOf<KIND>::T;
+    constexpr int TCAP = TileOf<KIND>::cap;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WalkSmem& W = reinterpret_cast<WalkSmem*>(smem_raw)[wib];
+    Tile& T = reinterpret_cast<Tile*>(smem_raw + kWarpsPerBlock * sizeof(WalkSmem))[wib];
+    constexpr bool kSup = (MODE == kSupCount || MODE == kSupFill);
+    const bool allow_slices = (MODE == kAcc);
+    const Layout L = make_layout(a.g, lane, allow_slices);
+    LocalCounters lc;
+    const uint32_t lt = (1u << lane) - 1u;
+
+    for (;;) {
+        int gid = 0;
+        if (lane == 0) gid = atomicAdd(a.work, 1);
+        gid = __shfl_sync(0xffffffffu, gid, 0);
+        if (gid >= a.ngroups) break;
+        const int gbase = gid * a.g;
+        const int gcnt = min(a.g, a.nu - gbase);
+        // ---- group set-up: centre = fixed-point position of the first member
+        uint32_t cx = 0, cy = 0, cz = 0;
+        if (lane == 0) {
+            uint4 P = a.pfix[a.U[gbase]];
+            cx = P.x; cy = P.y; cz = P.z;
+        }
+        cx = __shfl_sync(0xffffffffu, cx, 0);
+        cy = __shfl_sync(0xffffffffu, cy, 0);
+        cz = __shfl_sync(0xffffffffu, cz, 0);
+
+        DMember dm[KIND == 0 ? M : 1];
+        HMember hm[KIND == 1 ? M : 1];
+        float rlane = 0.0f, hlane = 0.0f;   // walk radius ingredients of this lane
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) {
+            int k = member_of(L, lane, mm, a.g);
+            int rank = (k >= 0 && k < gcnt) ? a.U[gbase + k] : -1;
+            if (KIND == 0) {
+                dmember_init(dm[mm], a, rank, cx, cy, cz);
+                if (rank >= 0) {
+                    float mr = sqrtf(dm[mm].mx * dm[mm].mx + dm[mm].my * dm[mm].my + dm[mm].mz * dm[mm].mz);
+                    rlane = fmaxf(rlane, mr + (float)a.h64[rank]);
+                }
+            } else {
+                hmember_init(hm[mm], a, rank, cx, cy, cz);
+                if (rank >= 0) {
+                    float mr = sqrtf(hm[mm].mx * hm[mm].mx + hm[mm].my * hm[mm].my + hm[mm].mz * hm[mm].mz);
+                    rlane = fmaxf(rlane, mr);
+                    hlane = fmaxf(hlane, hm[mm].h);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            rlane = fmaxf(rlane, __shfl_xor_sync(0xffffffffu, rlane, o));
+            hlane = fmaxf(hlane, __shfl_xor_sync(0xffffffffu, hlane, o));
+        }
+        // density: R_s = max_k (|m_k| + h_k); hydro: R_g = max_k |m_k|, hmax_g
+        const float Rd2 = radius2_units(rlane);
+        const float Rg = rlane, hmax_g = hlane;
+
+        // export: write positions of every slot
+        if (MODE == kFill) {
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+                int rk = KIND == 0 ? dm[mm].rank : hm[mm].rank;
+                if (rk >= 0) {
+                    int64_t p = a.x_off[a.perm[rk]];
+                    if (KIND == 0) dm[mm].xpos = p; else hm[mm].xpos = p;
+                }
+            }
+        }
+        int64_t sup_pos = 0, sup_n = 0;
+        if (MODE == kSupFill) sup_pos = a.x_off[gid];
+
+        // ---- walk
+        int sp = 1;
+        if (lane == 0) W.stack[0] = 0u;   // root: node 0, one node
+        int nr = 0, pending = 0;
+        __syncwarp();
+        for (;;) {
+            while (sp > 0 && pending < TCAP && nr <= kRangeCap - 32) {
+                // take range entries from the top of the stack, up to 32 nodes
+                uint32_t ent = 0;
+                int ecnt = 0;
+                if (lane < sp) {
+                    ent = W.stack[sp - 1 - lane];
+                    ecnt = (int)(ent & 7u) + 1;
+                }
+                int incl = warp_incl_scan(ecnt, lane);
+                bool take = (lane < sp) && (incl <= 32);
+                unsigned tm = __ballot_sync(0xffffffffu, take);
+                int nent = __popc(tm);
+                int nnodes = __shfl_sync(0xffffffffu, incl, nent - 1);
+                if (take) {
+                    int first = (int)(ent >> 3), ex = incl - ecnt;
+                    for (int q = 0; q < ecnt; ++q) W.nodes[ex + q] = first + q;
+                }
+                sp -= nent;
+                __syncwarp();
+                int node = lane < nnodes ? W.nodes[lane] : -1;
+                __syncwarp();
+                bool open = false, leaf = false;
+                int4 lk = make_int4(0, 0, -1, 0);
+                int nch = 0;
+                if (node >= 0) {
+                    uint4 cen = a.ncen[node];
+                    float4 ext = a.next[node];
+                    lk = a.nlink[node];
+                    nch = __float_as_int(ext.w);
+                    float gap2 = node_gap2(cen, ext, cx, cy, cz);
+                    float R2;
+                    if (KIND == 0) R2 = Rd2;
+                    else R2 = radius2_units(Rg + fmaxf(hmax_g, __uint_as_float(cen.w)));
+                    open = gap2 <= R2;
+                    leaf = lk.z < 0;
+                }
+                lc.nodes += (lane == 0) ? nnodes : 0;
+                bool emit = open && leaf && lk.y > 0;
+                unsigned em = __ballot_sync(0xffffffffu, emit);
+                if (emit) {
+                    int pos = nr + __popc(em & lt);
+                    W.ranges[pos] = make_int2(lk.x, lk.y);
+                }
+                nr += __popc(em);
+                int add = emit ? lk.y : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+                pending += add;
+                bool push = open && !leaf;
+                unsigned pm = __ballot_sync(0xffffffffu, push);
+                if (push) {
+                    int pos = sp + __popc(pm & lt);
+                    if (pos < kStackCap) W.stack[pos] = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
+                    else atomicOr(a.err, kErrStack);
+                }
+                sp = min(sp + __popc(pm), kStackCap);
+                lc.max_stack = max(lc.max_stack, sp);
+                __syncwarp();
+            }
+            if (nr > 0) {
+                // ---- flush the pending leaf ranges in tiles
+                int run = 0;
+                for (int e0 = 0; e0 < nr; e0 += 32) {
+                    int e = e0 + lane;
+                    int c = e < nr ? W.ranges[e].y : 0;
+                    int inc = warp_incl_scan(c, lane);
+                    if (e < nr) W.rpre[e] = run + inc - c;
+                    run += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                if (lane == 0) W.rpre[nr] = run;
+                __syncwarp();
+                const int total = run;
+                lc.cands += (lane == 0) ? total : 0;
+                for (int t0 = 0; t0 < total; t0 += TCAP) {
+                    const int nt = min(TCAP, total - t0);
+                    for (int t = lane; t < nt; t += 32) {
+                        int gt = t0 + t;
+                        int lo = 0, hi = nr;   // largest e with rpre[e] <= gt
+                        while (hi - lo > 1) {
+                            int mid = (lo + hi) >> 1;
+                            if (W.rpre[mid] <= gt) lo = mid; else hi = mid;
+                        }
+                        int rank = W.ranges[lo].x + (gt - W.rpre[lo]);
+                        if (kSup) {
+                            if (MODE == kSupFill) {
+                                int64_t p = sup_pos + sup_n + gt;
+                                if (p < a.x_cap) a.x_idx[p] = a.perm[rank];
+                                else atomicOr(a.err, kErrCap);
+                            }
+                            continue;
+                        }
+                        uint4 P = a.pfix[rank];
+                        float4 O = a.poff[rank];
+                        float4 rel = make_float4(rel_coord(P.x, O.x, cx), rel_coord(P.y, O.y, cy),
+                                                 rel_coord(P.z, O.z, cz), O.w);
+                        if constexpr (KIND == 0) {
+                            T.p[t] = rel;
+                            T.r[t] = rank;
+                        } else {
+                            float4 H0 = a.hyd0[rank], H1 = a.hyd1[rank];
+                            T.p[t] = rel;
+                            T.h[t] = make_float4(__uint_as_float(P.w), H1.z, H1.w, H1.x);
+                            T.v[t] = H0;
+                            T.rho[t] = H1.y;
+                            T.r[t] = rank;
+                        }
+                    }
+                    __syncwarp();
+                    if (!kSup) {
+                        // ---- member x candidate filter of the tile
+                        const int njj = (nt > L.slice) ? (nt - L.slice + L.S - 1) / L.S : 0;
+                        for (int base = 0; base < njj; base += 32) {
+                            const int cnt = min(32, njj - base);
+                            uint32_t mask[M];
+#pragma unroll
+                            for (int mm = 0; mm < M; ++mm) mask[mm] = 0u;
+#pragma unroll 8
+                            for (int q = 0; q < 32; ++q) {
+                                int jj = min(base + q, njj - 1);
+                                int j = L.slice + L.S * jj;
+                                float4 cp = T.p[j];
+                                float hj = 0.0f;
+                                if constexpr (KIND == 1) hj = T.h[j].x;
+#pragma unroll
+                                for (int mm = 0; mm < M; ++mm) {
+                                    float mx, my, mz, thr;
+                                    if constexpr (KIND == 0) {
+                                        mx = dm[mm].mx; my = dm[mm].my; mz = dm[mm].mz; thr = dm[mm].h2hi;
+                                    } else {
+                                        mx = hm[mm].mx; my = hm[mm].my; mz = hm[mm].mz;
+                                        thr = fmaf(fmaxf(hm[mm].h2, hj * hj), 1.0f + 3.0f * kBandRel, hm[mm].bk);
+                                    }
+                                    float dx = cp.x - mx, dy = cp.y - my, dz = cp.z - mz;
+                                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                                    if (r2 < thr && q < cnt) mask[mm] |= 1u << q;
+                                }
+                            }
+#pragma unroll
+                            for (int mm = 0; mm < M; ++mm) {
+                                int rk = KIND == 0 ? dm[mm].rank : hm[mm].rank;
+                                if (rk >= 0) lc.tests += cnt;
+                                while (mask[mm]) {
+                                    int q = __ffs(mask[mm]) - 1;
+                                    mask[mm] &= mask[mm] - 1u;
+                                    int j = L.slice + L.S * (base + q);
+                                    if constexpr (KIND == 0) {
+                                        density_pair<MODE>(dm[mm], a, T.p[j], T.r[j], lc);
+                                    } else {
+                                        hydro_pair<MODE>(hm[mm], a, T.p[j], T.h[j], T.v[j], T.rho[j], T.r[j], lc);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                if (kSup) sup_n += total;
+                nr = 0;
+                pending = 0;
+            }
+            if (sp == 0) break;
+        }
+        lc.max_stack = max(lc.max_stack, 0);
+
+        // ---- results
+        if (kSup) {
+            if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
+            continue;
+        }
+        if (L.S > 1) {
+            // combine the slices of every member (lanes k, k+g, k+2g, ...)
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+                for (int o = a.g; o < 32; o <<= 1) {
+                    if constexpr (KIND == 0) {
+                        dm[mm].s0 += __shfl_xor_sync(0xffffffffu, dm[mm].s0, o);
+                        dm[mm].c0 += __shfl_xor_sync(0xffffffffu, dm[mm].c0, o);
+                        dm[mm].s1 += __shfl_xor_sync(0xffffffffu, dm[mm].s1, o);
+                        dm[mm].c1 += __shfl_xor_sync(0xffffffffu, dm[mm].c1, o);
+                        dm[mm].n += __shfl_xor_sync(0xffffffffu, dm[mm].n, o);
+                    } else {
+                        hm[mm].sx += __shfl_xor_sync(0xffffffffu, hm[mm].sx, o);
+                        hm[mm].cx_ += __shfl_xor_sync(0xffffffffu, hm[mm].cx_, o);
+                        hm[mm].sy += __shfl_xor_sync(0xffffffffu, hm[mm].sy, o);
+                        hm[mm].cy_ += __shfl_xor_sync(0xffffffffu, hm[mm].cy_, o);
+                        hm[mm].sz += __shfl_xor_sync(0xffffffffu, hm[mm].sz, o);
+                        hm[mm].cz_ += __shfl_xor_sync(0xffffffffu, hm[mm].cz_, o);
+                        hm[mm].su += __shfl_xor_sync(0xffffffffu, hm[mm].su, o);
+                        hm[mm].cu += __shfl_xor_sync(0xffffffffu, hm[mm].cu, o);
+                        hm[mm].n += __shfl_xor_sync(0xffffffffu, hm[mm].n, o);
+                    }
+                }
+            }
+        }
+        if (L.slice == 0) {
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+                if constexpr (KIND == 0) {
+                    const DMember& D = dm[mm];
+                    if (D.rank < 0) continue;
+                    if (MODE == kAcc) {
+                        a.o_s0[D.rank] = D.s0 - D.c0;
+                        a.o_s1[D.rank] = D.s1 - D.c1;
+                        a.o_n[D.rank] = D.n;
+                    } else if (MODE == kCount) {
+                        a.x_cnt[a.perm[D.rank]] = D.n;
+                    }
+                } else {
+                    const HMember& H = hm[mm];
+                    if (H.rank < 0) continue;
+                    int orig = a.perm[H.rank];
+                    if (MODE == kAcc) {
+                        a.o_acc[3 * (int64_t)orig] = H.sx - H.cx_;
+                        a.o_acc[3 * (int64_t)orig + 1] = H.sy - H.cy_;
+                        a.o_acc[3 * (int64_t)orig + 2] = H.sz - H.cz_;
+                        a.o_dudt[orig] = H.su - H.cu;
+                        if (a.o_nh) a.o_nh[orig] = H.n;
+                    } else if (MODE == kCount) {
+                        a.x_cnt[orig] = H.n;
+                    }
+                }
+            }
+        }
+    }
+    flush_counters(a, lc, lane);
+}
+
+// ---------------------------------------------------------------------------------
+// Individual form: one thread per particle, depth-first walk with skip pointers
+// ---------------------------------------------------------------------------------
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
+    const int lane = threadIdx.x & 31;
+    LocalCounters lc;
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < a.nu) {
+        const int rank = a.U[u];
+        uint4 P = a.pfix[rank];
+        const uint32_t cx = P.x, cy = P.y, cz = P.z;
+        DMember dm;
+        HMember hm;
+        float Rbox;
+        if (KIND == 0) {
+            dmember_init(dm, a, rank, cx, cy, cz);
+            Rbox = (float)a.h64[rank];
+            if (MODE == kFill) dm.xpos = a.x_off[a.perm[rank]];
+        } else {
+            hmember_init(hm, a, rank, cx, cy, cz);
+            Rbox = hm.h;
+            if (MODE == kFill) hm.xpos = a.x_off[a.perm[rank]];
+        }
+        const float R2d = radius2_units(Rbox);
+        int node = 0;
+        while (node >= 0) {
+            uint4 cen = a.ncen[node];
+            float4 ext = a.next[node];
+            int4 lk = a.nlink[node];
+            lc.nodes++;
+            float gap2 = node_gap2(cen, ext, cx, cy, cz);
+            float R2 = KIND == 0 ? R2d : radius2_units(fmaxf(Rbox, __uint_as_float(cen.w)));
+            if (gap2 <= R2) {
+                if (lk.z < 0) {
+                    lc.cands += lk.y;
+                    lc.tests += lk.y;
+                    for (int q = lk.x; q < lk.x + lk.y; ++q) {
+                        uint4 Q = a.pfix[q];
+                        float4 O = a.poff[q];
+                        float4 rel = make_float4(rel_coord(Q.x, O.x, cx), rel_coord(Q.y, O.y, cy),
+                                                 rel_coord(Q.z, O.z, cz), O.w);
+                        if (KIND == 0) {
+                            float dx = rel.x - dm.mx, dy = rel.y - dm.my, dz = rel.z - dm.mz;
+                            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            if (r2 < dm.h2hi) density_pair<MODE>(dm, a, rel, q, lc);
+                        } else {
+                            float hj = __uint_as_float(Q.w);
+                            float dx = rel.x - hm.mx, dy = rel.y - hm.my, dz = rel.z - hm.mz;
+                            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            float thr = fmaf(fmaxf(hm.h2, hj * hj), 1.0f + 3.0f * kBandRel, hm.bk);
+                            if (r2 < thr) {
+                                float4 H0 = a.hyd0[q], H1 = a.hyd1[q];
+                                hydro_pair<MODE>(hm, a, rel, make_float4(hj, H1.z, H1.w, H1.x), H0, H1.y, q, lc);
+                            }
+                        }
+                    }
+                    node = lk.w;
+                } else {
+                    node = lk.z;
+                }
+            } else {
+                node = lk.w;
+            }
+        }
+        if (KIND == 0) {
+            if (MODE == kAcc) {
+                a.o_s0[rank] = dm.s0 - dm.c0;
+                a.o_s1[rank] = dm.s1 - dm.c1;
+                a.o_n[rank] = dm.n;
+            } else if (MODE == kCount) {
+                a.x_cnt[a.perm[rank]] = dm.n;
+            }
+        } else {
+            int orig = a.perm[rank];
+            if (MODE == kAcc) {
+                a.o_acc[3 * (int64_t)orig] = hm.sx - hm.cx_;
+                a.o_acc[3 * (int64_t)orig + 1] = hm.sy - hm.cy_;
+                a.o_acc[3 * (int64_t)orig + 2] = hm.sz - hm.cz_;
+                a.o_dudt[orig] = hm.su - hm.cu;
+                if (a.o_nh) a.o_nh[orig] = hm.n;
+            } else if (MODE == kCount) {
+                a.x_cnt[orig] = hm.n;
+            }
+        }
+    }
+    flush_counters(a, lc, lane);
+}
+
+// ---------------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------------
+
+template <int KIND>
+static size_t group_smem() {
+    return kWarpsPerBlock * (sizeof(WalkSmem) + sizeof(typename TileOf<KIND>::T));
+}
+
+template <int KIND, int MODE, int M>
+static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
+    auto kern = k_group<KIND, MODE, M>;
+    size_t sh = group_smem<KIND>();
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+        configured = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, sh);
+    if (per_sm < 1) per_sm = 1;
+    int64_t want = (a.ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    int64_t grid = std::min<int64_t>((int64_t)per_sm * sm_count, want);
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kWarpsPerBlock * 32, sh, s>>>(a);
+    return check_cuda(cudaGetLastError(), "grouped search kernel");
+}
+
+template <int KIND, int MODE>
+static int launch_group_m(const SearchArgs& a, int sm_count, cudaStream_t s) {
+    int M = (a.g + 31) / 32;
+    if (M <= 1) return launch_group_t<KIND, MODE, 1>(a, sm_count, s);
+    if (M <= 2) return launch_group_t<KIND, MODE, 2>(a, sm_count, s);
+    if (M <= 4) return launch_group_t<KIND, MODE, 4>(a, sm_count, s);
+    return set_error(SPHGRP_EINVAL, "group_size must be <= 128");
+}
+
+int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s) {
+    if (a.nu <= 0) return SPHGRP_OK;
+    if (grouped) {
+        cudaMemsetAsync(a.work, 0, sizeof(int), s);
+        if (kind == 0) {
+            switch (mode) {
+                case kAcc: return launch_group_m<0, kAcc>(a, sm_count, s);
+                case kCount: return launch_group_m<0, kCount>(a, sm_count, s);
+                case kFill: return launch_group_m<0, kFill>(a, sm_count, s);
+                case kSupCount: return launch_group_m<0, kSupCount>(a, sm_count, s);
+                case kSupFill: return launch_group_m<0, kSupFill>(a, sm_count, s);
+            }
+        } else {
+            switch (mode) {
+                case kAcc: return launch_group_m<1, kAcc>(a, sm_count, s);
+                case kCount: return launch_group_m<1, kCount>(a, sm_count, s);
+                case kFill: return launch_group_m<1, kFill>(a, sm_count, s);
+                case kSupCount: return launch_group_m<1, kSupCount>(a, sm_count, s);
+                case kSupFill: return launch_group_m<1, kSupFill>(a, sm_count, s);
+            }
+        }
+        return set_error(SPHGRP_EINVAL, "bad search mode");
+    }
+    int blocks = blocks_for(a.nu, 128);
+    if (kind == 0) {
+        if (mode == kAcc) k_indiv<0, kAcc><<<blocks, 128, 0, s>>>(a);
+        else if (mode == kCount) k_indiv<0, kCount><<<blocks, 128, 0, s>>>(a);
+        else if (mode == kFill) k_indiv<0, kFill><<<blocks, 128, 0, s>>>(a);
+        else return set_error(SPHGRP_EINVAL, "bad search mode");
+    } else {
+        if (mode == kAcc) k_indiv<1, kAcc><<<blocks, 128, 0, s>>>(a);
+        else if (mode == kCount) k_indiv<1, kCount><<<blocks, 128, 0, s>>>(a);
+        else if (mode == kFill) k_indiv<1, kFill><<<blocks, 128, 0, s>>>(a);
+        else return set_error(SPHGRP_EINVAL, "bad search mode");
+    }
+    return check_cuda(cudaGetLastError(), "individual search kernel");
+}
+
+// ---------------------------------------------------------------------------------
+// Smoothing-length iteration: per unconverged particle, FP64
+// ---------------------------------------------------------------------------------
+
+__global__ void k_hsml_update(UpdateArgs a) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= a.nu) return;
+    const int r = a.U[u];
+    const double h = a.h64[r];
+    const double m = (double)a.poff[r].w;
+    const double kPi = 3.14159265358979323846;
+    const double sigma = 8.0 / (kPi * h * h * h);
+    const double rho = sigma * (double)a.s0[r];
+    const double drho = -sigma / h * (double)a.s1[r];
+    const double neff = 4.0 * kPi / 3.0 * h * h * h * rho / m;
+    bool done = !a.iterate || fabs(neff - a.nngb) <= a.tol;
+    bool last = a.it >= a.max_iter;
+    if (done || last) {
+        const int orig = a.perm[r];
+        a.rho[orig] = (float)rho;
+        a.drhodh[orig] = (float)drho;
+        a.fgrad[orig] = (float)(1.0 / (1.0 + h / (3.0 * rho) * drho));
+        a.nngb_out[orig] = a.n[r];
+        if (a.iters) a.iters[orig] = a.it;
+        a.h_out[orig] = h;
+        a.keep[u] = 0;
+        if (!done) atomicAdd(a.nfail, 1);
+        return;
+    }
+    double lo = a.it == 1 ? 0.0 : a.lo[r];
+    double hi = a.it == 1 ? __longlong_as_double(0x7ff0000000000000ll) : a.hi[r];
+    if (neff < a.nngb) lo = h; else hi = h;
+    const double g = 4.0 * kPi / 3.0 * h * h * h * rho - a.nngb * m;
+    const double gp = 4.0 * kPi * h * h * rho + 4.0 * kPi / 3.0 * h * h * h * drho;
+    double hn = h - g / gp;
+    const double cbrt2 = 1.2599210498948731647672106;
+    if (!(hn > lo && hn < hi) || !isfinite(hn)) {
+        if (isinf(hi)) hn = h * cbrt2;
+        else if (lo == 0.0) hn = h / cbrt2;
+        else hn = cbrt(0.5 * (lo * lo * lo + hi * hi * hi));
+    }
+    a.lo[r] = lo;
+    a.hi[r] = hi;
+    a.h64[r] = hn;
+    a.pfix[r].w = __float_as_uint((float)hn);
+    a.keep[u] = 1;
+}
+
+int launch_hsml_update(const UpdateArgs& a, cudaStream_t s) {
+    if (a.nu <= 0) return SPHGRP_OK;
+    k_hsml_update<<<blocks_for(a.nu, 256), 256, 0, s>>>(a);
+    return check_cuda(cudaGetLastError(), "hsml update");
+}
+
+}  // namespace sphgrp

@@ -1,0 +1,83 @@
+// Argument blocks of the search and smoothing-length kernels (ngb.cu), filled by
+// the C ABI layer (api.cu).
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sphgrp {
+
+enum Mode { kAcc = 0, kCount = 1, kFill = 2, kSupCount = 3, kSupFill = 4 };
+
+struct SearchArgs {
+    // octree
+    const uint4* ncen;
+    const float4* next;
+    const int4* nlink;
+    // key-ordered particles
+    const uint4* pfix;
+    const float4* poff;
+    const double *xd, *yd, *zd;
+    const double* h64;
+    const float4* hyd0;   // {vx, vy, vz, c}
+    const float4* hyd1;   // {A, rho, hinv, s}
+    const int32_t* perm;
+    // work list: ranks of the particles to process, in key order
+    const int32_t* U;
+    int nu;
+    int g;          // group size (grouped form)
+    int ngroups;
+    // density pass results (rank space)
+    float* o_s0;
+    float* o_s1;
+    int32_t* o_n;
+    // hydro results (original order)
+    float* o_acc;
+    float* o_dudt;
+    int32_t* o_nh;
+    // export (indexed by original particle index)
+    const int64_t* x_off;
+    int64_t* x_cnt;
+    int32_t* x_idx;
+    int64_t x_cap;
+    // hydro constants
+    float alpha, beta, eps;
+    // bookkeeping
+    DevCounters* ctr;
+    unsigned* err;
+    int* work;
+};
+
+struct UpdateArgs {
+    const int32_t* U;
+    int nu;
+    int it;
+    int max_iter;
+    double nngb, tol;
+    const float* s0;
+    const float* s1;
+    const int32_t* n;
+    const float4* poff;
+    double* h64;
+    uint4* pfix;
+    double* lo;
+    double* hi;
+    int32_t* keep;        // 1 = still unconverged
+    const int32_t* perm;
+    // caller outputs (original order)
+    double* h_out;
+    float* rho;
+    float* drhodh;
+    float* fgrad;
+    int32_t* nngb_out;
+    int32_t* iters;
+    int iterate;
+    int* nfail;
+};
+
+int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s);
+int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
+int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s);
+int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+                       cudaStream_t s);
+
+}  // namespace sphgrp

@@ -1,0 +1,305 @@
+// Peano-Hilbert keys, the stable device radix sort of (key, index) and a device
+// exclusive scan (Sec. 2.2: Gadget3 orders its particles along the Hilbert curve).
+#include <cooperative_groups.h>
+
+#include "sph_internal.cuh"
+
+namespace sphgrp {
+
+// ---------------------------------------------------------------------------------
+// Keys
+// ---------------------------------------------------------------------------------
+
+// Spreads the low 21 bits of v so that bit b lands on bit 3b.
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Hilbert index of a cell of the 2^21 grid by Skilling's transpose construction:
+// from the coarsest level down, every axis either reflects (bit set) or swaps its
+// lower bits with axis 0 (bit clear); then a Gray code across the axes and a common
+// correction; the index interleaves the transposed words, axis 0 most significant.
+__device__ __forceinline__ uint64_t hilbert_key(uint32_t a0, uint32_t a1, uint32_t a2) {
+#pragma unroll 1
+    for (uint32_t q = 1u << (kKeyLevels - 1); q > 1u; q >>= 1) {
+        const uint32_t lowmask = q - 1u;
+        if (a0 & q) a0 ^= lowmask;
+        if (a1 & q) {
+            a0 ^= lowmask;
+        } else {
+            uint32_t t = (a0 ^ a1) & lowmask;
+            a0 ^= t;
+            a1 ^= t;
+        }
+        if (a2 & q) {
+            a0 ^= lowmask;
+        } else {
+            uint32_t t = (a0 ^ a2) & lowmask;
+            a0 ^= t;
+            a2 ^= t;
+        }
+    }
+    a1 ^= a0;
+    a2 ^= a1;
+    uint32_t corr = 0;
+#pragma unroll 1
+    for (uint32_t q = 1u << (kKeyLevels - 1); q > 1u; q >>= 1)
+        if (a2 & q) corr ^= q - 1u;
+    a0 ^= corr;
+    a1 ^= corr;
+    a2 ^= corr;
+    return (spread3(a0) << 2) | (spread3(a1) << 1) | spread3(a2);
+}
+
+__device__ __forceinline__ uint32_t grid21(double x) {
+    double s = floor(x * 2097152.0);
+    s = fmin(fmax(s, 0.0), 2097151.0);
+    return (uint32_t)s;
+}
+
+__global__ void k_keys(int64_t n, const double* __restrict__ pos, uint64_t* __restrict__ keys,
+                       unsigned* err) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    bool ok = (x >= 0.0) & (x < 1.0) & (y >= 0.0) & (y < 1.0) & (z >= 0.0) & (z < 1.0);
+    if (!ok) atomicOr(err, kErrRange);
+    keys[i] = hilbert_key(grid21(x), grid21(y), grid21(z));
+}
+
+// ---------------------------------------------------------------------------------
+// Exclusive scan (int32 / int64), three phases: tile sums, scan of the sums
+// (recursive), tile scan with carry.  Tiles of 4096 = 1024 threads x 4 items.
+// ---------------------------------------------------------------------------------
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ __forceinline__ T block_exclusive(T v, T* warp_tot, T& block_total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T s = (lane < (int)(blockDim.x >> 5)) ? warp_tot[lane] : T(0);
+        T si = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += t;
+        }
+        warp_tot[lane] = si - s;  // exclusive prefix of warp totals
+        if (lane == 31) warp_tot[32] = si;
+    }
+    __syncthreads();
+    block_total = warp_tot[32];
+    T r = warp_tot[w] + inc - v;
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void k_scan_reduce(const T* __restrict__ in, int64_t n, T* __restrict__ sums) {
+    __shared__ T wt[33];
+    int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    T tot;
+    block_exclusive<T>(s, wt, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void k_scan_down(const T* in, T* out, int64_t n, const T* __restrict__ carry,
+                            T* total) {
+    __shared__ T wt[33];
+    int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : T(0);
+        s += v[k];
+    }
+    T tot;
+    T ex = block_exclusive<T>(s, wt, tot);
+    T c = carry ? carry[blockIdx.x] : T(0);
+    T run = c + ex;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) *total = c + tot;
+}
+
+template <typename T>
+static void scan_rec(const T* in, T* out, int64_t n, T* aux, T* total, cudaStream_t s) {
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb <= 1) {
+        k_scan_down<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total);
+        return;
+    }
+    k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, aux);
+    scan_rec<T>(aux, aux, nb, aux + nb, nullptr, s);
+    k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, aux, total);
+}
+
+static int64_t scan_aux_need(int64_t n) {
+    int64_t need = 0;
+    while (n > kScanTile) {
+        n = (n + kScanTile - 1) / kScanTile;
+        need += n;
+    }
+    return need + 8;
+}
+
+int exclusive_scan_i32(Ctx* c, const int32_t* in, int32_t* out, int64_t n, int32_t* total_dev,
+                       cudaStream_t s) {
+    if (n <= 0) return SPHGRP_OK;
+    if (scan_aux_need(n) > c->scan_aux_cap) return set_error(SPHGRP_EOVERFLOW, "scan scratch too small");
+    scan_rec<int32_t>(in, out, n, c->scan_aux, total_dev, s);
+    return check_cuda(cudaGetLastError(), "scan");
+}
+
+int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+                       cudaStream_t s) {
+    if (n <= 0) return SPHGRP_OK;
+    if (2 * scan_aux_need(n) > c->scan_aux_cap) return set_error(SPHGRP_EOVERFLOW, "scan scratch too small");
+    scan_rec<int64_t>(in, out, n, reinterpret_cast<int64_t*>(c->scan_aux), total_dev, s);
+    return check_cuda(cudaGetLastError(), "scan");
+}
+
+// ---------------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits, stable.  Per pass: tile histograms (digit-major),
+// exclusive scan, and a scatter that ranks keys inside the tile with warp matching.
+// A tile is 256 threads x 8 keys; warp w owns the contiguous 256 keys
+// [w*256, w*256+256) of the tile, processed 32 at a time in order, so ranks follow
+// the input order (stability).
+// ---------------------------------------------------------------------------------
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortWarps = kSortThreads / 32;
+
+__global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                             uint32_t* __restrict__ hist, int nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = blockIdx.x * (int64_t)kSortTile;
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        int64_t i = base + k * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xffu], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
+                                uint64_t* __restrict__ kout, int32_t* __restrict__ vout,
+                                int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                int nblocks) {
+    __shared__ uint32_t wh[kSortWarps][256];
+    __shared__ uint32_t gbase[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wh[0][0])[d] = 0;
+    gbase[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    __syncthreads();
+    const int64_t base = blockIdx.x * (int64_t)kSortTile + w * 256;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint64_t kk[kSortItems];
+    int32_t vv[kSortItems];
+    uint32_t rk[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = base + r * 32 + lane;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0ull;
+        kk[r] = key;
+        vv[r] = valid ? (vin ? vin[i] : (int32_t)i) : 0;
+        uint32_t d = valid ? (uint32_t)((key >> shift) & 0xffu) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t prev = (d < 256u) ? wh[w][d] : 0u;
+        __syncwarp();
+        if (d < 256u && lane == __ffs(peers) - 1) wh[w][d] = prev + __popc(peers);
+        __syncwarp();
+        rk[r] = prev + __popc(peers & lt);
+    }
+    __syncthreads();
+    // exclusive prefix over warps for every digit (thread t owns digit t)
+    {
+        uint32_t run = 0;
+        const int d = threadIdx.x;
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            uint32_t c = wh[ww][d];
+            wh[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = (uint32_t)((kk[r] >> shift) & 0xffu);
+            uint32_t p = gbase[d] + wh[w][d] + rk[r];
+            kout[p] = kk[r];
+            vout[p] = vv[r];
+        }
+    }
+}
+
+__global__ void k_invert_perm(int64_t n, const int32_t* __restrict__ perm, int32_t* __restrict__ rank_of) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r < n) rank_of[perm[r]] = (int32_t)r;
+}
+
+int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s) {
+    // keys in input order go to keys_alt; the passes ping-pong keys_alt <-> keys
+    k_keys<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, c->keys_alt, c->err);
+    int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    int64_t nh = (int64_t)256 * nblocks;
+    if (nh > c->hist_cap) return set_error(SPHGRP_EOVERFLOW, "radix histogram scratch too small");
+    uint64_t* kin = c->keys_alt;
+    uint64_t* kout = c->keys;
+    int32_t* vin = nullptr;
+    int32_t* vout = c->perm;
+    for (int pass = 0; pass < 8; ++pass) {
+        int shift = 8 * pass;
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, n, shift, c->hist, nblocks);
+        int rc = exclusive_scan_i32(c, reinterpret_cast<const int32_t*>(c->hist),
+                                    reinterpret_cast<int32_t*>(c->hist), nh, nullptr, s);
+        if (rc) return rc;
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, c->hist, nblocks);
+        // swap
+        uint64_t* tk = kin; kin = kout; kout = tk;
+        if (pass == 0) { vin = c->perm; vout = c->perm_alt; }
+        else { int32_t* tv = vin; vin = vout; vout = tv; }
+    }
+    // the last pass wrote into the alternate buffers: swap the context's pointers
+    if (kin != c->keys) { uint64_t* t = c->keys; c->keys = c->keys_alt; c->keys_alt = t; }
+    if (vin != c->perm) { int32_t* t = c->perm; c->perm = c->perm_alt; c->perm_alt = t; }
+    k_invert_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->rank_of);
+    return check_cuda(cudaGetLastError(), "sort");
+}
+
+}  // namespace sphgrp

@@ -1,0 +1,178 @@
+// Internal declarations of the CUDA path: the context, the key-ordered particle
+// layout, the octree layout and the device helpers used by several kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sphgrp.h"
+
+namespace sphgrp {
+
+// ---------------------------------------------------------------------------------
+// Layout in HBM (all arrays indexed by rank = position in key order unless noted)
+//
+//   keys      uint64   sorted Peano-Hilbert keys
+//   perm      int32    rank -> original index
+//   rank_of   int32    original index -> rank
+//   xd,yd,zd  double   absolute positions (FP64; read only by the rare FP64 re-tests)
+//   pfix      uint4    {X, Y, Z, h_f32 bits}: fixed-point position X = floor(x 2^32)
+//   poff      float4   {x 2^32 - X, ..., m}: sub-unit offsets in [0,1) and the mass
+//   h64       double   smoothing length (FP64 master)
+//   hyd0      float4   {vx, vy, vz, A = f P / rho^2}          (hydro candidates)
+//   hyd1      float4   {rho, c, unused, unused}               (hydro candidates)
+//
+// A coordinate relative to a fixed-point centre C is
+//   float(int32(X - C)) + off, scaled by 2^-32:
+// the integer difference is exact and wraps to the minimum image of the periodic
+// unit cube for free (two's complement), the offset keeps the FP64 position's
+// precision, so the only rounding is the final FP32 one.
+// ---------------------------------------------------------------------------------
+
+constexpr float kUnitToBox = 2.3283064365386962890625e-10f;  // 2^-32
+constexpr double kBoxToUnit = 4294967296.0;                   // 2^32
+constexpr int kKeyLevels = 21;
+
+// Octree: nodes are stored level by level; the children of a node are contiguous.
+//   ncen  uint4  {cx, cy, cz, hmax bits}   centre of the tight box in fixed point
+//   next  float4 {ex, ey, ez, nchild bits} half extents in fixed-point units, padded
+//                                          to cover the sub-unit offsets
+//   nlink int4   {first, count, child_first (-1 = leaf), skip}
+// skip = the node visited after this one's subtree in a depth-first walk (-1 = end).
+struct Tree {
+    uint4* ncen = nullptr;
+    float4* next = nullptr;
+    int4* nlink = nullptr;
+    int32_t* nlevel = nullptr;     // level of every node
+    int64_t cap = 0;               // allocated nodes
+    int64_t count = 0;             // nodes in the current tree
+    int level_begin[kKeyLevels + 3] = {0};  // node ranges per level (host copy)
+    int nlevels = 0;
+};
+
+struct DevCounters {
+    unsigned long long walks, nodes, cands, tests, pairs, retests, max_stack, pad;
+};
+
+enum ErrBits : unsigned {
+    kErrRange = 1u,      // position outside [0,1) or NaN
+    kErrStack = 2u,      // walk stack overflow
+    kErrNodes = 4u,      // node capacity exceeded
+    kErrCap = 8u,        // export capacity exceeded
+    kErrH = 16u,         // smoothing length outside (0, 0.5)
+};
+
+struct Ctx {
+    sphgrp_params p;
+    int64_t n_max = 0;
+    int64_t n = 0;
+    bool sorted = false;
+    bool built = false;
+    int sm_count = 0;
+
+    // key order
+    uint64_t* keys = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* rank_of = nullptr;
+    // sort scratch
+    uint64_t* keys_alt = nullptr;
+    int32_t* perm_alt = nullptr;
+    uint32_t* hist = nullptr;      // radix histograms
+    int64_t hist_cap = 0;
+    // particle copies
+    double *xd = nullptr, *yd = nullptr, *zd = nullptr;
+    uint4* pfix = nullptr;
+    float4* poff = nullptr;
+    double* h64 = nullptr;
+    float4* hyd0 = nullptr;
+    float4* hyd1 = nullptr;
+    // active / iteration state (rank space)
+    int32_t* act = nullptr;        // active ranks (key order)
+    int32_t* act2 = nullptr;       // compaction target
+    int32_t* flag = nullptr;       // per-rank flags / scan input
+    int32_t* scan = nullptr;       // scan output
+    int32_t* scan_aux = nullptr;   // scan block sums
+    int64_t scan_aux_cap = 0;
+    double* lo = nullptr;          // bracket of the iteration
+    double* hi = nullptr;
+    float* acc_rho = nullptr;      // per-rank density sums of the current pass
+    float* acc_drho = nullptr;
+    int32_t* acc_n = nullptr;
+    int32_t* it_count = nullptr;
+    int64_t* cnt64 = nullptr;      // per-target pair counts (export)
+    // tree
+    Tree tree;
+    // counters and error flags
+    DevCounters* ctr = nullptr;
+    unsigned* err = nullptr;
+    int* work = nullptr;           // dynamic work counters for persistent kernels
+    int* host_small = nullptr;     // pinned host scratch
+    sphgrp_stats last{};
+};
+
+// error reporting (api.cu)
+int set_error(int code, const std::string& msg);
+int check_cuda(cudaError_t e, const char* what);
+
+// ---------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ float rel_coord(uint32_t X, float off, uint32_t C) {
+    return (__int2float_rn((int32_t)(X - C)) + off) * kUnitToBox;
+}
+
+// M4 cubic-spline shape w(q) (support q < 1) and its derivative dw/dq.
+// W(r,h) = 8/(pi h^3) w(r/h).
+__device__ __forceinline__ void m4_shape(float q, float& w, float& dw) {
+    float u = 1.0f - q;
+    float w_in = fmaf(q * q, 6.0f * q - 6.0f, 1.0f);
+    float dw_in = q * (18.0f * q - 12.0f);
+    float w_out = 2.0f * u * u * u;
+    float dw_out = -6.0f * u * u;
+    bool inner = q <= 0.5f;
+    w = inner ? w_in : w_out;
+    dw = inner ? dw_in : dw_out;
+    if (q >= 1.0f) { w = 0.0f; dw = 0.0f; }
+}
+
+// compensated (Kahan) accumulation
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+    float y = __fsub_rn(x, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// exact FP64 minimum-image squared distance of the oracle's definition (no FMA)
+__device__ __forceinline__ double exact_r2(const double* xd, const double* yd, const double* zd,
+                                           int i, int j) {
+    double dx = __dsub_rn(xd[j], xd[i]);
+    double dy = __dsub_rn(yd[j], yd[i]);
+    double dz = __dsub_rn(zd[j], zd[i]);
+    dx = __dsub_rn(dx, rint(dx));
+    dy = __dsub_rn(dy, rint(dy));
+    dz = __dsub_rn(dz, rint(dz));
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Relative half-width of the FP32 decision band: a pair whose FP32 r^2 lies within
+// kBandRel * (2|m| + H)^2 + kBandRel * H^2 of the threshold H^2 is re-decided in FP64.
+// (Bound: each FP32 relative coordinate carries at most one ulp of its magnitude,
+// the difference and the three-term sum add at most a few more; the total is below
+// 2^-20 (|p| + |m|)^2 with |p| <= |m| + r near the threshold.  2^-18 leaves a factor 4.)
+constexpr float kBandRel = 3.814697265625e-06f;  // 2^-18
+
+// launch helpers
+inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// kernels' host launchers (defined in the .cu files)
+int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s);              // sort.cu
+int exclusive_scan_i32(Ctx* c, const int32_t* in, int32_t* out, int64_t n,
+                       int32_t* total_dev, cudaStream_t s);                        // sort.cu
+int build_tree(Ctx* c, cudaStream_t s);                                            // tree.cu
+int refresh_hmax(Ctx* c, cudaStream_t s);                                          // tree.cu
+
+}  // namespace sphgrp

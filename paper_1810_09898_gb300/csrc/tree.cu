@@ -1,0 +1,267 @@
+// Gather into key order and the linear octree over the key-ordered particles
+// (Sec. 2.2: an octree divides the volume; particles follow the Hilbert curve, so
+// every octree cell is one contiguous range of the sorted order).
+#include <algorithm>
+
+#include "sph_internal.cuh"
+
+namespace sphgrp {
+
+// pos/m (original order) -> key-ordered FP64 copies and the fixed-point layout.
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ pos,
+                         const float* __restrict__ m, double* __restrict__ xd, double* __restrict__ yd,
+                         double* __restrict__ zd, uint4* __restrict__ pfix, float4* __restrict__ poff) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int i = perm[r];
+    double x = pos[3 * (int64_t)i], y = pos[3 * (int64_t)i + 1], z = pos[3 * (int64_t)i + 2];
+    // x * 2^32 is exact; its floor is the fixed-point coordinate, the remainder (exact in
+    // FP64, < 1) keeps the rest of the position and is rounded once to FP32.
+    double sx = x * kBoxToUnit, sy = y * kBoxToUnit, sz = z * kBoxToUnit;
+    double fx = floor(sx), fy = floor(sy), fz = floor(sz);
+    uint4 P;
+    P.x = (uint32_t)fx;
+    P.y = (uint32_t)fy;
+    P.z = (uint32_t)fz;
+    P.w = 0u;
+    pfix[r] = P;
+    poff[r] = make_float4((float)(sx - fx), (float)(sy - fy), (float)(sz - fz), m[i]);
+    xd[r] = x;
+    yd[r] = y;
+    zd[r] = z;
+}
+
+__device__ __forceinline__ int key_digit(uint64_t key, int shift) { return (int)((key >> shift) & 7u); }
+
+// first index in [lo, hi) whose digit is >= d (digits are non-decreasing in the range)
+__device__ __forceinline__ int lower_digit(const uint64_t* keys, int lo, int hi, int shift, int d) {
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (key_digit(keys[mid], shift) < d) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Number of non-empty octants of every node of one level that must split.
+__global__ void k_split_count(const uint64_t* __restrict__ keys, const int4* __restrict__ nlink,
+                              int a, int nf, int level, int leaf_size, int32_t* __restrict__ nchild) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    int4 L = nlink[a + k];
+    int cnt = 0;
+    if (L.y > leaf_size && level < kKeyLevels) {
+        int shift = 3 * (kKeyLevels - 1 - level);
+        int lo = L.x, hi = L.x + L.y;
+        int prev = lo;
+        for (int d = 1; d <= 8; ++d) {
+            int b = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
+            if (b > prev) ++cnt;
+            prev = b;
+        }
+    }
+    nchild[k] = cnt;
+}
+
+// Writes the children of every splitting node of one level.
+__global__ void k_split_write(const uint64_t* __restrict__ keys, int4* __restrict__ nlink,
+                              float4* __restrict__ next, int32_t* __restrict__ nlevel, int a,
+                              int nf, int level, const int32_t* __restrict__ nchild,
+                              const int32_t* __restrict__ coff, int b) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    int nc = nchild[k];
+    int4 L = nlink[a + k];
+    next[a + k].w = __int_as_float(nc);
+    if (nc == 0) return;
+    int shift = 3 * (kKeyLevels - 1 - level);
+    int child0 = b + coff[k];
+    int lo = L.x, hi = L.x + L.y;
+    int prev = lo, c = 0;
+    for (int d = 1; d <= 8; ++d) {
+        int e = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
+        if (e > prev) {
+            int id = child0 + c;
+            int skip = (c + 1 < nc) ? id + 1 : L.w;
+            nlink[id] = make_int4(prev, e - prev, -1, skip);
+            nlevel[id] = level + 1;
+            ++c;
+        }
+        prev = e;
+    }
+    L.z = child0;
+    nlink[a + k] = L;
+}
+
+// Tight boxes (fixed point) and hmax of one level, leaves from their particles,
+// internal nodes from their children.
+__global__ void k_box_level(int a, int nf, const int4* __restrict__ nlink, const float4* __restrict__ next,
+                            const uint4* __restrict__ pfix, uint4* __restrict__ blo, uint4* __restrict__ bhi,
+                            uint4* __restrict__ ncen) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    int id = a + k;
+    int4 L = nlink[id];
+    uint32_t lx = 0xffffffffu, ly = 0xffffffffu, lz = 0xffffffffu, hx = 0, hy = 0, hz = 0;
+    float hm = 0.0f;
+    if (L.z < 0) {
+        for (int q = L.x; q < L.x + L.y; ++q) {
+            uint4 P = pfix[q];
+            lx = min(lx, P.x); ly = min(ly, P.y); lz = min(lz, P.z);
+            hx = max(hx, P.x); hy = max(hy, P.y); hz = max(hz, P.z);
+            hm = fmaxf(hm, __uint_as_float(P.w));
+        }
+    } else {
+        int nc = __float_as_int(next[id].w);
+        for (int c = L.z; c < L.z + nc; ++c) {
+            uint4 l = blo[c], h = bhi[c];
+            lx = min(lx, l.x); ly = min(ly, l.y); lz = min(lz, l.z);
+            hx = max(hx, h.x); hy = max(hy, h.y); hz = max(hz, h.z);
+            hm = fmaxf(hm, __uint_as_float(ncen[c].w));
+        }
+    }
+    blo[id] = make_uint4(lx, ly, lz, 0u);
+    bhi[id] = make_uint4(hx, hy, hz, 0u);
+    ncen[id].w = __float_as_uint(hm);
+}
+
+// Box -> centre (fixed point) and padded half extents.  Particles of the node lie in
+// [lo, hi + 1) units; with the centre rounded down to a whole unit the half extent
+// (hi - lo + 2) / 2 covers that interval.  Extents are rounded up.
+__global__ void k_box_final(int64_t nn, const uint4* __restrict__ blo, const uint4* __restrict__ bhi,
+                            uint4* __restrict__ ncen, float4* __restrict__ next) {
+    int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (id >= nn) return;
+    uint4 l = blo[id], h = bhi[id];
+    uint4 C = ncen[id];
+    uint64_t wx = (uint64_t)h.x - l.x + 1, wy = (uint64_t)h.y - l.y + 1, wz = (uint64_t)h.z - l.z + 1;
+    C.x = l.x + (uint32_t)(wx >> 1);
+    C.y = l.y + (uint32_t)(wy >> 1);
+    C.z = l.z + (uint32_t)(wz >> 1);
+    ncen[id] = C;
+    float4 E = next[id];
+    E.x = __fmul_ru(__ull2float_ru(wx + 1), 0.5f);
+    E.y = __fmul_ru(__ull2float_ru(wy + 1), 0.5f);
+    E.z = __fmul_ru(__ull2float_ru(wz + 1), 0.5f);
+    next[id] = E;
+}
+
+// hmax only (after the smoothing lengths changed)
+__global__ void k_hmax_level(int a, int nf, const int4* __restrict__ nlink, const float4* __restrict__ next,
+                             const uint4* __restrict__ pfix, uint4* __restrict__ ncen) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    int id = a + k;
+    int4 L = nlink[id];
+    float hm = 0.0f;
+    if (L.z < 0) {
+        for (int q = L.x; q < L.x + L.y; ++q) hm = fmaxf(hm, __uint_as_float(pfix[q].w));
+    } else {
+        int nc = __float_as_int(next[id].w);
+        for (int c = L.z; c < L.z + nc; ++c) hm = fmaxf(hm, __uint_as_float(ncen[c].w));
+    }
+    ncen[id].w = __float_as_uint(hm);
+}
+
+static int grow_tree(Ctx* c, int64_t need, cudaStream_t s) {
+    Tree& t = c->tree;
+    if (need <= t.cap) return SPHGRP_OK;
+    int64_t cap = std::max<int64_t>(need + need / 2, 1024);
+    uint4* ncen;
+    float4* next;
+    int4* nlink;
+    int32_t* nlevel;
+    if (cudaMallocAsync(&ncen, cap * sizeof(uint4), s) != cudaSuccess ||
+        cudaMallocAsync(&next, cap * sizeof(float4), s) != cudaSuccess ||
+        cudaMallocAsync(&nlink, cap * sizeof(int4), s) != cudaSuccess ||
+        cudaMallocAsync(&nlevel, cap * sizeof(int32_t), s) != cudaSuccess)
+        return set_error(SPHGRP_ENOMEM, "octree allocation failed");
+    if (t.count > 0) {
+        cudaMemcpyAsync(ncen, t.ncen, t.count * sizeof(uint4), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(next, t.next, t.count * sizeof(float4), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nlink, t.nlink, t.count * sizeof(int4), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(nlevel, t.nlevel, t.count * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    }
+    if (t.ncen) {
+        cudaFreeAsync(t.ncen, s);
+        cudaFreeAsync(t.next, s);
+        cudaFreeAsync(t.nlink, s);
+        cudaFreeAsync(t.nlevel, s);
+    }
+    t.ncen = ncen;
+    t.next = next;
+    t.nlink = nlink;
+    t.nlevel = nlevel;
+    t.cap = cap;
+    return check_cuda(cudaGetLastError(), "octree allocation");
+}
+
+int build_tree(Ctx* c, cudaStream_t s) {
+    Tree& t = c->tree;
+    const int64_t n = c->n;
+    int rc = grow_tree(c, std::max<int64_t>(1024, 2 * n / std::max(1, c->p.leaf_size) + 64), s);
+    if (rc) return rc;
+    int4 root = make_int4(0, (int)n, -1, -1);
+    cudaMemcpyAsync(t.nlink, &root, sizeof(int4), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(t.nlevel, 0, sizeof(int32_t), s);
+    cudaMemsetAsync(t.next, 0, sizeof(float4), s);
+    t.level_begin[0] = 0;
+    t.level_begin[1] = 1;
+    t.count = 1;
+    int level = 0;
+    int32_t* total_dev = reinterpret_cast<int32_t*>(c->work) + 12;
+    for (level = 0; level <= kKeyLevels; ++level) {
+        int a = t.level_begin[level], b = t.level_begin[level + 1];
+        int nf = b - a;
+        if (nf == 0) break;
+        k_split_count<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, a, nf, level,
+                                                          c->p.leaf_size, c->flag);
+        rc = exclusive_scan_i32(c, c->flag, c->scan, nf, total_dev, s);
+        if (rc) return rc;
+        cudaMemcpyAsync(c->host_small, total_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "octree level"))) return rc;
+        int total = c->host_small[0];
+        if (b + (int64_t)total > t.cap) {
+            if ((rc = grow_tree(c, b + (int64_t)total, s))) return rc;
+        }
+        k_split_write<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, t.next, t.nlevel, a, nf,
+                                                          level, c->flag, c->scan, b);
+        t.level_begin[level + 2] = b + total;
+        t.count = b + total;
+        if (total == 0) { ++level; break; }
+    }
+    t.nlevels = level;
+    // boxes bottom-up (scratch for lo/hi boxes: the radix-sort key buffers, >= 16 B/node?)
+    uint4* blo;
+    uint4* bhi;
+    if (cudaMallocAsync(&blo, t.count * sizeof(uint4), s) != cudaSuccess ||
+        cudaMallocAsync(&bhi, t.count * sizeof(uint4), s) != cudaSuccess)
+        return set_error(SPHGRP_ENOMEM, "octree box scratch");
+    for (int lv = t.nlevels - 1; lv >= 0; --lv) {
+        int a = t.level_begin[lv], nf = t.level_begin[lv + 1] - a;
+        if (nf > 0)
+            k_box_level<<<blocks_for(nf, 128), 128, 0, s>>>(a, nf, t.nlink, t.next, c->pfix, blo, bhi, t.ncen);
+    }
+    k_box_final<<<blocks_for(t.count, 256), 256, 0, s>>>(t.count, blo, bhi, t.ncen, t.next);
+    cudaFreeAsync(blo, s);
+    cudaFreeAsync(bhi, s);
+    return check_cuda(cudaGetLastError(), "octree build");
+}
+
+int refresh_hmax(Ctx* c, cudaStream_t s) {
+    Tree& t = c->tree;
+    for (int lv = t.nlevels - 1; lv >= 0; --lv) {
+        int a = t.level_begin[lv], nf = t.level_begin[lv + 1] - a;
+        if (nf > 0)
+            k_hmax_level<<<blocks_for(nf, 128), 128, 0, s>>>(a, nf, t.nlink, t.next, c->pfix, t.ncen);
+    }
+    return check_cuda(cudaGetLastError(), "hmax refresh");
+}
+
+int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s) {
+    k_gather<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, pos, m, c->xd, c->yd, c->zd,
+                                                  c->pfix, c->poff);
+    return check_cuda(cudaGetLastError(), "gather");
+}
+
+}  // namespace sphgrp

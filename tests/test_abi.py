@@ -1,0 +1,66 @@
+"""CPU checks of the boundary: the library builds, loads, and exports every entry
+point declared in include/*.h; the product package never loads the oracle."""
+
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(sphgrp_\w+)\s*\(", text, flags=re.M))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1810_09898_gb300.build import build
+
+    return build()
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for must in ("sphgrp_sfc_keys_sort", "sphgrp_tree_build", "sphgrp_ngb_search", "sphgrp_density",
+                 "sphgrp_hydro_force"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    from paper_1810_09898_gb300 import binding
+
+    assert set(binding.EXPORTED) <= set(_declared())
+
+
+def test_library_does_not_link_the_oracle(lib_path):
+    out = subprocess.run(["ldd", lib_path], capture_output=True, text=True).stdout
+    assert "sphoracle" not in out
+    for f in glob.glob(os.path.join(ROOT, "paper_1810_09898_gb300", "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            text = open(f).read()
+            assert "import oracle" not in text and "sph_oracle" not in text, f
+
+
+def test_default_params_and_error_text(lib_path):
+    from paper_1810_09898_gb300 import binding
+
+    p = binding.default_params()
+    assert p.nngb == 64.0 and p.nngb_tol == 2.0 and p.leaf_size == 16
+    lib = binding.load_library()
+    # no device needed: argument checks fail before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.sphgrp_ctx_create(None, None, 10) == -1
+    assert lib.sphgrp_ctx_create(ctypes.byref(h), None, 0) == -1
+    assert b"n_max" in lib.sphgrp_last_error()
