@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Benchmark of the SPH hot path on one GB300: density (with the smoothing-length
+iteration) + hydro forces, grouped neighbour search (Neighbour Recycling) against the
+per-particle search, in active particles per second.
+
+One step = the whole hot path on one particle set: Peano-Hilbert keys and radix sort,
+octree build, density with the h iteration, hydro forces -- every stage a kernel of
+libsphgrp.so, called through its C ABI.
+
+Workload (default): 2^24 particles, half uniform and half in 256 Plummer spheres (seeded
+synthetic stand-in for a cosmological box), velocities N(0, 0.1^2), u log-normal,
+N_ngb = 64 +- 2, all particles active.  The step's initial smoothing lengths are the
+converged ones of a set-up pass scattered by a seeded log-normal factor (5%), the
+change of h over one timestep, so that every step re-converges h (a few passes).
+
+Output: one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead
+(the only reference implementation of this method), on a bounded sample.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SPH density+hydro active particles/s: grouped vs per-particle search, 1 GB300"
+UNIT = "active particles/s"
+
+# algorithmic bytes per unit (candidate, member, node) of the two search kernels
+B_CAND = {"density": 32, "hydro": 64}
+B_MEMBER = {"density": 32 + 16, "hydro": 64 + 16}
+B_NODE = 48
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--active", type=float, default=1.0)
+    ap.add_argument("--group", type=int, default=16)
+    ap.add_argument("--h-scatter", type=float, default=0.05)
+    ap.add_argument("--cpu-n", type=int, default=1 << 19, help="oracle sample size")
+    ap.add_argument("--no-individual", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"clustered N={a.n} (half uniform, half in 256 Plummer spheres), density+hydro, "
+            f"{a.active:.0%} active, Nngb=64+-2")
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+class CpuSample:
+    """The FP64 oracle on a smaller set of the same recipe (all active).  Set-up
+    (untimed): cold smoothing-length iteration.  One timed run: keys, order, density
+    with the h iteration from the scattered h, hydro."""
+
+    def __init__(self, n: int, h_scatter: float, seed_salt: int = 0):
+        import oracle
+        import sphgen
+
+        self.oracle = oracle
+        self.n = n
+        self.h_scatter = h_scatter
+        d = sphgen.make("clustered", n, config=3, seed_salt=seed_salt)
+        self.pos = d["pos"]
+        self.m = d["m"].astype(np.float32).astype(np.float64)
+        self.vel = d["vel"].astype(np.float32).astype(np.float64)
+        self.u = d["u"].astype(np.float32).astype(np.float64)
+        hc, _ = oracle.density_iterate(self.pos, self.m, np.full(n, d["h0"]))
+        rng = np.random.default_rng(77 + seed_salt)
+        self.h0 = hc * np.exp(h_scatter * rng.standard_normal(n))
+
+    def run(self) -> float:
+        o = self.oracle
+        t0 = time.perf_counter()
+        keys = o.hilbert_keys(self.pos)
+        o.stable_order(keys)
+        h, dens = o.density_iterate(self.pos, self.m, self.h0)
+        o.hydro(self.pos, self.vel, self.m, h, dens["rho"], dens["f"], self.u)
+        return time.perf_counter() - t0
+
+    def describe(self, seconds: float, value: float) -> dict:
+        return {"value": value, "unit": UNIT, "cores": self.oracle.threads(), "kind": "oracle",
+                "sample": f"clustered N={self.n} of the same recipe, all active: keys, order, density "
+                          f"with h iteration from {self.h_scatter:.0%}-scattered h, hydro "
+                          f"({seconds:.1f} s per run)"}
+
+
+def cpu_sample(n: int, h_scatter: float) -> dict:
+    S = CpuSample(n, h_scatter)
+    t = S.run()
+    return S.describe(t, n / t)
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    S = CpuSample(a.cpu_n, a.h_scatter)
+    for _ in range(max(0, min(a.warmup, 1))):
+        S.run()
+    ts = [S.run() for _ in range(a.steps)]
+    t = float(np.mean(ts))
+    v = a.cpu_n / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "oracle_sample_n": a.cpu_n},
+            "cpu_baseline": S.describe(t, v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict | None:
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+class Problem:
+    def __init__(self, a, rank: int):
+        import torch
+
+        import paper_1810_09898_gb300 as sg
+        import sphgen
+
+        self.torch, self.sg, self.a = torch, sg, a
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.dev = dev
+        n = a.n
+        d = sphgen.make("clustered", n, config=3, seed_salt=rank)
+        self.n = n
+        self.host = {
+            "pos": torch.from_numpy(d["pos"]).pin_memory(),
+            "m": torch.from_numpy(d["m"].astype(np.float32)).pin_memory(),
+            "vel": torch.from_numpy(d["vel"].astype(np.float32)).pin_memory(),
+            "u": torch.from_numpy(d["u"].astype(np.float32)).pin_memory(),
+        }
+        self.pos = self.host["pos"].to(dev)
+        self.m = self.host["m"].to(dev)
+        self.vel = self.host["vel"].to(dev)
+        self.u = self.host["u"].to(dev)
+        self.ctx = sg.Context(n)
+        self.perm = torch.empty(n, dtype=torch.int32, device=dev)
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.rho = torch.zeros(n, **f32)
+        self.drho = torch.zeros(n, **f32)
+        self.f = torch.zeros(n, **f32)
+        self.nn = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.nnh = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.acc = torch.zeros((n, 3), **f32)
+        self.dudt = torch.zeros(n, **f32)
+        self.h = torch.empty(n, dtype=torch.float64, device=dev)
+        # set-up: order, tree, converged h from the uniform-density guess (cold start)
+        self.ctx.sfc_keys_sort(self.pos, None, self.perm)
+        self.ctx.tree_build(self.pos, self.m)
+        all_act = torch.arange(n, dtype=torch.int32, device=dev)
+        self.h.fill_(d["h0"])
+        t0 = time.perf_counter()
+        self.ctx.density(all_act, self.h, 1, sg.GROUPED, 16, self.rho, self.drho, self.f, self.nn)
+        torch.cuda.synchronize()
+        self.cold_s = time.perf_counter() - t0
+        self.cold_stats = self.ctx.stats()
+        # active set: runs along the key order (all particles at 100%)
+        if a.active >= 1.0:
+            act = np.arange(n, dtype=np.int32)
+        else:
+            mask = sphgen.active_rank_mask(n, a.active, 32.0, np.random.default_rng(1000 + rank))
+            act = np.sort(self.perm.cpu().numpy()[np.flatnonzero(mask)]).astype(np.int32)
+        self.n_act = len(act)
+        self.act = torch.from_numpy(act).to(dev)
+        self.host["act"] = torch.from_numpy(act).pin_memory()
+        rng = np.random.default_rng(77 + rank)
+        hc = self.h.cpu().numpy()
+        hi = hc.copy()
+        hi[act] = hc[act] * np.exp(a.h_scatter * rng.standard_normal(len(act)))
+        self.h_init = torch.from_numpy(hi).to(dev)
+        self.host["h_init"] = torch.from_numpy(hi).pin_memory()
+        self.out_host = {
+            "acc": torch.empty((n, 3), dtype=torch.float32).pin_memory(),
+            "dudt": torch.empty(n, dtype=torch.float32).pin_memory(),
+            "rho": torch.empty(n, dtype=torch.float32).pin_memory(),
+            "h": torch.empty(n, dtype=torch.float64).pin_memory(),
+        }
+
+    def step(self, mode: int, g: int, collect: list | None = None):
+        c = self.ctx
+        c.sfc_keys_sort(self.pos, None, self.perm)
+        c.tree_build(self.pos, self.m)
+        self.h.copy_(self.h_init)
+        c.density(self.act, self.h, 1, mode, g, self.rho, self.drho, self.f, self.nn)
+        sd = c.stats() if collect is not None else None
+        c.hydro_force(self.act, self.h, self.rho, self.f, self.vel, self.u, mode, g, self.acc, self.dudt,
+                      self.nnh)
+        if collect is not None:
+            collect.append({"density": sd, "hydro": c.stats()})
+
+    def step_e2e(self, g: int):
+        """The same step from host buffers: inputs copied in, results copied out."""
+        H = self.host
+        self.pos.copy_(H["pos"], non_blocking=True)
+        self.m.copy_(H["m"], non_blocking=True)
+        self.vel.copy_(H["vel"], non_blocking=True)
+        self.u.copy_(H["u"], non_blocking=True)
+        self.act.copy_(H["act"], non_blocking=True)
+        self.h_init.copy_(H["h_init"], non_blocking=True)
+        self.step(self.sg.GROUPED, g)
+        O = self.out_host
+        O["acc"].copy_(self.acc, non_blocking=True)
+        O["dudt"].copy_(self.dudt, non_blocking=True)
+        O["rho"].copy_(self.rho, non_blocking=True)
+        O["h"].copy_(self.h, non_blocking=True)
+        self.torch.cuda.current_stream().synchronize()
+
+    def io_bytes(self):
+        n = self.n
+        h2d = n * (24 + 4 + 12 + 4 + 8) + 4 * self.n_act
+        d2h = n * (12 + 4 + 4 + 8)
+        return h2d, d2h
+
+
+def timed(P, fn, steps, warmup, dist):
+    torch = P.torch
+    for _ in range(warmup):
+        fn(None)
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    collect = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = P.sg.kernel_launches()
+    ev0.record(stream)
+    for _ in range(steps):
+        fn(collect)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = P.sg.kernel_launches() - l0
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=P.dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, collect, launches
+
+
+def roofline(collect, peak_gbs):
+    """Dominant search kernel: algorithmic bytes per launch / event time per launch."""
+    agg = {}
+    for rec in collect:
+        for k in ("density", "hydro"):
+            s = rec[k]
+            A = agg.setdefault(k, {"ms": 0.0, "launches": 0, "bytes": 0.0, "cand": 0, "tests": 0, "pairs": 0,
+                                   "members": 0, "walks": 0, "nodes": 0})
+            A["ms"] += s["search_ms"]
+            A["launches"] += s["search_launches"]
+            A["bytes"] += s["candidates"] * B_CAND[k] + s["members"] * B_MEMBER[k] + s["nodes_tested"] * B_NODE
+            A["cand"] += s["candidates"]
+            A["tests"] += s["pair_tests"]
+            A["pairs"] += s["pairs"]
+            A["members"] += s["members"]
+            A["walks"] += s["walks"]
+            A["nodes"] += s["nodes_tested"]
+    dom = max(agg, key=lambda k: agg[k]["ms"])
+    A = agg[dom]
+    per_launch_bytes = A["bytes"] / max(1, A["launches"])
+    per_launch_s = A["ms"] / max(1, A["launches"]) / 1e3
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    detail = {k: {"ms_per_step": v["ms"] / max(1, len(collect)), "launches_per_step": v["launches"] / max(1, len(collect)),
+                  "candidates_per_member": v["cand"] / max(1, v["members"]),
+                  "pair_tests_per_member": v["tests"] / max(1, v["members"]),
+                  "pairs_per_member": v["pairs"] / max(1, v["members"]),
+                  "members_per_walk": v["members"] / max(1, v["walks"]),
+                  "nodes_per_walk": v["nodes"] / max(1, v["walks"])} for k, v in agg.items()}
+    return {"bound": "hbm", "kernel": f"k_group ({dom})", "achieved": achieved, "peak": peak_gbs,
+            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None,
+            "bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}, detail
+
+
+def measured_peak_hbm() -> float:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def run_ours(a):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    P = Problem(a, rank)
+    sg = P.sg
+    g = a.group
+    steps, warmup = a.steps, max(3, a.warmup)
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms_g, col_g, launches = timed(P, lambda c: P.step(sg.GROUPED, g, c), steps, warmup, dist)
+    clocks = clk.summary()
+    ms_i = None
+    col_i = []
+    if not a.no_individual:
+        ms_i, col_i, _ = timed(P, lambda c: P.step(sg.INDIVIDUAL, 1, c), steps, warmup, dist)
+    e2e = None
+    if not a.no_e2e:
+        for _ in range(2):
+            P.step_e2e(g)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            P.step_e2e(g)
+        t_e2e = (time.perf_counter() - t0) / steps
+        if dist:
+            tt = torch.tensor([t_e2e], device=P.dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        h2d, d2h = P.io_bytes()
+        e2e = {"value": world * P.n_act / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e}
+    peak = measured_peak_hbm()
+    roof, detail = roofline(col_g, peak)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_sample(a.cpu_n, a.h_scatter)
+        cpu.pop("seconds", None)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    ms_step = ms_g / steps
+    value = world * P.n_act / (ms_step / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n": P.n, "n_active": P.n_act, "group_size": g,
+                   "form": "grouped", "positions": "f64 (fixed-point + f32 offsets on device)",
+                   "h_init": f"converged h x exp({a.h_scatter} N(0,1)) per step",
+                   "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "individual": None if ms_i is None else {
+            "value": world * P.n_act / (ms_i / steps / 1e3), "ms_per_step": ms_i / steps,
+            "speedup_grouped": (ms_i / steps) / ms_step},
+        "roofline": roof,
+        "search_detail": detail,
+        "cold_start": {"seconds": P.cold_s, "iterations": P.cold_stats["iterations"]},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if ms_i is not None:
+        _, di = roofline(col_i, peak)
+        line["individual"]["search_detail"] = di
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -73,7 +73,17 @@ typedef struct sphgrp_params {
     double alpha;     /* Monaghan viscosity alpha, e.g. 1 */
     double beta;      /* Monaghan viscosity beta, e.g. 2 */
     double eps;       /* viscosity softening (mu denominator r^2 + eps hbar^2), e.g. 0.01 */
+    int group_centre; /* centre of a group's search sphere: SPHGRP_CENTRE_FIRST (the group's
+                         first particle, Sec. 3.1) or SPHGRP_CENTRE_BOX (the centre of the
+                         members' bounding box; same superset guarantee, smaller radius) */
+    double group_split; /* a group is cut in halves (recursively) while its search sphere
+                           (sqrt(3)/2 * width of the members' box + smallest h)^3 exceeds
+                           group_split * members * (smallest h)^3, i.e. while every member
+                           would filter more than group_split times its own sphere; <= 0
+                           keeps plain chunks of group_size.  e.g. 2 */
 } sphgrp_params;
+
+enum { SPHGRP_CENTRE_FIRST = 0, SPHGRP_CENTRE_BOX = 1 };
 
 /* Fills p with the defaults quoted above. */
 void sphgrp_default_params(sphgrp_params* p);
@@ -87,6 +97,9 @@ typedef struct sphgrp_stats {
     int64_t fp64_retests;   /* pairs re-decided from FP64 positions (within the FP32 error band) */
     int64_t iterations;     /* smoothing-length passes made by the last density call */
     int64_t max_stack;      /* deepest walk stack seen */
+    int64_t members;        /* particles processed by the search kernels (summed over passes) */
+    int64_t search_launches; /* search-kernel launches timed in the last call */
+    double search_ms;       /* their summed device time (CUDA events on the call's stream) */
 } sphgrp_stats;
 
 typedef struct sphgrp_ctx sphgrp_ctx;
@@ -138,15 +151,21 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
                       int32_t* idx, int64_t* n_pairs, cudaStream_t stream);
 
 /* The candidate superset of every group of the grouped form (Sec. 3.1), for
- * inspection.  Groups are group_size consecutive active particles in key order.
- * group_offsets: device, n_groups + 1 int64 over cand (n_groups = ceil(n_act/group_size));
- * members:       device, n_act int32: the active original indices in group order;
+ * inspection.  Groups are runs of consecutive active particles in key order: chunks
+ * of group_size, each cut in halves while its members are spread wider than
+ * params.group_split times their smallest h.
+ * group_offsets: device, n_act + 1 int64 offsets of every group's candidates in cand;
+ * group_first:   device, n_act + 1 int32 (may be NULL): group k's members are
+ *                members[group_first[k] .. group_first[k+1]);
+ * members:       device, n_act int32 (may be NULL): the active original indices in
+ *                key order;
  * cand:          device, cap int32 original indices, or NULL to count only;
- * n_cand:        host, total candidates.  kind selects the density or hydro radius. */
+ * n_groups, n_cand: host, number of groups (walks) and total candidates.
+ * kind selects the density or hydro radius. */
 int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
                            const double* h, int kind, int group_size, int64_t cap,
-                           int64_t* group_offsets, int32_t* members, int32_t* cand,
-                           int64_t* n_cand, cudaStream_t stream);
+                           int64_t* group_offsets, int32_t* group_first, int32_t* members,
+                           int32_t* cand, int64_t* n_groups, int64_t* n_cand, cudaStream_t stream);
 
 /* a6 + a7: SPH density of the active particles,
  *   rho_i = sum_{j in N_i} m_j W(r_ij, h_i),   dRho_i/dh_i,
@@ -180,6 +199,18 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
 
 /* Counters of the most recent search, density or hydro call. */
 int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out);
+
+/* Per-launch record of the search kernels of the most recent call, in launch order
+ * (one entry per smoothing-length pass for sphgrp_density): particles processed,
+ * candidates staged, member x candidate tests, node tests and device time in ms
+ * (CUDA events).  All arrays are host arrays of cap entries and may be NULL;
+ * count receives the number of entries written.  No device work. */
+int sphgrp_get_launch_log(sphgrp_ctx* ctx, int cap, int64_t* members, int64_t* candidates,
+                          int64_t* pair_tests, int64_t* nodes, double* ms, int* count);
+
+/* Number of CUDA kernels the library has launched in this process so far (all
+ * contexts, all threads).  Diagnostics only; no device work. */
+int sphgrp_kernel_launches(int64_t* count);
 
 #ifdef __cplusplus
 }

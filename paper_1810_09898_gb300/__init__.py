@@ -7,12 +7,15 @@ calls raise.
 """
 
 from .binding import (  # noqa: F401
+    CENTRE_BOX,
+    CENTRE_FIRST,
     DENSITY,
     GROUPED,
     HYDRO,
     INDIVIDUAL,
     SphgrpError,
     Context,
+    kernel_launches,
     library_path,
     load_library,
 )

@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(HERE, "_build", "libsphgrp.so")
 
 INDIVIDUAL, GROUPED = 0, 1
+CENTRE_FIRST, CENTRE_BOX = 0, 1
 DENSITY, HYDRO = 0, 1
 
 EXPORTED = [
@@ -28,6 +29,8 @@ EXPORTED = [
     "sphgrp_density",
     "sphgrp_hydro_force",
     "sphgrp_get_stats",
+    "sphgrp_kernel_launches",
+    "sphgrp_get_launch_log",
 ]
 
 _ERRORS = {
@@ -57,16 +60,18 @@ class Params(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("beta", ctypes.c_double),
         ("eps", ctypes.c_double),
+        ("group_centre", ctypes.c_int),
+        ("group_split", ctypes.c_double),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "walks", "nodes_tested", "candidates", "pair_tests", "pairs", "fp64_retests",
-        "iterations", "max_stack")]
+        "iterations", "max_stack", "members", "search_launches")] + [("search_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 _lib = None
@@ -94,11 +99,13 @@ def load_library():
     L.sphgrp_tree_build.argtypes = [P, I64, P, P, P]
     L.sphgrp_ngb_search.argtypes = [P, I64, P, P, I32, I32, I32, I64, P, P,
                                     ctypes.POINTER(I64), P]
-    L.sphgrp_group_supersets.argtypes = [P, I64, P, P, I32, I32, I64, P, P, P,
-                                         ctypes.POINTER(I64), P]
+    L.sphgrp_group_supersets.argtypes = [P, I64, P, P, I32, I32, I64, P, P, P, P,
+                                         ctypes.POINTER(I64), ctypes.POINTER(I64), P]
     L.sphgrp_density.argtypes = [P, I64, P, P, I32, I32, I32, P, P, P, P, P, P]
     L.sphgrp_hydro_force.argtypes = [P, I64, P, P, P, P, P, P, I32, I32, P, P, P, P]
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    L.sphgrp_kernel_launches.argtypes = [ctypes.POINTER(I64)]
+    L.sphgrp_get_launch_log.argtypes = [P, I32, P, P, P, P, P, ctypes.POINTER(I32)]
     for name in EXPORTED:
         if name not in ("sphgrp_default_params", "sphgrp_last_error"):
             getattr(L, name).restype = I32
@@ -121,6 +128,13 @@ def _stream():
 def _check(rc: int):
     if rc != 0:
         raise SphgrpError(rc, load_library().sphgrp_last_error().decode())
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    n = ctypes.c_int64()
+    _check(load_library().sphgrp_kernel_launches(ctypes.byref(n)))
+    return int(n.value)
 
 
 def default_params(**over) -> Params:
@@ -173,13 +187,16 @@ class Context:
                                          ctypes.byref(n_pairs), _stream()))
         return int(n_pairs.value)
 
-    def group_supersets(self, active, h, kind, group_size, group_offsets, members=None, cand=None,
-                        cap=0) -> int:
+    def group_supersets(self, active, h, kind, group_size, group_offsets, group_first=None, members=None,
+                        cand=None, cap=0):
+        """Returns (n_groups, n_candidates)."""
+        ng = ctypes.c_int64()
         n = ctypes.c_int64()
         _check(self._L.sphgrp_group_supersets(self._h, active.shape[0], _ptr(active), _ptr(h), kind,
-                                              group_size, int(cap), _ptr(group_offsets), _ptr(members),
-                                              _ptr(cand), ctypes.byref(n), _stream()))
-        return int(n.value)
+                                              group_size, int(cap), _ptr(group_offsets), _ptr(group_first),
+                                              _ptr(members), _ptr(cand), ctypes.byref(ng), ctypes.byref(n),
+                                              _stream()))
+        return int(ng.value), int(n.value)
 
     # -- a6 + a7
     def density(self, active, h, iterate, mode, group_size, rho, drhodh, fgrad, nngb, iters=None):
@@ -192,6 +209,19 @@ class Context:
         _check(self._L.sphgrp_hydro_force(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
                                           _ptr(fgrad), _ptr(vel), _ptr(u), mode, group_size, _ptr(acc),
                                           _ptr(dudt), _ptr(nngb), _stream()))
+
+    def launch_log(self) -> list:
+        import numpy as np
+
+        cap = 128
+        arrs = [np.zeros(cap, np.int64) for _ in range(4)]
+        ms = np.zeros(cap, np.float64)
+        cnt = ctypes.c_int()
+        _check(self._L.sphgrp_get_launch_log(self._h, cap, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs],
+                                             ms.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
+        k = cnt.value
+        return [{"members": int(arrs[0][i]), "candidates": int(arrs[1][i]), "pair_tests": int(arrs[2][i]),
+                 "nodes": int(arrs[3][i]), "ms": float(ms[i])} for i in range(k)]
 
     def stats(self) -> dict:
         s = Stats()

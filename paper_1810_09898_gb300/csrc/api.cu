@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/sphgrp.h): context, argument checks and
 // the orchestration of the kernels of sort.cu, tree.cu and ngb.cu.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -11,6 +12,22 @@ namespace sphgrp {
 
 
 static thread_local std::string g_last_error = "no error";
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void timer_begin(Ctx* c, cudaStream_t s) {
+    if (c->ntimed < Ctx::kMaxTimed) cudaEventRecord(c->tev[2 * c->ntimed], s);
+}
+
+void timer_end(Ctx* c, cudaStream_t s, int64_t members) {
+    if (c->ntimed < Ctx::kMaxTimed) {
+        cudaEventRecord(c->tev[2 * c->ntimed + 1], s);
+        cudaMemcpyAsync(c->ctr_log + c->ntimed, c->ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, s);
+        c->log_members[c->ntimed] = members;
+        c->ntimed++;
+    }
+}
 
 int set_error(int code, const std::string& msg) {
     g_last_error = msg;
@@ -108,6 +125,12 @@ __global__ void k_offsets_by_orig(int64_t n_act, const int32_t* __restrict__ act
     if (k < n_act) out[active[k]] = off[k];
 }
 
+__global__ void k_group_first(int ng, int nu, int g, const int2* __restrict__ groups, int32_t* __restrict__ out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ng) out[k] = groups ? groups[k].x : k * g;
+    else if (k == ng) out[k] = nu;
+}
+
 __global__ void k_members(int nu, const int32_t* __restrict__ U, const int32_t* __restrict__ perm,
                           int32_t* __restrict__ out) {
     int u = blockIdx.x * blockDim.x + threadIdx.x;
@@ -135,6 +158,16 @@ int finish(Ctx* c, cudaStream_t s, int rc) {
     c->last.pairs = (int64_t)dc.pairs;
     c->last.fp64_retests = (int64_t)dc.retests;
     c->last.max_stack = (int64_t)dc.max_stack;
+    double ms = 0.0;
+    for (int k = 0; k < c->ntimed; ++k) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, c->tev[2 * k], c->tev[2 * k + 1]) == cudaSuccess) ms += t;
+        c->log_ms[k] = t;
+    }
+    if (c->ntimed > 0)
+        cudaMemcpy(c->ctr_log_host, c->ctr_log, c->ntimed * sizeof(DevCounters), cudaMemcpyDeviceToHost);
+    c->last.search_ms = ms;
+    c->last.search_launches = c->ntimed;
     if (err & kErrRange) return set_error(SPHGRP_EINVAL, "a position is outside [0,1) or not finite");
     if (err & kErrH) return set_error(SPHGRP_EINVAL, "a smoothing length is outside (0, 0.5)");
     if (err & 32u) return set_error(SPHGRP_EINVAL, "an active index is outside [0, n)");
@@ -148,6 +181,7 @@ void reset_flags(Ctx* c, cudaStream_t s) {
     cudaMemsetAsync(c->err, 0, sizeof(unsigned), s);
     cudaMemsetAsync(c->ctr, 0, sizeof(DevCounters), s);
     std::memset(&c->last, 0, sizeof(c->last));
+    c->ntimed = 0;
 }
 
 // active original indices -> key-ordered ranks in c->act; returns the count
@@ -155,14 +189,36 @@ int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s,
     const int64_t n = c->n;
     cudaMemsetAsync(c->flag, 0, n * sizeof(int32_t), s);
     k_mark_active<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, n, c->rank_of, c->flag, c->err);
+    note_launch();
     int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
     int rc = exclusive_scan_i32(c, c->flag, c->scan, n, total, s);
     if (rc) return rc;
     k_compact_ranks<<<blocks_for(n, 256), 256, 0, s>>>(n, c->flag, c->scan, c->act);
+    note_launch();
     cudaMemcpyAsync(c->host_small, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     rc = check_cuda(cudaStreamSynchronize(s), "active list");
     if (rc) return rc;
     *nu = c->host_small[0];
+    return SPHGRP_OK;
+}
+
+// Groups of the grouped form over the work list U (see k_split_groups); fills
+// a->groups and a->ngroups.  Reads the group count back (stream sync).
+int make_groups(Ctx* c, SearchArgs* a, const int32_t* U, int nu, int g, cudaStream_t s) {
+    a->groups = nullptr;
+    a->ngroups = (nu + g - 1) / g;
+    if (nu <= 0 || g <= 1 || !(c->p.group_split > 0.0)) return SPHGRP_OK;
+    int nch = (nu + g - 1) / g;
+    int rc = launch_split_groups(U, nu, g, (float)c->p.group_split, c->pfix, c->h64, c->groups_tmp,
+                                 c->grp_cnt, s);
+    if (rc) return rc;
+    int32_t* total = reinterpret_cast<int32_t*>(c->work) + 16;
+    if ((rc = exclusive_scan_i32(c, c->grp_cnt, c->grp_off, nch, total, s))) return rc;
+    if ((rc = launch_gather_groups(nch, g, c->groups_tmp, c->grp_cnt, c->grp_off, c->groups, s))) return rc;
+    cudaMemcpyAsync(c->host_small + 40, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "group count"))) return rc;
+    a->groups = c->groups;
+    a->ngroups = c->host_small[40];
     return SPHGRP_OK;
 }
 
@@ -187,6 +243,7 @@ SearchArgs base_args(Ctx* c) {
     a.ctr = c->ctr;
     a.err = c->err;
     a.work = c->work;
+    a.centre_box = c->p.group_centre == SPHGRP_CENTRE_BOX;
     return a;
 }
 
@@ -215,9 +272,17 @@ void sphgrp_default_params(sphgrp_params* p) {
     p->alpha = 1.0;
     p->beta = 2.0;
     p->eps = 0.01;
+    p->group_centre = SPHGRP_CENTRE_BOX;
+    p->group_split = 2.0;
 }
 
 const char* sphgrp_last_error(void) { return g_last_error.c_str(); }
+
+int sphgrp_kernel_launches(int64_t* count) {
+    if (!count) return set_error(SPHGRP_EINVAL, "null count");
+    *count = (int64_t)g_launches.load();
+    return SPHGRP_OK;
+}
 
 int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     if (!out) return set_error(SPHGRP_EINVAL, "null output pointer");
@@ -227,7 +292,7 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     if (p) c->p = *p;
     else sphgrp_default_params(&c->p);
     if (c->p.leaf_size < 1 || c->p.leaf_size > 1024 || !(c->p.nngb > 0) || !(c->p.nngb_tol >= 0) ||
-        c->p.max_iter < 1) {
+        c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX)) {
         delete c;
         return set_error(SPHGRP_EINVAL, "bad parameters");
     }
@@ -264,10 +329,19 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     rc |= dalloc(&c->acc_drho, n);
     rc |= dalloc(&c->acc_n, n);
     rc |= dalloc(&c->cnt64, n + 1);
+    rc |= dalloc(&c->groups, n + 1);
+    rc |= dalloc(&c->groups_tmp, n + 1);
+    rc |= dalloc(&c->grp_cnt, n + 1);
+    rc |= dalloc(&c->grp_off, n + 1);
     rc |= dalloc(&c->ctr, 1);
     rc |= dalloc(&c->err, 1);
     rc |= dalloc(&c->work, 64);
+    rc |= dalloc(&c->ctr_log, Ctx::kMaxTimed);
+    if (rc == 0 && cudaMallocHost(&c->ctr_log_host, Ctx::kMaxTimed * sizeof(DevCounters)) != cudaSuccess)
+        rc = SPHGRP_ENOMEM;
     if (rc == 0 && cudaMallocHost(&c->host_small, 64 * sizeof(int)) != cudaSuccess) rc = SPHGRP_ENOMEM;
+    for (int k = 0; rc == 0 && k < 2 * Ctx::kMaxTimed; ++k)
+        if (cudaEventCreate(&c->tev[k]) != cudaSuccess) rc = SPHGRP_ECUDA;
     if (rc) {
         sphgrp_ctx_destroy(reinterpret_cast<sphgrp_ctx*>(c));
         return set_error(SPHGRP_ENOMEM, "device allocation failed for n_max = " + std::to_string(n_max));
@@ -282,11 +356,15 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
     void* ptrs[] = {c->keys, c->keys_alt, c->perm, c->perm_alt, c->rank_of, c->hist, c->xd, c->yd,
                     c->zd, c->pfix, c->poff, c->h64, c->hyd0, c->hyd1, c->act, c->act2, c->flag,
                     c->scan, c->scan_aux, c->lo, c->hi, c->acc_rho, c->acc_drho, c->acc_n,
-                    c->cnt64, c->ctr, c->err, c->work, c->tree.ncen, c->tree.next, c->tree.nlink,
+                    c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
+                    c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
                     c->tree.nlevel};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_small) cudaFreeHost(c->host_small);
+    if (c->ctr_log_host) cudaFreeHost(c->ctr_log_host);
+    for (int k = 0; k < 2 * Ctx::kMaxTimed; ++k)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
     delete c;
     return SPHGRP_OK;
 }
@@ -333,6 +411,7 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
     if (!h || !offsets || !n_pairs) return set_error(SPHGRP_EINVAL, "null h, offsets or n_pairs");
     reset_flags(c, s);
     k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    note_launch();
     if (kind == SPHGRP_HYDRO) {
         cudaMemsetAsync(c->hyd0, 0, c->n * sizeof(float4), s);
         cudaMemsetAsync(c->hyd1, 0, c->n * sizeof(float4), s);
@@ -346,12 +425,17 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
     a.nu = nu;
     a.g = grouped ? group_size : 1;
     a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
+    if (grouped && (rc = make_groups(c, &a, c->act, nu, group_size, s))) return rc;
     a.x_cnt = c->cnt64;
     a.x_off = c->cnt64;
     a.x_cap = cap;
     cudaMemsetAsync(c->cnt64, 0, c->n * sizeof(int64_t), s);
-    if ((rc = launch_search(a, kind, kCount, grouped, c->sm_count, s))) return rc;
+    timer_begin(c, s);
+    rc = launch_search(a, kind, kCount, grouped, c->sm_count, s);
+    timer_end(c, s, a.nu);
+    if (rc) return rc;
     k_counts_by_caller<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->cnt64, offsets);
+    note_launch();
     if ((rc = exclusive_scan_i64(c, offsets, offsets, n_act, offsets + n_act, s))) return rc;
     if (n_act == 0) cudaMemsetAsync(offsets, 0, sizeof(int64_t), s);
     int64_t total = 0;
@@ -361,26 +445,35 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
     *n_pairs = total;
     if (idx) {
         k_offsets_by_orig<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, offsets, c->cnt64);
-        if ((rc = launch_search(a, kind, kFill, grouped, c->sm_count, s))) return rc;
+        note_launch();
+        a.x_idx = idx;
+        timer_begin(c, s);
+        rc = launch_search(a, kind, kFill, grouped, c->sm_count, s);
+        timer_end(c, s, a.nu);
+        if (rc) return rc;
         if (total > cap) {
             finish(c, s, 0);
             return set_error(SPHGRP_EOVERFLOW, "more pairs than cap");
         }
     }
     c->last.walks = a.ngroups;
+    c->last.members = nu;
     return finish(c, s, 0);
 }
 
 int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
                            int kind, int group_size, int64_t cap, int64_t* group_offsets,
-                           int32_t* members, int32_t* cand, int64_t* n_cand, cudaStream_t s) {
+                           int32_t* group_first, int32_t* members, int32_t* cand, int64_t* n_groups,
+                           int64_t* n_cand, cudaStream_t s) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     int rc = check_common(c, n_act, active, SPHGRP_GROUPED, group_size);
     if (rc) return rc;
     if (kind != SPHGRP_DENSITY && kind != SPHGRP_HYDRO) return set_error(SPHGRP_EINVAL, "bad kind");
-    if (!h || !group_offsets || !n_cand) return set_error(SPHGRP_EINVAL, "null h, group_offsets or n_cand");
+    if (!h || !group_offsets || !n_cand || !n_groups)
+        return set_error(SPHGRP_EINVAL, "null h, group_offsets, n_groups or n_cand");
     reset_flags(c, s);
     k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    note_launch();
     if (kind == SPHGRP_HYDRO) {
         cudaMemsetAsync(c->hyd0, 0, c->n * sizeof(float4), s);
         cudaMemsetAsync(c->hyd1, 0, c->n * sizeof(float4), s);
@@ -392,29 +485,44 @@ int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
     a.U = c->act;
     a.nu = nu;
     a.g = group_size;
-    a.ngroups = (nu + group_size - 1) / group_size;
+    if ((rc = make_groups(c, &a, c->act, nu, group_size, s))) return rc;
     a.x_cnt = c->cnt64;
     a.x_cap = cap;
-    if ((rc = launch_search(a, kind, kSupCount, true, c->sm_count, s))) return rc;
+    timer_begin(c, s);
+    rc = launch_search(a, kind, kSupCount, true, c->sm_count, s);
+    timer_end(c, s, a.nu);
+    if (rc) return rc;
     int ng = a.ngroups;
     if ((rc = exclusive_scan_i64(c, c->cnt64, group_offsets, ng, group_offsets + ng, s))) return rc;
     if (ng == 0) cudaMemsetAsync(group_offsets, 0, sizeof(int64_t), s);
-    if (members) k_members<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->act, c->perm, members);
+    if (members) {
+        k_members<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->act, c->perm, members);
+        note_launch();
+    }
+    if (group_first) {
+        k_group_first<<<blocks_for(ng + 1, 256), 256, 0, s>>>(ng, nu, group_size, a.groups, group_first);
+        note_launch();
+    }
     cudaMemcpyAsync(c->host_small + 32, group_offsets + ng, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if ((rc = check_cuda(cudaStreamSynchronize(s), "superset count"))) return rc;
     int64_t total = 0;
     std::memcpy(&total, c->host_small + 32, sizeof(int64_t));
     *n_cand = total;
+    *n_groups = ng;
     if (cand) {
         a.x_off = group_offsets;
         a.x_idx = cand;
-        if ((rc = launch_search(a, kind, kSupFill, true, c->sm_count, s))) return rc;
+        timer_begin(c, s);
+        rc = launch_search(a, kind, kSupFill, true, c->sm_count, s);
+        timer_end(c, s, a.nu);
+        if (rc) return rc;
         if (total > cap) {
             finish(c, s, 0);
             return set_error(SPHGRP_EOVERFLOW, "more candidates than cap");
         }
     }
     c->last.walks = ng;
+    c->last.members = nu;
     return finish(c, s, 0);
 }
 
@@ -427,6 +535,7 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     if (!h || !rho || !drhodh || !fgrad || !nngb) return set_error(SPHGRP_EINVAL, "null output array");
     reset_flags(c, s);
     k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    note_launch();
     int nu = 0;
     if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
     const bool grouped = mode == SPHGRP_GROUPED;
@@ -434,7 +543,7 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     int32_t* U2 = c->act2;
     int* nfail = c->work + 8;
     cudaMemsetAsync(nfail, 0, sizeof(int), s);
-    int64_t walks = 0;
+    int64_t walks = 0, members = 0;
     int it = 1;
     const int max_iter = iterate ? c->p.max_iter : 1;
     for (it = 1; it <= max_iter && nu > 0; ++it) {
@@ -443,11 +552,16 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         a.nu = nu;
         a.g = grouped ? group_size : 1;
         a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
+        if (grouped && (rc = make_groups(c, &a, U, nu, group_size, s))) return rc;
         a.o_s0 = c->acc_rho;
         a.o_s1 = c->acc_drho;
         a.o_n = c->acc_n;
         walks += a.ngroups;
-        if ((rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s))) return rc;
+        members += nu;
+        timer_begin(c, s);
+        rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
+        timer_end(c, s, a.nu);
+        if (rc) return rc;
         UpdateArgs ua;
         std::memset(&ua, 0, sizeof(ua));
         ua.U = U;
@@ -479,6 +593,7 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
         if ((rc = exclusive_scan_i32(c, c->flag, c->scan, nu, total, s))) return rc;
         k_compact_list<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->flag, c->scan, U, U2);
+        note_launch();
         cudaMemcpyAsync(c->host_small, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if ((rc = check_cuda(cudaStreamSynchronize(s), "iteration count"))) return rc;
         nu = c->host_small[0];
@@ -487,6 +602,7 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     cudaMemcpyAsync(c->host_small + 2, nfail, sizeof(int), cudaMemcpyDeviceToHost, s);
     rc = finish(c, s, 0);
     c->last.walks = walks;
+    c->last.members = members;
     c->last.iterations = std::min(it, max_iter);
     if (rc) return rc;
     if (c->host_small[2] > 0)
@@ -506,6 +622,7 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, co
     k_hydro_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, rho, fgrad, vel, u,
                                                       (float)c->p.gamma, c->h64, c->pfix, c->hyd0,
                                                       c->hyd1, c->err);
+    note_launch();
     if ((rc = refresh_hmax(c, s))) return rc;
     int nu = 0;
     if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
@@ -515,12 +632,36 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, co
     a.nu = nu;
     a.g = grouped ? group_size : 1;
     a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
+    if (grouped && (rc = make_groups(c, &a, c->act, nu, group_size, s))) return rc;
     a.o_acc = acc;
     a.o_dudt = dudt;
     a.o_nh = nngb;
-    if ((rc = launch_search(a, SPHGRP_HYDRO, kAcc, grouped, c->sm_count, s))) return rc;
+    timer_begin(c, s);
+    rc = launch_search(a, SPHGRP_HYDRO, kAcc, grouped, c->sm_count, s);
+    timer_end(c, s, a.nu);
+    if (rc) return rc;
     c->last.walks = a.ngroups;
+    c->last.members = nu;
     return finish(c, s, 0);
+}
+
+int sphgrp_get_launch_log(sphgrp_ctx* ctx, int cap, int64_t* members, int64_t* candidates,
+                          int64_t* pair_tests, int64_t* nodes, double* ms, int* count) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c || !count || cap < 0) return set_error(SPHGRP_EINVAL, "null argument");
+    int n = std::min(cap, c->ntimed);
+    for (int k = 0; k < n; ++k) {
+        const DevCounters& cur = c->ctr_log_host[k];
+        DevCounters prev{};
+        if (k > 0) prev = c->ctr_log_host[k - 1];
+        if (members) members[k] = c->log_members[k];
+        if (candidates) candidates[k] = (int64_t)(cur.cands - prev.cands);
+        if (pair_tests) pair_tests[k] = (int64_t)(cur.tests - prev.tests);
+        if (nodes) nodes[k] = (int64_t)(cur.nodes - prev.nodes);
+        if (ms) ms[k] = c->log_ms[k];
+    }
+    *count = n;
+    return SPHGRP_OK;
 }
 
 int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out) {

@@ -74,8 +74,21 @@ __device__ __forceinline__ float radius2_units(float r_box) {
 // Per-member state
 // ---------------------------------------------------------------------------------
 
+// Members farther than this many smoothing lengths from the group centre (per axis)
+// evaluate the pair physics from exact fixed-point differences: the FP32 difference of
+// two large centre-relative coordinates would lose up to |m| / h ulps of r.
+constexpr float kPreciseReach = 2.0f;
+
+// x_j - x_k from the fixed-point layout: exact integer minimum image plus the offsets.
+__device__ __forceinline__ float fix_diff(uint32_t Xj, float oj, uint32_t Xk, float ok) {
+    return (__int2float_rn((int32_t)(Xj - Xk)) + (oj - ok)) * kUnitToBox;
+}
+
 struct DMember {
     float mx, my, mz;
+    uint32_t X, Y, Z;   // fixed-point position (exact pair differences)
+    float ox, oy, oz;
+    bool precise;       // far from the group centre: physics from exact differences
     float hinv;
     float h2lo, h2hi;   // decided-inside below h2lo, candidate below h2hi
     int rank;           // -1: slot empty
@@ -86,6 +99,9 @@ struct DMember {
 
 struct HMember {
     float mx, my, mz;
+    uint32_t X, Y, Z;
+    float ox, oy, oz;
+    bool precise;
     float h, hinv, sk;  // sk = 8 / (pi h^4): dW/dr = sk * dw/dq
     float h2, bk;       // h^2 (FP32 of the FP64 square), band offset 8 b |m|^2
     float vx, vy, vz, cs, A, rho;
@@ -101,6 +117,7 @@ __device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, in
     M.s0 = M.c0 = M.s1 = M.c1 = 0.0f;
     M.n = 0;
     M.xpos = 0;
+    M.precise = false;
     if (rank < 0) {
         M.mx = M.my = M.mz = 0.0f;
         M.hinv = 0.0f;
@@ -112,9 +129,12 @@ __device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, in
     M.mx = rel_coord(P.x, O.x, cx);
     M.my = rel_coord(P.y, O.y, cy);
     M.mz = rel_coord(P.z, O.z, cz);
+    M.X = P.x; M.Y = P.y; M.Z = P.z;
+    M.ox = O.x; M.oy = O.y; M.oz = O.z;
     double h = a.h64[rank];
     float hf = (float)h;
     M.hinv = 1.0f / hf;
+    M.precise = fmaxf(fabsf(M.mx), fmaxf(fabsf(M.my), fabsf(M.mz))) > kPreciseReach * hf;
     float h2 = (float)(h * h);
     float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
     float bk = 8.0f * kBandRel * m2;
@@ -128,6 +148,7 @@ __device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, in
     M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = M.su = M.cu = 0.0f;
     M.n = 0;
     M.xpos = 0;
+    M.precise = false;
     if (rank < 0) {
         M.mx = M.my = M.mz = 0.0f;
         M.h = 0.0f; M.hinv = 0.0f; M.sk = 0.0f;
@@ -140,8 +161,11 @@ __device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, in
     M.mx = rel_coord(P.x, O.x, cx);
     M.my = rel_coord(P.y, O.y, cy);
     M.mz = rel_coord(P.z, O.z, cz);
+    M.X = P.x; M.Y = P.y; M.Z = P.z;
+    M.ox = O.x; M.oy = O.y; M.oz = O.z;
     double h = a.h64[rank];
     M.h = (float)h;
+    M.precise = fmaxf(fabsf(M.mx), fmaxf(fabsf(M.my), fabsf(M.mz))) > kPreciseReach * M.h;
     float4 H0 = a.hyd0[rank];
     float4 H1 = a.hyd1[rank];
     M.hinv = H1.z;
@@ -158,11 +182,21 @@ __device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, in
 // Pair physics shared by both forms
 // ---------------------------------------------------------------------------------
 
+// Difference of two coordinates relative to one centre.  Both lie in [-1/2, 1/2); when
+// a group can reach half the box (WRAP) the difference is brought back to the nearest
+// periodic image, otherwise it already is that image (|m| + h < 1/2 for every member).
+template <bool WRAP>
+__device__ __forceinline__ float rel_diff(float p, float m) {
+    float d = p - m;
+    if (WRAP) d -= rintf(d);
+    return d;
+}
+
 // density pair: cand = {dx, dy, dz, m_j} relative to the same centre as the member
-template <int MODE>
+template <int MODE, bool WRAP = false>
 __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, float4 cand, int crank,
                                              LocalCounters& lc) {
-    float dx = cand.x - M.mx, dy = cand.y - M.my, dz = cand.z - M.mz;
+    float dx = rel_diff<WRAP>(cand.x, M.mx), dy = rel_diff<WRAP>(cand.y, M.my), dz = rel_diff<WRAP>(cand.z, M.mz);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     bool in = r2 < M.h2lo;
     if (!in) {
@@ -175,6 +209,14 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
     M.n++;
     lc.pairs++;
     if (MODE == kAcc) {
+        if (M.precise) {
+            uint4 Q = a.pfix[crank];
+            float4 O = a.poff[crank];
+            dx = fix_diff(Q.x, O.x, M.X, M.ox);
+            dy = fix_diff(Q.y, O.y, M.Y, M.oy);
+            dz = fix_diff(Q.z, O.z, M.Z, M.oz);
+            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        }
         float q = sqrtf(r2) * M.hinv;
         float w, dw;
         m4_shape(q, w, dw);
@@ -188,11 +230,11 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
 }
 
 // hydro pair: p = {dx, dy, dz, m_j}, hh = {h_j, hinv_j, s_j, A_j}, v = {vx, vy, vz, c_j}
-template <int MODE>
+template <int MODE, bool WRAP = false>
 __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 hh,
                                            float4 v, float rho_j, int crank, LocalCounters& lc) {
     if (crank == M.rank) return;
-    float dx = p.x - M.mx, dy = p.y - M.my, dz = p.z - M.mz;
+    float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float H2 = fmaxf(M.h2, hh.x * hh.x);
     bool in = r2 < fmaf(H2, 1.0f - 3.0f * kBandRel, -M.bk);
@@ -212,6 +254,14 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
         return;
     }
     if (MODE != kAcc) return;
+    if (M.precise) {
+        uint4 Q = a.pfix[crank];
+        float4 O = a.poff[crank];
+        dx = fix_diff(Q.x, O.x, M.X, M.ox);
+        dy = fix_diff(Q.y, O.y, M.Y, M.oy);
+        dz = fix_diff(Q.z, O.z, M.Z, M.oz);
+        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    }
     if (r2 == 0.0f) return;  // coincident: the kernel gradient vanishes
     float r = sqrtf(r2);
     float rinv = 1.0f / r;
@@ -243,7 +293,7 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
 // Grouped form: one warp per group
 // ---------------------------------------------------------------------------------
 
-struct WalkSmem {
+struct alignas(16) WalkSmem {
     uint32_t stack[kStackCap];   // node ranges: (first child << 3) | (count - 1)
     int2 ranges[kRangeCap];      // pending leaf ranges (first rank, count)
     int rpre[kRangeCap + 1];     // prefix of the pending counts
@@ -303,6 +353,57 @@ __device__ __forceinline__ int member_of(const Layout& L, int lane, int mm, int 
     return k < g ? k : -1;
 }
 
+// Member x candidate filter of one staged tile: phase A marks, for 32 candidates at a
+// time, the candidates inside each member's FP32 threshold (a bit mask per member);
+// phase B takes the marked pairs one by one for the exact decision and the physics.
+template <int KIND, int MODE, int M, bool WRAP, class Tile>
+__device__ __forceinline__ void filter_tile(const Tile& T, const Layout& L, DMember* dm, HMember* hm,
+                                            int nt, const SearchArgs& a, LocalCounters& lc) {
+    const int njj = (nt > L.slice) ? (nt - L.slice + L.S - 1) / L.S : 0;
+    for (int base = 0; base < njj; base += 32) {
+        const int cnt = min(32, njj - base);
+        uint32_t mask[M];
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) mask[mm] = 0u;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            int jj = min(base + q, njj - 1);
+            int j = L.slice + L.S * jj;
+            float4 cp = T.p[j];
+            float hj = 0.0f;
+            if constexpr (KIND == 1) hj = T.h[j].x;
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+                float mx, my, mz, thr;
+                if constexpr (KIND == 0) {
+                    mx = dm[mm].mx; my = dm[mm].my; mz = dm[mm].mz; thr = dm[mm].h2hi;
+                } else {
+                    mx = hm[mm].mx; my = hm[mm].my; mz = hm[mm].mz;
+                    thr = fmaf(fmaxf(hm[mm].h2, hj * hj), 1.0f + 3.0f * kBandRel, hm[mm].bk);
+                }
+                float dx = rel_diff<WRAP>(cp.x, mx), dy = rel_diff<WRAP>(cp.y, my), dz = rel_diff<WRAP>(cp.z, mz);
+                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (r2 < thr && q < cnt) mask[mm] |= 1u << q;
+            }
+        }
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) {
+            int rk = KIND == 0 ? dm[mm].rank : hm[mm].rank;
+            if (rk >= 0) lc.tests += cnt;
+            while (mask[mm]) {
+                int q = __ffs(mask[mm]) - 1;
+                mask[mm] &= mask[mm] - 1u;
+                int j = L.slice + L.S * (base + q);
+                if constexpr (KIND == 0) {
+                    density_pair<MODE, WRAP>(dm[mm], a, T.p[j], T.r[j], lc);
+                } else {
+                    hydro_pair<MODE, WRAP>(hm[mm], a, T.p[j], T.h[j], T.v[j], T.rho[j], T.r[j], lc);
+                }
+            }
+        }
+    }
+}
+
 template <int KIND, int MODE, int M>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_group(SearchArgs a) {
@@ -324,9 +425,18 @@ k_group(SearchArgs a) {
         if (lane == 0) gid = atomicAdd(a.work, 1);
         gid = __shfl_sync(0xffffffffu, gid, 0);
         if (gid >= a.ngroups) break;
-        const int gbase = gid * a.g;
-        const int gcnt = min(a.g, a.nu - gbase);
-        // ---- group set-up: centre = fixed-point position of the first member
+        int gbase, gcnt;
+        if (a.groups) {
+            int2 G = a.groups[gid];
+            gbase = G.x;
+            gcnt = G.y;
+        } else {
+            gbase = gid * a.g;
+            gcnt = min(a.g, a.nu - gbase);
+        }
+        // ---- group set-up: centre = fixed-point position of the first member, or the
+        // centre of the members' bounding box (offsets from the first member are exact
+        // minimum-image integers)
         uint32_t cx = 0, cy = 0, cz = 0;
         if (lane == 0) {
             uint4 P = a.pfix[a.U[gbase]];
@@ -335,6 +445,32 @@ k_group(SearchArgs a) {
         cx = __shfl_sync(0xffffffffu, cx, 0);
         cy = __shfl_sync(0xffffffffu, cy, 0);
         cz = __shfl_sync(0xffffffffu, cz, 0);
+        if (a.centre_box) {
+            int lox = 0, loy = 0, loz = 0, hix = 0, hiy = 0, hiz = 0;
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+                int k = member_of(L, lane, mm, a.g);
+                if (k >= 0 && k < gcnt) {
+                    uint4 P = a.pfix[a.U[gbase + k]];
+                    int dx = (int32_t)(P.x - cx), dy = (int32_t)(P.y - cy), dz = (int32_t)(P.z - cz);
+                    lox = min(lox, dx); hix = max(hix, dx);
+                    loy = min(loy, dy); hiy = max(hiy, dy);
+                    loz = min(loz, dz); hiz = max(hiz, dz);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lox = min(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+                loy = min(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+                loz = min(loz, __shfl_xor_sync(0xffffffffu, loz, o));
+                hix = max(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+                hiy = max(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+                hiz = max(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
+            }
+            cx += (uint32_t)(int32_t)(((int64_t)lox + hix) >> 1);
+            cy += (uint32_t)(int32_t)(((int64_t)loy + hiy) >> 1);
+            cz += (uint32_t)(int32_t)(((int64_t)loz + hiz) >> 1);
+        }
 
         DMember dm[KIND == 0 ? M : 1];
         HMember hm[KIND == 1 ? M : 1];
@@ -366,6 +502,10 @@ k_group(SearchArgs a) {
         // density: R_s = max_k (|m_k| + h_k); hydro: R_g = max_k |m_k|, hmax_g
         const float Rd2 = radius2_units(rlane);
         const float Rg = rlane, hmax_g = hlane;
+        // every relevant pair difference is already the nearest image when the group's
+        // reach stays below half the box (hydro: with the largest h of all particles)
+        const float reach = KIND == 0 ? rlane : Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[0].w));
+        const bool wrap_safe = reach < 0.49f;
 
         // export: write positions of every slot
         if (MODE == kFill) {
@@ -496,50 +636,8 @@ k_group(SearchArgs a) {
                     }
                     __syncwarp();
                     if (!kSup) {
-                        // ---- member x candidate filter of the tile
-                        const int njj = (nt > L.slice) ? (nt - L.slice + L.S - 1) / L.S : 0;
-                        for (int base = 0; base < njj; base += 32) {
-                            const int cnt = min(32, njj - base);
-                            uint32_t mask[M];
-#pragma unroll
-                            for (int mm = 0; mm < M; ++mm) mask[mm] = 0u;
-#pragma unroll 8
-                            for (int q = 0; q < 32; ++q) {
-                                int jj = min(base + q, njj - 1);
-                                int j = L.slice + L.S * jj;
-                                float4 cp = T.p[j];
-                                float hj = 0.0f;
-                                if constexpr (KIND == 1) hj = T.h[j].x;
-#pragma unroll
-                                for (int mm = 0; mm < M; ++mm) {
-                                    float mx, my, mz, thr;
-                                    if constexpr (KIND == 0) {
-                                        mx = dm[mm].mx; my = dm[mm].my; mz = dm[mm].mz; thr = dm[mm].h2hi;
-                                    } else {
-                                        mx = hm[mm].mx; my = hm[mm].my; mz = hm[mm].mz;
-                                        thr = fmaf(fmaxf(hm[mm].h2, hj * hj), 1.0f + 3.0f * kBandRel, hm[mm].bk);
-                                    }
-                                    float dx = cp.x - mx, dy = cp.y - my, dz = cp.z - mz;
-                                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                                    if (r2 < thr && q < cnt) mask[mm] |= 1u << q;
-                                }
-                            }
-#pragma unroll
-                            for (int mm = 0; mm < M; ++mm) {
-                                int rk = KIND == 0 ? dm[mm].rank : hm[mm].rank;
-                                if (rk >= 0) lc.tests += cnt;
-                                while (mask[mm]) {
-                                    int q = __ffs(mask[mm]) - 1;
-                                    mask[mm] &= mask[mm] - 1u;
-                                    int j = L.slice + L.S * (base + q);
-                                    if constexpr (KIND == 0) {
-                                        density_pair<MODE>(dm[mm], a, T.p[j], T.r[j], lc);
-                                    } else {
-                                        hydro_pair<MODE>(hm[mm], a, T.p[j], T.h[j], T.v[j], T.rho[j], T.r[j], lc);
-                                    }
-                                }
-                            }
-                        }
+                        if (wrap_safe) filter_tile<KIND, MODE, M, false>(T, L, dm, hm, nt, a, lc);
+                        else filter_tile<KIND, MODE, M, true>(T, L, dm, hm, nt, a, lc);
                     }
                     __syncwarp();
                 }
@@ -705,6 +803,83 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
+// Grouping: chunks of g consecutive entries of the work list, each split in halves
+// (recursively) while the group's search sphere, ((sqrt(3)/2) box width + h_min)^3,
+// exceeds split * (members) member spheres h_min^3.  The
+// work list follows the key order, so chunks of a dense list are compact; chunks of a
+// sparse list (the last smoothing-length passes, scattered active sets) would give
+// search spheres spanning much of the box and are cut down instead.
+// ---------------------------------------------------------------------------------
+
+__global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, float split,
+                               const uint4* __restrict__ pfix, const double* __restrict__ h64,
+                               int2* __restrict__ tmp, int32_t* __restrict__ cnt) {
+    int ch = blockIdx.x * blockDim.x + threadIdx.x;
+    int nch = (nu + g - 1) / g;
+    if (ch >= nch) return;
+    const int s0 = ch * g, e0 = min(s0 + g, nu);
+    int2 st[16];
+    int sp = 0, ng = 0;
+    st[sp++] = make_int2(s0, e0);
+    while (sp > 0) {
+        int2 r = st[--sp];
+        int s = r.x, e = r.y;
+        bool keep = (e - s == 1) || split <= 0.0f;
+        if (!keep) {
+            uint4 P0 = pfix[U[s]];
+            int lox = 0, loy = 0, loz = 0, hix = 0, hiy = 0, hiz = 0;
+            float hmin = (float)h64[U[s]];
+            for (int k = s + 1; k < e; ++k) {
+                int rk = U[k];
+                uint4 P = pfix[rk];
+                int dx = (int32_t)(P.x - P0.x), dy = (int32_t)(P.y - P0.y), dz = (int32_t)(P.z - P0.z);
+                lox = min(lox, dx); hix = max(hix, dx);
+                loy = min(loy, dy); hiy = max(hiy, dy);
+                loz = min(loz, dz); hiz = max(hiz, dz);
+                hmin = fminf(hmin, (float)h64[rk]);
+            }
+            float ext = fmaxf(fmaxf((float)((int64_t)hix - lox), (float)((int64_t)hiy - loy)),
+                              (float)((int64_t)hiz - loz)) * kUnitToBox;
+            // search sphere of the group (box centre) relative to one member's sphere,
+            // in volume: the candidates every member filters, per member's own
+            float rel = fmaf(0.8660254f, ext / hmin, 1.0f);
+            keep = rel * rel * rel <= split * (float)(e - s);
+        }
+        if (keep) {
+            tmp[s0 + ng++] = make_int2(s, e - s);
+        } else {
+            int mid = s + (e - s + 1) / 2;
+            st[sp++] = make_int2(mid, e);
+            st[sp++] = make_int2(s, mid);
+        }
+    }
+    cnt[ch] = ng;
+}
+
+__global__ void k_gather_groups(int nch, int g, const int2* __restrict__ tmp, const int32_t* __restrict__ cnt,
+                                const int32_t* __restrict__ off, int2* __restrict__ groups) {
+    int ch = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ch >= nch) return;
+    int o = off[ch];
+    for (int k = 0; k < cnt[ch]; ++k) groups[o + k] = tmp[ch * g + k];
+}
+
+int launch_split_groups(const int32_t* U, int nu, int g, float split, const uint4* pfix, const double* h64,
+                        int2* tmp, int32_t* cnt, cudaStream_t s) {
+    int nch = (nu + g - 1) / g;
+    k_split_groups<<<blocks_for(nch, 128), 128, 0, s>>>(U, nu, g, split, pfix, h64, tmp, cnt);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "group split");
+}
+
+int launch_gather_groups(int nch, int g, const int2* tmp, const int32_t* cnt, const int32_t* off, int2* groups,
+                         cudaStream_t s) {
+    k_gather_groups<<<blocks_for(nch, 256), 256, 0, s>>>(nch, g, tmp, cnt, off, groups);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "group gather");
+}
+
+// ---------------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------------
 
@@ -729,6 +904,7 @@ static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
     int64_t grid = std::min<int64_t>((int64_t)per_sm * sm_count, want);
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, kWarpsPerBlock * 32, sh, s>>>(a);
+    note_launch();
     return check_cuda(cudaGetLastError(), "grouped search kernel");
 }
 
@@ -776,6 +952,7 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
         else if (mode == kFill) k_indiv<1, kFill><<<blocks, 128, 0, s>>>(a);
         else return set_error(SPHGRP_EINVAL, "bad search mode");
     }
+    note_launch();
     return check_cuda(cudaGetLastError(), "individual search kernel");
 }
 
@@ -830,6 +1007,7 @@ __global__ void k_hsml_update(UpdateArgs a) {
 int launch_hsml_update(const UpdateArgs& a, cudaStream_t s) {
     if (a.nu <= 0) return SPHGRP_OK;
     k_hsml_update<<<blocks_for(a.nu, 256), 256, 0, s>>>(a);
+    note_launch();
     return check_cuda(cudaGetLastError(), "hsml update");
 }
 

@@ -26,6 +26,8 @@ struct SearchArgs {
     int nu;
     int g;          // group size (grouped form)
     int ngroups;
+    bool centre_box; // group sphere centred on the members' box (else on the first member)
+    const int2* groups; // (first entry of U, count) per group; null: chunks of g
     // density pass results (rank space)
     float* o_s0;
     float* o_s1;
@@ -76,6 +78,10 @@ struct UpdateArgs {
 
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s);
 int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
+int launch_split_groups(const int32_t* U, int nu, int g, float split, const uint4* pfix, const double* h64,
+                        int2* tmp, int32_t* cnt, cudaStream_t s);
+int launch_gather_groups(int nch, int g, const int2* tmp, const int32_t* cnt, const int32_t* off, int2* groups,
+                         cudaStream_t s);
 int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s);
 int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
                        cudaStream_t s);

@@ -153,11 +153,14 @@ static void scan_rec(const T* in, T* out, int64_t n, T* aux, T* total, cudaStrea
     int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb <= 1) {
         k_scan_down<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr, total);
+        note_launch();
         return;
     }
     k_scan_reduce<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, aux);
+    note_launch();
     scan_rec<T>(aux, aux, nb, aux + nb, nullptr, s);
     k_scan_down<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, aux, total);
+    note_launch();
 }
 
 static int64_t scan_aux_need(int64_t n) {
@@ -276,6 +279,7 @@ __global__ void k_invert_perm(int64_t n, const int32_t* __restrict__ perm, int32
 int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s) {
     // keys in input order go to keys_alt; the passes ping-pong keys_alt <-> keys
     k_keys<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, c->keys_alt, c->err);
+    note_launch();
     int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     int64_t nh = (int64_t)256 * nblocks;
     if (nh > c->hist_cap) return set_error(SPHGRP_EOVERFLOW, "radix histogram scratch too small");
@@ -286,10 +290,12 @@ int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s) {
     for (int pass = 0; pass < 8; ++pass) {
         int shift = 8 * pass;
         k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, n, shift, c->hist, nblocks);
+        note_launch();
         int rc = exclusive_scan_i32(c, reinterpret_cast<const int32_t*>(c->hist),
                                     reinterpret_cast<int32_t*>(c->hist), nh, nullptr, s);
         if (rc) return rc;
         k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, c->hist, nblocks);
+        note_launch();
         // swap
         uint64_t* tk = kin; kin = kout; kout = tk;
         if (pass == 0) { vin = c->perm; vout = c->perm_alt; }
@@ -299,6 +305,7 @@ int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s) {
     if (kin != c->keys) { uint64_t* t = c->keys; c->keys = c->keys_alt; c->keys_alt = t; }
     if (vin != c->perm) { int32_t* t = c->perm; c->perm = c->perm_alt; c->perm_alt = t; }
     k_invert_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->rank_of);
+    note_launch();
     return check_cuda(cudaGetLastError(), "sort");
 }
 

@@ -21,8 +21,8 @@ namespace sphgrp {
 //   pfix      uint4    {X, Y, Z, h_f32 bits}: fixed-point position X = floor(x 2^32)
 //   poff      float4   {x 2^32 - X, ..., m}: sub-unit offsets in [0,1) and the mass
 //   h64       double   smoothing length (FP64 master)
-//   hyd0      float4   {vx, vy, vz, A = f P / rho^2}          (hydro candidates)
-//   hyd1      float4   {rho, c, unused, unused}               (hydro candidates)
+//   hyd0      float4   {vx, vy, vz, c}                        (hydro candidates)
+//   hyd1      float4   {A = f P / rho^2, rho, 1/h, 8/(pi h^4)} (hydro candidates)
 //
 // A coordinate relative to a fixed-point centre C is
 //   float(int32(X - C)) + off, scaled by 2^-32:
@@ -102,6 +102,10 @@ struct Ctx {
     int32_t* acc_n = nullptr;
     int32_t* it_count = nullptr;
     int64_t* cnt64 = nullptr;      // per-target pair counts (export)
+    int2* groups = nullptr;        // group list of the current search (first, count)
+    int2* groups_tmp = nullptr;
+    int32_t* grp_cnt = nullptr;
+    int32_t* grp_off = nullptr;
     // tree
     Tree tree;
     // counters and error flags
@@ -110,7 +114,22 @@ struct Ctx {
     int* work = nullptr;           // dynamic work counters for persistent kernels
     int* host_small = nullptr;     // pinned host scratch
     sphgrp_stats last{};
+    // device timing of the search kernels of the current call
+    static constexpr int kMaxTimed = 128;
+    cudaEvent_t tev[2 * kMaxTimed] = {};
+    int ntimed = 0;
+    DevCounters* ctr_log = nullptr;       // counters after every timed launch (device)
+    int64_t log_members[kMaxTimed] = {};  // particles processed by every timed launch
+    DevCounters* ctr_log_host = nullptr;  // pinned copy
+    float log_ms[kMaxTimed] = {};
 };
+
+// CUDA-event bracket around one search-kernel launch (api.cu)
+void timer_begin(Ctx* c, cudaStream_t s);
+void timer_end(Ctx* c, cudaStream_t s, int64_t members);
+
+// process-wide count of the kernels this library has launched (api.cu)
+void note_launch();
 
 // error reporting (api.cu)
 int set_error(int code, const std::string& msg);
@@ -166,7 +185,11 @@ __device__ __forceinline__ double exact_r2(const double* xd, const double* yd, c
 constexpr float kBandRel = 3.814697265625e-06f;  // 2^-18
 
 // launch helpers
-inline int blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) / threads); }
+// at least one block: kernels bound-check their index, and an empty grid is a launch error
+inline int blocks_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    return b < 1 ? 1 : (int)b;
+}
 
 // kernels' host launchers (defined in the .cu files)
 int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s);              // sort.cu

@@ -216,6 +216,7 @@ int build_tree(Ctx* c, cudaStream_t s) {
         if (nf == 0) break;
         k_split_count<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, a, nf, level,
                                                           c->p.leaf_size, c->flag);
+        note_launch();
         rc = exclusive_scan_i32(c, c->flag, c->scan, nf, total_dev, s);
         if (rc) return rc;
         cudaMemcpyAsync(c->host_small, total_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -226,6 +227,7 @@ int build_tree(Ctx* c, cudaStream_t s) {
         }
         k_split_write<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, t.next, t.nlevel, a, nf,
                                                           level, c->flag, c->scan, b);
+        note_launch();
         t.level_begin[level + 2] = b + total;
         t.count = b + total;
         if (total == 0) { ++level; break; }
@@ -239,10 +241,13 @@ int build_tree(Ctx* c, cudaStream_t s) {
         return set_error(SPHGRP_ENOMEM, "octree box scratch");
     for (int lv = t.nlevels - 1; lv >= 0; --lv) {
         int a = t.level_begin[lv], nf = t.level_begin[lv + 1] - a;
-        if (nf > 0)
+        if (nf > 0) {
             k_box_level<<<blocks_for(nf, 128), 128, 0, s>>>(a, nf, t.nlink, t.next, c->pfix, blo, bhi, t.ncen);
+            note_launch();
+        }
     }
     k_box_final<<<blocks_for(t.count, 256), 256, 0, s>>>(t.count, blo, bhi, t.ncen, t.next);
+    note_launch();
     cudaFreeAsync(blo, s);
     cudaFreeAsync(bhi, s);
     return check_cuda(cudaGetLastError(), "octree build");
@@ -252,8 +257,10 @@ int refresh_hmax(Ctx* c, cudaStream_t s) {
     Tree& t = c->tree;
     for (int lv = t.nlevels - 1; lv >= 0; --lv) {
         int a = t.level_begin[lv], nf = t.level_begin[lv + 1] - a;
-        if (nf > 0)
+        if (nf > 0) {
             k_hmax_level<<<blocks_for(nf, 128), 128, 0, s>>>(a, nf, t.nlink, t.next, c->pfix, t.ncen);
+            note_launch();
+        }
     }
     return check_cuda(cudaGetLastError(), "hmax refresh");
 }
@@ -261,6 +268,7 @@ int refresh_hmax(Ctx* c, cudaStream_t s) {
 int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s) {
     k_gather<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, pos, m, c->xd, c->yd, c->zd,
                                                   c->pfix, c->poff);
+    note_launch();
     return check_cuda(cudaGetLastError(), "gather");
 }
 

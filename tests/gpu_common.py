@@ -75,16 +75,20 @@ class Gpu:
         return off.cpu().numpy(), idx.cpu().numpy()[:total]
 
     def supersets(self, active, h, kind, g):
+        """(group_first, members in key order, group candidate offsets, candidates)."""
         torch = self.torch
         act = self.t(active, torch.int32)
         hh = self.t(h, torch.float64)
-        ng = (len(active) + g - 1) // g
-        goff = torch.empty(ng + 1, dtype=torch.int64, device=self.dev)
-        mem = torch.empty(max(len(active), 1), dtype=torch.int32, device=self.dev)
-        total = self.ctx.group_supersets(act, hh, kind, g, goff)
+        na = len(active)
+        goff = torch.empty(na + 1, dtype=torch.int64, device=self.dev)
+        gfirst = torch.empty(na + 1, dtype=torch.int32, device=self.dev)
+        mem = torch.empty(max(na, 1), dtype=torch.int32, device=self.dev)
+        ng, total = self.ctx.group_supersets(act, hh, kind, g, goff)
         cand = torch.empty(max(total, 1), dtype=torch.int32, device=self.dev)
-        self.ctx.group_supersets(act, hh, kind, g, goff, mem, cand, cap=total)
-        return goff.cpu().numpy(), mem.cpu().numpy()[:len(active)], cand.cpu().numpy()[:total]
+        ng2, total2 = self.ctx.group_supersets(act, hh, kind, g, goff, gfirst, mem, cand, cap=total)
+        assert (ng2, total2) == (ng, total)
+        return (gfirst.cpu().numpy()[:ng + 1], mem.cpu().numpy()[:na], goff.cpu().numpy()[:ng + 1],
+                cand.cpu().numpy()[:total])
 
     def density(self, active, h, iterate, mode, g):
         torch = self.torch
