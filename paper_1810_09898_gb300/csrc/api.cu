@@ -174,6 +174,7 @@ int finish(Ctx* c, cudaStream_t s, int rc) {
     if (err & kErrStack) return set_error(SPHGRP_EOVERFLOW, "walk stack overflow");
     if (err & kErrNodes) return set_error(SPHGRP_EOVERFLOW, "octree capacity exceeded");
     if (err & kErrCap) return set_error(SPHGRP_EOVERFLOW, "export capacity exceeded");
+    if (err & kErrTimeout) return set_error(SPHGRP_ETIMEOUT, "a bounded device wait (tile copy) gave up");
     return SPHGRP_OK;
 }
 

@@ -91,8 +91,10 @@ struct DMember {
     bool precise;       // far from the group centre: physics from exact differences
     float hinv;
     float h2lo, h2hi;   // decided-inside below h2lo, candidate below h2hi
+    float thr_dot;      // phase-A threshold of |p|^2 - 2 p.m (= h2hi - |m|^2)
     int rank;           // -1: slot empty
-    float s0, c0, s1, c1;
+    float s0, c0, s1, c1;   // compensated totals
+    float p0, p1;           // plain partial sums of the current tile
     int n;
     int64_t xpos;       // export write position
 };
@@ -104,9 +106,11 @@ struct HMember {
     bool precise;
     float h, hinv, sk;  // sk = 8 / (pi h^4): dW/dr = sk * dw/dq
     float h2, bk;       // h^2 (FP32 of the FP64 square), band offset 8 b |m|^2
+    float bk_dot;       // bk - |m|^2: phase-A offset of the dot form
     float vx, vy, vz, cs, A, rho;
     int rank;
-    float sx, cx_, sy, cy_, sz, cz_, su, cu;
+    float sx, cx_, sy, cy_, sz, cz_, su, cu;   // compensated totals
+    float px_, py_, pz_, pu;                   // plain partial sums of the current tile
     int n;
     int64_t xpos;
 };
@@ -115,6 +119,7 @@ __device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, in
                                              uint32_t cy, uint32_t cz) {
     M.rank = rank;
     M.s0 = M.c0 = M.s1 = M.c1 = 0.0f;
+    M.p0 = M.p1 = 0.0f;
     M.n = 0;
     M.xpos = 0;
     M.precise = false;
@@ -122,6 +127,7 @@ __device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, in
         M.mx = M.my = M.mz = 0.0f;
         M.hinv = 0.0f;
         M.h2lo = M.h2hi = -1.0f;
+        M.thr_dot = -3.0e38f;
         return;
     }
     uint4 P = a.pfix[rank];
@@ -140,12 +146,14 @@ __device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, in
     float bk = 8.0f * kBandRel * m2;
     M.h2hi = fmaf(h2, 1.0f + 3.0f * kBandRel, bk);
     M.h2lo = fmaf(h2, 1.0f - 3.0f * kBandRel, -bk);
+    M.thr_dot = M.h2hi - m2;
 }
 
 __device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, int rank, uint32_t cx,
                                              uint32_t cy, uint32_t cz) {
     M.rank = rank;
     M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = M.su = M.cu = 0.0f;
+    M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
     M.n = 0;
     M.xpos = 0;
     M.precise = false;
@@ -153,6 +161,7 @@ __device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, in
         M.mx = M.my = M.mz = 0.0f;
         M.h = 0.0f; M.hinv = 0.0f; M.sk = 0.0f;
         M.h2 = -1.0f; M.bk = -1.0f;
+        M.bk_dot = -3.0e38f;
         M.vx = M.vy = M.vz = M.cs = M.A = M.rho = 0.0f;
         return;
     }
@@ -173,6 +182,7 @@ __device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, in
     M.h2 = (float)(h * h);
     float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
     M.bk = 8.0f * kBandRel * m2;
+    M.bk_dot = M.bk - m2;
     M.vx = H0.x; M.vy = H0.y; M.vz = H0.z; M.cs = H0.w;
     M.A = H1.x;
     M.rho = H1.y;
@@ -192,14 +202,31 @@ __device__ __forceinline__ float rel_diff(float p, float m) {
     return d;
 }
 
-// density pair: cand = {dx, dy, dz, m_j} relative to the same centre as the member
+// Plain per-tile partial sums are folded into the compensated totals after every
+// tile (or leaf): a few tens of terms in plain FP32, Kahan across blocks.
+__device__ __forceinline__ void dflush(DMember& M) {
+    kahan_add(M.s0, M.c0, M.p0);
+    kahan_add(M.s1, M.c1, M.p1);
+    M.p0 = M.p1 = 0.0f;
+}
+
+__device__ __forceinline__ void hflush(HMember& M) {
+    kahan_add(M.sx, M.cx_, M.px_);
+    kahan_add(M.sy, M.cy_, M.py_);
+    kahan_add(M.sz, M.cz_, M.pz_);
+    kahan_add(M.su, M.cu, M.pu);
+    M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
+}
+
+// density pair: p = candidate's coordinates relative to the member's centre, m_j its mass
 template <int MODE, bool WRAP = false>
-__device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, float4 cand, int crank,
+__device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, float4 p, float mj, int crank,
                                              LocalCounters& lc) {
-    float dx = rel_diff<WRAP>(cand.x, M.mx), dy = rel_diff<WRAP>(cand.y, M.my), dz = rel_diff<WRAP>(cand.z, M.mz);
+    float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     bool in = r2 < M.h2lo;
     if (!in) {
+        if (!(r2 < M.h2hi)) return;
         double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
         double h = a.h64[M.rank];
         in = e < __dmul_rn(h, h);
@@ -207,7 +234,6 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
     }
     if (!in) return;
     M.n++;
-    lc.pairs++;
     if (MODE == kAcc) {
         if (M.precise) {
             uint4 Q = a.pfix[crank];
@@ -217,28 +243,30 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
             dz = fix_diff(Q.z, O.z, M.Z, M.oz);
             r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         }
-        float q = sqrtf(r2) * M.hinv;
+        float q = r2 * rsqrtf(fmaxf(r2, 1.0e-30f)) * M.hinv;
         float w, dw;
         m4_shape(q, w, dw);
-        kahan_add(M.s0, M.c0, cand.w * w);
-        kahan_add(M.s1, M.c1, cand.w * fmaf(q, dw, 3.0f * w));
+        M.p0 = fmaf(mj, w, M.p0);
+        M.p1 = fmaf(mj, fmaf(q, dw, 3.0f * w), M.p1);
     } else if (MODE == kFill) {
-        int64_t p = M.xpos++;
-        if (p < a.x_cap) a.x_idx[p] = a.perm[crank];
+        int64_t q = M.xpos++;
+        if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
         else atomicOr(a.err, kErrCap);
     }
 }
 
-// hydro pair: p = {dx, dy, dz, m_j}, hh = {h_j, hinv_j, s_j, A_j}, v = {vx, vy, vz, c_j}
+// hydro pair: p = relative coordinates, q = {h_j^2, m_j, -, -}, v = {vx, vy, vz, c_j},
+// hh = {A_j, rho_j, 1/h_j, s_j}
 template <int MODE, bool WRAP = false>
-__device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 hh,
-                                           float4 v, float rho_j, int crank, LocalCounters& lc) {
+__device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 q,
+                                           float4 v, float4 hh, int crank, LocalCounters& lc) {
     if (crank == M.rank) return;
     float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float H2 = fmaxf(M.h2, hh.x * hh.x);
+    float H2 = fmaxf(M.h2, q.x);
     bool in = r2 < fmaf(H2, 1.0f - 3.0f * kBandRel, -M.bk);
     if (!in) {
+        if (!(r2 < fmaf(H2, 1.0f + 3.0f * kBandRel, M.bk))) return;
         double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
         double hi = a.h64[M.rank], hj = a.h64[crank];
         in = e < fmax(__dmul_rn(hi, hi), __dmul_rn(hj, hj));
@@ -246,7 +274,6 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
     }
     if (!in) return;
     M.n++;
-    lc.pairs++;
     if (MODE == kFill) {
         int64_t q = M.xpos++;
         if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
@@ -263,30 +290,30 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
         r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     }
     if (r2 == 0.0f) return;  // coincident: the kernel gradient vanishes
-    float r = sqrtf(r2);
-    float rinv = 1.0f / r;
+    float rinv = rsqrtf(r2);
+    float r = r2 * rinv;
     float wi, dwi, wj, dwj;
     m4_shape(r * M.hinv, wi, dwi);
-    m4_shape(r * hh.y, wj, dwj);
+    m4_shape(r * hh.z, wj, dwj);
     float dWi = M.sk * dwi;
-    float dWj = hh.z * dwj;
+    float dWj = hh.w * dwj;
     float rx = -dx, ry = -dy, rz = -dz;  // r_ij = x_i - x_j
     float vx = M.vx - v.x, vy = M.vy - v.y, vz = M.vz - v.z;
     float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
     float visc = 0.0f;
     if (vr < 0.0f) {
-        float hb = 0.5f * (M.h + hh.x);
+        float hb = 0.5f * fmaf(q.x, hh.z, M.h);
         float mu = hb * vr / fmaf(a.eps * hb, hb, r2);
         float cb = 0.5f * (M.cs + v.w);
-        float rb = 0.5f * (M.rho + rho_j);
+        float rb = 0.5f * (M.rho + hh.y);
         visc = fmaf(-a.alpha * cb, mu, a.beta * mu * mu) / rb;
     }
     float gbar = 0.5f * (dWi + dWj);
-    float coef = p.w * fmaf(M.A, dWi, fmaf(hh.w, dWj, visc * gbar)) * rinv;
-    kahan_add(M.sx, M.cx_, -coef * rx);
-    kahan_add(M.sy, M.cy_, -coef * ry);
-    kahan_add(M.sz, M.cz_, -coef * rz);
-    kahan_add(M.su, M.cu, p.w * fmaf(M.A, dWi, 0.5f * visc * gbar) * vr * rinv);
+    float coef = q.y * fmaf(M.A, dWi, fmaf(hh.x, dWj, visc * gbar)) * rinv;
+    M.px_ = fmaf(coef, dx, M.px_);
+    M.py_ = fmaf(coef, dy, M.py_);
+    M.pz_ = fmaf(coef, dz, M.pz_);
+    M.pu = fmaf(q.y * fmaf(M.A, dWi, 0.5f * visc * gbar) * rinv, vr, M.pu);
 }
 
 // ---------------------------------------------------------------------------------
@@ -294,23 +321,84 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
 // ---------------------------------------------------------------------------------
 
 struct alignas(16) WalkSmem {
+    unsigned long long bar;      // mbarrier of the tile copies
     uint32_t stack[kStackCap];   // node ranges: (first child << 3) | (count - 1)
     int2 ranges[kRangeCap];      // pending leaf ranges (first rank, count)
     int rpre[kRangeCap + 1];     // prefix of the pending counts
     int nodes[32];
 };
 
+// ---------------------------------------------------------------------------------
+// TMA bulk copies (global -> shared) completing on an mbarrier
+// ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// orders this thread's earlier generic accesses of shared memory before later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// both addresses 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+// Waits for the phase with the given parity; gives up after a bounded number of polls
+// (the copies of a tile take microseconds), setting the timeout flag.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, unsigned* err) {
+    for (uint32_t k = 0; k < (1u << 24); ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicOr(err, kErrTimeout);
+    return false;
+}
+
+// Candidate tiles in shared memory.  The raw key-ordered records of a tile's leaf
+// ranges land here by TMA bulk copies (cp.async.bulk, global -> shared, completion
+// on an mbarrier); the fixed-point positions are then converted in place to FP32
+// coordinates relative to the group centre, {px, py, pz, |p|^2}.  With S slices the
+// lane of slice s filters positions s, s + S, s + 2S, ...; positions beyond the tile's
+// candidates, up to whole chunks of 32 per slice, hold NaN dummies.
 struct DensTile {
-    float4 p[kTileD];   // {dx, dy, dz, m}
-    int r[kTileD];
+    float4 p[kTileD];   // raw pfix -> {px, py, pz, |p|^2}
+    float4 o[kTileD];   // raw poff {ox, oy, oz, m}
+    int r[kTileD];      // ranks
+    uint32_t masks[kTileD];   // phase-A bit masks [chunk][lane]
 };
 
 struct HydroTile {
-    float4 p[kTileH];   // {dx, dy, dz, m}
-    float4 h[kTileH];   // {h, hinv, s, A}
-    float4 v[kTileH];   // {vx, vy, vz, c}
-    float rho[kTileH];
+    float4 p[kTileH];   // raw pfix -> {px, py, pz, |p|^2}
+    float4 o[kTileH];   // raw poff {ox, oy, oz, m} -> {h^2, m, -, -}
+    float4 v[kTileH];   // raw hyd0 {vx, vy, vz, c}
+    float4 h[kTileH];   // raw hyd1 {A, rho, 1/h, 8/(pi h^4)}
     int r[kTileH];
+    uint32_t masks[kTileH];
 };
 
 template <int KIND>
@@ -336,70 +424,102 @@ struct Layout {
     int gw;      // members per slice row (min(g, 32))
 };
 
-__device__ __forceinline__ Layout make_layout(int g, int lane, bool allow_slices) {
+__device__ __forceinline__ Layout make_layout(int g, int lane, bool allow_slices, int max_slices) {
     Layout L;
     L.gw = g < 32 ? g : 32;
     bool pow2 = (g & (g - 1)) == 0;
-    L.S = (allow_slices && g < 32 && pow2) ? 32 / g : 1;
+    L.S = (allow_slices && g < 32 && pow2) ? min(32 / g, max_slices) : 1;
     L.slice = L.S > 1 ? lane / g : 0;
+    if (L.slice >= L.S) L.slice = L.S;   // lanes beyond the last slice hold no member
     return L;
 }
 
 // member index (within the group) held by slot mm of this lane; -1 if none
 __device__ __forceinline__ int member_of(const Layout& L, int lane, int mm, int g) {
     int k;
-    if (L.S > 1) k = lane % g;
-    else k = lane + 32 * mm;
+    if (L.S > 1) {
+        if (L.slice >= L.S) return -1;
+        k = lane % g;
+    } else {
+        k = lane + 32 * mm;
+    }
     return k < g ? k : -1;
 }
 
-// Member x candidate filter of one staged tile: phase A marks, for 32 candidates at a
-// time, the candidates inside each member's FP32 threshold (a bit mask per member);
-// phase B takes the marked pairs one by one for the exact decision and the physics.
+// Member x candidate filter of one staged tile.  Phase A: for every chunk of 32 of
+// the lane's slice, a bit mask of the candidates inside the member's FP32 threshold,
+// tested in dot-product form |p|^2 - 2 p.m < h^2 - |m|^2 (three FMAs; its rounding
+// stays inside the FP64 decision band).  Phase B: every lane walks its own set bits
+// across all chunks (no per-chunk wait for the slowest lane) for the exact decision
+// and the physics; plain partial sums are folded into the compensated totals after
+// the tile.
 template <int KIND, int MODE, int M, bool WRAP, class Tile>
-__device__ __forceinline__ void filter_tile(const Tile& T, const Layout& L, DMember* dm, HMember* hm,
-                                            int nt, const SearchArgs& a, LocalCounters& lc) {
-    const int njj = (nt > L.slice) ? (nt - L.slice + L.S - 1) / L.S : 0;
-    for (int base = 0; base < njj; base += 32) {
-        const int cnt = min(32, njj - base);
-        uint32_t mask[M];
+__device__ __forceinline__ void filter_tile(Tile& T, const Layout& L, DMember* dm, HMember* hm, int nt,
+                                            const SearchArgs& a, LocalCounters& lc, int lane) {
+    const int S = L.S;
+    if (L.slice >= S) return;
+    const int cnt_slice = (nt > L.slice) ? (nt - L.slice + S - 1) / S : 0;
+    const int nch = ((nt + S - 1) / S + 31) >> 5;
 #pragma unroll
-        for (int mm = 0; mm < M; ++mm) mask[mm] = 0u;
-#pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-            int jj = min(base + q, njj - 1);
-            int j = L.slice + L.S * jj;
-            float4 cp = T.p[j];
-            float hj = 0.0f;
-            if constexpr (KIND == 1) hj = T.h[j].x;
+    for (int mm = 0; mm < M; ++mm) {
+        float ax, ay, az, mx, my, mz;
+        int rk;
+        if constexpr (KIND == 0) {
+            mx = dm[mm].mx; my = dm[mm].my; mz = dm[mm].mz; rk = dm[mm].rank;
+        } else {
+            mx = hm[mm].mx; my = hm[mm].my; mz = hm[mm].mz; rk = hm[mm].rank;
+        }
+        ax = -2.0f * mx; ay = -2.0f * my; az = -2.0f * mz;
+        for (int c = 0; c < nch; ++c) {
+            uint32_t mask = 0u;
+            const float4* P = T.p + L.slice + S * (c << 5);
 #pragma unroll
-            for (int mm = 0; mm < M; ++mm) {
-                float mx, my, mz, thr;
-                if constexpr (KIND == 0) {
-                    mx = dm[mm].mx; my = dm[mm].my; mz = dm[mm].mz; thr = dm[mm].h2hi;
+            for (int q = 0; q < 32; ++q) {
+                const float4 cp = P[q * S];
+                bool pass;
+                if constexpr (!WRAP) {
+                    float t = fmaf(cp.x, ax, fmaf(cp.y, ay, fmaf(cp.z, az, cp.w)));
+                    if constexpr (KIND == 0) {
+                        pass = t < dm[mm].thr_dot;
+                    } else {
+                        const float hj2 = T.o[L.slice + S * ((c << 5) + q)].x;
+                        pass = t < fmaf(fmaxf(hm[mm].h2, hj2), 1.0f + 3.0f * kBandRel, hm[mm].bk_dot);
+                    }
                 } else {
-                    mx = hm[mm].mx; my = hm[mm].my; mz = hm[mm].mz;
-                    thr = fmaf(fmaxf(hm[mm].h2, hj * hj), 1.0f + 3.0f * kBandRel, hm[mm].bk);
+                    float dx = rel_diff<true>(cp.x, mx), dy = rel_diff<true>(cp.y, my), dz = rel_diff<true>(cp.z, mz);
+                    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if constexpr (KIND == 0) {
+                        pass = r2 < dm[mm].h2hi;
+                    } else {
+                        const float hj2 = T.o[L.slice + S * ((c << 5) + q)].x;
+                        pass = r2 < fmaf(fmaxf(hm[mm].h2, hj2), 1.0f + 3.0f * kBandRel, hm[mm].bk);
+                    }
                 }
-                float dx = rel_diff<WRAP>(cp.x, mx), dy = rel_diff<WRAP>(cp.y, my), dz = rel_diff<WRAP>(cp.z, mz);
-                float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 < thr && q < cnt) mask[mm] |= 1u << q;
+                mask |= (pass ? 1u : 0u) << q;
+            }
+            T.masks[(c << 5) + lane] = mask;
+            if (rk >= 0) lc.tests += min(32, cnt_slice - (c << 5));
+        }
+        int c = 0;
+        uint32_t cur = T.masks[lane];
+        for (;;) {
+            while (cur == 0u) {
+                if (++c >= nch) break;
+                cur = T.masks[(c << 5) + lane];
+            }
+            if (cur == 0u) break;
+            const int q = __ffs(cur) - 1;
+            cur &= cur - 1u;
+            const int j = L.slice + S * ((c << 5) + q);
+            if constexpr (KIND == 0) {
+                density_pair<MODE, WRAP>(dm[mm], a, T.p[j], T.o[j].w, T.r[j], lc);
+            } else {
+                hydro_pair<MODE, WRAP>(hm[mm], a, T.p[j], T.o[j], T.v[j], T.h[j], T.r[j], lc);
             }
         }
-#pragma unroll
-        for (int mm = 0; mm < M; ++mm) {
-            int rk = KIND == 0 ? dm[mm].rank : hm[mm].rank;
-            if (rk >= 0) lc.tests += cnt;
-            while (mask[mm]) {
-                int q = __ffs(mask[mm]) - 1;
-                mask[mm] &= mask[mm] - 1u;
-                int j = L.slice + L.S * (base + q);
-                if constexpr (KIND == 0) {
-                    density_pair<MODE, WRAP>(dm[mm], a, T.p[j], T.r[j], lc);
-                } else {
-                    hydro_pair<MODE, WRAP>(hm[mm], a, T.p[j], T.h[j], T.v[j], T.rho[j], T.r[j], lc);
-                }
-            }
+        if (MODE == kAcc) {
+            if constexpr (KIND == 0) dflush(dm[mm]);
+            else hflush(hm[mm]);
         }
     }
 }
@@ -416,9 +536,12 @@ k_group(SearchArgs a) {
     Tile& T = reinterpret_cast<Tile*>(smem_raw + kWarpsPerBlock * sizeof(WalkSmem))[wib];
     constexpr bool kSup = (MODE == kSupCount || MODE == kSupFill);
     const bool allow_slices = (MODE == kAcc);
-    const Layout L = make_layout(a.g, lane, allow_slices);
+    const Layout L = make_layout(a.g, lane, allow_slices, TCAP / 32);
     LocalCounters lc;
     const uint32_t lt = (1u << lane) - 1u;
+    uint32_t tma_phase = 0u;
+    if (lane == 0) mbar_init(&W.bar, 1u);
+    __syncwarp();
 
     for (;;) {
         int gid = 0;
@@ -602,42 +725,76 @@ k_group(SearchArgs a) {
                 lc.cands += (lane == 0) ? total : 0;
                 for (int t0 = 0; t0 < total; t0 += TCAP) {
                     const int nt = min(TCAP, total - t0);
-                    for (int t = lane; t < nt; t += 32) {
-                        int gt = t0 + t;
-                        int lo = 0, hi = nr;   // largest e with rpre[e] <= gt
+                    // first range reaching into this tile
+                    int e0 = 0;
+                    {
+                        int lo = 0, hi = nr;
                         while (hi - lo > 1) {
                             int mid = (lo + hi) >> 1;
-                            if (W.rpre[mid] <= gt) lo = mid; else hi = mid;
+                            if (W.rpre[mid] <= t0) lo = mid; else hi = mid;
                         }
-                        int rank = W.ranges[lo].x + (gt - W.rpre[lo]);
-                        if (kSup) {
-                            if (MODE == kSupFill) {
-                                int64_t p = sup_pos + sup_n + gt;
-                                if (p < a.x_cap) a.x_idx[p] = a.perm[rank];
-                                else atomicOr(a.err, kErrCap);
+                        e0 = lo;
+                    }
+                    if (kSup) {
+                        if (MODE == kSupFill) {
+                            for (int e = e0 + (lane >> 4); e < nr; e += 2) {
+                                const int rb = W.rpre[e];
+                                if (rb >= t0 + nt) break;
+                                const int2 R = W.ranges[e];
+                                const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
+                                for (int gt = lo + (lane & 15); gt < hi; gt += 16) {
+                                    int64_t p = sup_pos + sup_n + gt;
+                                    if (p < a.x_cap) a.x_idx[p] = a.perm[R.x + (gt - rb)];
+                                    else atomicOr(a.err, kErrCap);
+                                }
                             }
-                            continue;
                         }
-                        uint4 P = a.pfix[rank];
-                        float4 O = a.poff[rank];
-                        float4 rel = make_float4(rel_coord(P.x, O.x, cx), rel_coord(P.y, O.y, cy),
-                                                 rel_coord(P.z, O.z, cz), O.w);
-                        if constexpr (KIND == 0) {
-                            T.p[t] = rel;
-                            T.r[t] = rank;
-                        } else {
-                            float4 H0 = a.hyd0[rank], H1 = a.hyd1[rank];
-                            T.p[t] = rel;
-                            T.h[t] = make_float4(__uint_as_float(P.w), H1.z, H1.w, H1.x);
-                            T.v[t] = H0;
-                            T.rho[t] = H1.y;
-                            T.r[t] = rank;
+                        continue;
+                    }
+                    // the tile's piece of every range: one bulk copy per SoA array, by one lane
+                    constexpr uint32_t kBytesPer = (KIND == 0) ? 32u : 64u;
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * kBytesPer);
+                    __syncwarp();
+                    for (int e = e0 + lane; e < nr; e += 32) {
+                        const int rb = W.rpre[e];
+                        if (rb >= t0 + nt) break;
+                        const int2 R = W.ranges[e];
+                        const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
+                        const int src = R.x + (lo - rb), dst = lo - t0, cnt = hi - lo;
+                        bulk_to_smem(&T.p[dst], a.pfix + src, (uint32_t)cnt * 16u, &W.bar);
+                        bulk_to_smem(&T.o[dst], a.poff + src, (uint32_t)cnt * 16u, &W.bar);
+                        if constexpr (KIND == 1) {
+                            bulk_to_smem(&T.v[dst], a.hyd0 + src, (uint32_t)cnt * 16u, &W.bar);
+                            bulk_to_smem(&T.h[dst], a.hyd1 + src, (uint32_t)cnt * 16u, &W.bar);
                         }
+                        for (int k = 0; k < cnt; ++k) T.r[dst + k] = src + k;
+                    }
+                    if (!mbar_wait_bounded(&W.bar, tma_phase, a.err)) mbar_wait_bounded(&W.bar, tma_phase, a.err);
+                    tma_phase ^= 1u;
+                    // in place: fixed point -> coordinates relative to the centre
+                    for (int t = lane; t < nt; t += 32) {
+                        const uint4 P = *reinterpret_cast<const uint4*>(&T.p[t]);
+                        const float4 O = T.o[t];
+                        const float px = rel_coord(P.x, O.x, cx), py = rel_coord(P.y, O.y, cy),
+                                    pz = rel_coord(P.z, O.z, cz);
+                        T.p[t] = make_float4(px, py, pz, fmaf(px, px, fmaf(py, py, pz * pz)));
+                        if constexpr (KIND == 1) {
+                            const float hj = __uint_as_float(P.w);
+                            T.o[t] = make_float4(hj * hj, O.w, 0.0f, 0.0f);
+                        }
+                    }
+                    {
+                        // NaN dummies up to whole chunks of 32 in every slice
+                        const int padded = L.S * ((((nt + L.S - 1) / L.S) + 31) >> 5) * 32;
+                        const float nanv = __int_as_float(0x7fffffff);
+                        for (int t = nt + lane; t < padded; t += 32) T.p[t] = make_float4(nanv, nanv, nanv, nanv);
                     }
                     __syncwarp();
                     if (!kSup) {
-                        if (wrap_safe) filter_tile<KIND, MODE, M, false>(T, L, dm, hm, nt, a, lc);
-                        else filter_tile<KIND, MODE, M, true>(T, L, dm, hm, nt, a, lc);
+                        if (wrap_safe) filter_tile<KIND, MODE, M, false>(T, L, dm, hm, nt, a, lc, lane);
+                        else filter_tile<KIND, MODE, M, true>(T, L, dm, hm, nt, a, lc, lane);
                     }
                     __syncwarp();
                 }
@@ -650,6 +807,8 @@ k_group(SearchArgs a) {
         lc.max_stack = max(lc.max_stack, 0);
 
         // ---- results
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) lc.pairs += (KIND == 0) ? dm[mm].n : hm[mm].n;
         if (kSup) {
             if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
             continue;
@@ -756,9 +915,7 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
                         float4 rel = make_float4(rel_coord(Q.x, O.x, cx), rel_coord(Q.y, O.y, cy),
                                                  rel_coord(Q.z, O.z, cz), O.w);
                         if (KIND == 0) {
-                            float dx = rel.x - dm.mx, dy = rel.y - dm.my, dz = rel.z - dm.mz;
-                            float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            if (r2 < dm.h2hi) density_pair<MODE>(dm, a, rel, q, lc);
+                            density_pair<MODE>(dm, a, rel, O.w, q, lc);
                         } else {
                             float hj = __uint_as_float(Q.w);
                             float dx = rel.x - hm.mx, dy = rel.y - hm.my, dz = rel.z - hm.mz;
@@ -766,9 +923,13 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
                             float thr = fmaf(fmaxf(hm.h2, hj * hj), 1.0f + 3.0f * kBandRel, hm.bk);
                             if (r2 < thr) {
                                 float4 H0 = a.hyd0[q], H1 = a.hyd1[q];
-                                hydro_pair<MODE>(hm, a, rel, make_float4(hj, H1.z, H1.w, H1.x), H0, H1.y, q, lc);
+                                hydro_pair<MODE>(hm, a, rel, make_float4(hj * hj, O.w, 0.0f, 0.0f), H0, H1, q, lc);
                             }
                         }
+                    }
+                    if (MODE == kAcc) {
+                        if (KIND == 0) dflush(dm);
+                        else hflush(hm);
                     }
                     node = lk.w;
                 } else {
@@ -778,6 +939,7 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
                 node = lk.w;
             }
         }
+        lc.pairs += (KIND == 0) ? dm.n : hm.n;
         if (KIND == 0) {
             if (MODE == kAcc) {
                 a.o_s0[rank] = dm.s0 - dm.c0;

@@ -62,6 +62,7 @@ enum ErrBits : unsigned {
     kErrNodes = 4u,      // node capacity exceeded
     kErrCap = 8u,        // export capacity exceeded
     kErrH = 16u,         // smoothing length outside (0, 0.5)
+    kErrTimeout = 64u,   // a bounded device-side wait gave up
 };
 
 struct Ctx {
