@@ -208,6 +208,27 @@ int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out);
 int sphgrp_get_launch_log(sphgrp_ctx* ctx, int cap, int64_t* members, int64_t* candidates,
                           int64_t* pair_tests, int64_t* nodes, double* ms, int* count);
 
+/* Keys + stable sort (as sphgrp_sfc_keys_sort) without any device allocation, for
+ * callers that may not call cudaMalloc / cudaFree: plug-ins whose host application
+ * owns all device memory through its own pool, and latency-critical paths that cannot
+ * take the implicit device synchronisation of an allocation.  The paper has no
+ * counterpart; this is a deployment variant of the a1 + a2 step.
+ * The sort's scratch lives in one fixed-size __device__ array inside the library
+ * (about 6.3 MB, held on every GPU that loads the library until the process exits),
+ * so n may not exceed SPHGRP_STATIC_SORT_MAX_N (EINVAL otherwise).
+ * pos:      device, n x 3 FP64 in [0,1).
+ * keys_out: device, n uint64, receives the sorted keys (also used as sort scratch).
+ * perm_out: device, n int32, receives rank -> original index (also used as scratch).
+ * No context is involved and nothing is kept for later calls.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the one
+ * array: calls whose work overlaps on the GPU (different streams, or different host
+ * threads without ordering) race and give wrong results; serialise them.  Returns
+ * after synchronising the stream (the range check is read back). */
+#define SPHGRP_STATIC_SORT_MAX_N (1 << 19)
+int sphgrp_sfc_keys_sort_static(int64_t n, const double* pos, uint64_t* keys_out,
+                                int32_t* perm_out, cudaStream_t stream);
+
 /* Number of CUDA kernels the library has launched in this process so far (all
  * contexts, all threads).  Diagnostics only; no device work. */
 int sphgrp_kernel_launches(int64_t* count);

@@ -31,6 +31,7 @@ EXPORTED = [
     "sphgrp_get_stats",
     "sphgrp_kernel_launches",
     "sphgrp_get_launch_log",
+    "sphgrp_sfc_keys_sort_static",
 ]
 
 _ERRORS = {
@@ -106,6 +107,7 @@ def load_library():
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     L.sphgrp_kernel_launches.argtypes = [ctypes.POINTER(I64)]
     L.sphgrp_get_launch_log.argtypes = [P, I32, P, P, P, P, P, ctypes.POINTER(I32)]
+    L.sphgrp_sfc_keys_sort_static.argtypes = [I64, P, P, P, P]
     for name in EXPORTED:
         if name not in ("sphgrp_default_params", "sphgrp_last_error"):
             getattr(L, name).restype = I32

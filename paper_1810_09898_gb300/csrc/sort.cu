@@ -309,4 +309,35 @@ int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s) {
     return check_cuda(cudaGetLastError(), "sort");
 }
 
+// The same keys + stable radix sort on caller-provided buffers: the sorted keys and
+// the permutation end in keys_out / perm_out (which also serve as one ping-pong pair;
+// eight passes return to them), keys_alt / perm_alt are the other pair, hist holds
+// 256 * ceil(n / 2048) counters and scan_aux the scan's block sums (scan_aux_words
+// entries).  err receives the range-check flag.  No allocation.
+int sort_keys_scratch(int64_t n, const double* pos, uint64_t* keys_out, int32_t* perm_out,
+                      uint64_t* keys_alt, int32_t* perm_alt, uint32_t* hist, int32_t* scan_aux,
+                      int64_t scan_aux_words, unsigned* err, cudaStream_t s) {
+    const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    const int64_t nh = (int64_t)256 * nblocks;
+    if (scan_aux_need(nh) > scan_aux_words) return set_error(SPHGRP_EOVERFLOW, "scan scratch too small");
+    k_keys<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, keys_out, err);
+    note_launch();
+    uint64_t* kbuf[2] = {keys_out, keys_alt};
+    int32_t* vbuf[2] = {perm_out, perm_alt};
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        uint64_t* kin = kbuf[pass & 1];
+        uint64_t* kout = kbuf[(pass + 1) & 1];
+        const int32_t* vin = pass == 0 ? nullptr : vbuf[pass & 1];
+        int32_t* vout = vbuf[(pass + 1) & 1];
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, n, shift, hist, nblocks);
+        note_launch();
+        scan_rec<int32_t>(reinterpret_cast<const int32_t*>(hist), reinterpret_cast<int32_t*>(hist), nh,
+                          scan_aux, nullptr, s);
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
+        note_launch();
+    }
+    return check_cuda(cudaGetLastError(), "sort (caller buffers)");
+}
+
 }  // namespace sphgrp
