@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-individual", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-pass", action="store_true",
+                    help="after set-up run one grouped and one per-particle density+hydro pass inside "
+                         "the NVTX range 'pass' (for ncu --nvtx-include pass/) and exit")
     return ap.parse_args()
 
 
@@ -345,10 +348,28 @@ def roofline(collect, peak_gbs):
                   "pairs_per_member": v["pairs"] / max(1, v["members"]),
                   "members_per_walk": v["members"] / max(1, v["walks"]),
                   "nodes_per_walk": v["nodes"] / max(1, v["walks"])} for k, v in agg.items()}
+    traffic = measured_traffic(dom, A["members"] / max(1, A["launches"]))
     return {"bound": "hbm", "kernel": f"k_group ({dom})", "achieved": achieved, "peak": peak_gbs,
-            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
             "bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}, detail
+
+
+def measured_traffic(kind: str, members_per_launch: float):
+    """DRAM bytes per launch from the last ncu capture of the search kernel (recorded per
+    member in profiles/traffic.json), scaled to the units one launch processes; None when
+    the kernel source changed since the capture."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, rec["kernel_source"]), "rb").read()
+    except (OSError, KeyError, ValueError):
+        return None
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("kernel_source_sha256_16"):
+        return None
+    per = rec.get(f"{kind}_dram_bytes_per_member")
+    return None if per is None else per * members_per_launch
 
 
 def measured_peak_hbm() -> float:
@@ -376,6 +397,16 @@ def run_ours(a):
     P = Problem(a, rank)
     sg = P.sg
     g = a.group
+    if a.profile_pass:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("pass")
+        for mode, gs in ((sg.GROUPED, g), (sg.INDIVIDUAL, 1)):
+            P.ctx.density(P.act, P.h, 0, mode, gs, P.rho, P.drho, P.f, P.nn)
+            P.ctx.hydro_force(P.act, P.h, P.rho, P.f, P.vel, P.u, mode, gs, P.acc, P.dudt, P.nnh)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_pass": "done", "n": P.n}))
+        return
     steps, warmup = a.steps, max(3, a.warmup)
 
     with ClockSampler(torch.cuda.current_device()) as clk:

@@ -22,7 +22,7 @@ namespace sphgrp {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kStackCap = 512;
 constexpr int kRangeCap = 96;
-constexpr int kTileD = 256;   // density tile (candidates)
+constexpr int kTileD = 128;   // density tile (candidates)
 constexpr int kTileH = 128;   // hydro tile
 
 struct LocalCounters {
@@ -757,19 +757,49 @@ k_group(SearchArgs a) {
                     __syncwarp();
                     if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * kBytesPer);
                     __syncwarp();
-                    for (int e = e0 + lane; e < nr; e += 32) {
-                        const int rb = W.rpre[e];
-                        if (rb >= t0 + nt) break;
-                        const int2 R = W.ranges[e];
-                        const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
-                        const int src = R.x + (lo - rb), dst = lo - t0, cnt = hi - lo;
-                        bulk_to_smem(&T.p[dst], a.pfix + src, (uint32_t)cnt * 16u, &W.bar);
-                        bulk_to_smem(&T.o[dst], a.poff + src, (uint32_t)cnt * 16u, &W.bar);
-                        if constexpr (KIND == 1) {
-                            bulk_to_smem(&T.v[dst], a.hyd0 + src, (uint32_t)cnt * 16u, &W.bar);
-                            bulk_to_smem(&T.h[dst], a.hyd1 + src, (uint32_t)cnt * 16u, &W.bar);
+                    // Ranges adjacent in memory (consecutive leaves of the walk usually are)
+                    // are merged into one copy: the first range of a run (or of a 32-range
+                    // chunk) issues the copy of the whole run.
+                    for (int eb = e0; eb < nr; eb += 32) {
+                        const int e = eb + lane;
+                        int rb = 0, src = 0, dst = 0, cnt = 0;
+                        bool valid = false, cont = false;
+                        if (e < nr) {
+                            rb = W.rpre[e];
+                            valid = rb < t0 + nt;
                         }
-                        for (int k = 0; k < cnt; ++k) T.r[dst + k] = src + k;
+                        if (valid) {
+                            const int2 R = W.ranges[e];
+                            const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
+                            src = R.x + (lo - rb);
+                            dst = lo - t0;
+                            cnt = hi - lo;
+                            if (lane > 0 && e > e0) {
+                                const int2 Q = W.ranges[e - 1];
+                                cont = Q.x + Q.y == R.x;
+                            }
+                            for (int k = 0; k < cnt; ++k) T.r[dst + k] = src + k;
+                        }
+                        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                        if (vmask == 0u) break;
+                        const bool head = valid && !cont;
+                        const unsigned hmask = __ballot_sync(0xffffffffu, head);
+                        const int last = 31 - __clz(vmask);
+                        const int chunk_end = __shfl_sync(0xffffffffu, dst + cnt, last);
+                        const unsigned above = (lane == 31) ? 0u : (hmask >> (lane + 1)) << (lane + 1);
+                        const int nxt = above ? __ffs(above) - 1 : 0;
+                        const int nxt_dst = __shfl_sync(0xffffffffu, dst, nxt);
+                        if (head) {
+                            const int run = (above ? nxt_dst : chunk_end) - dst;
+                            const uint32_t bytes = (uint32_t)run * 16u;
+                            bulk_to_smem(&T.p[dst], a.pfix + src, bytes, &W.bar);
+                            bulk_to_smem(&T.o[dst], a.poff + src, bytes, &W.bar);
+                            if constexpr (KIND == 1) {
+                                bulk_to_smem(&T.v[dst], a.hyd0 + src, bytes, &W.bar);
+                                bulk_to_smem(&T.h[dst], a.hyd1 + src, bytes, &W.bar);
+                            }
+                        }
+                        if (vmask != 0xffffffffu) break;
                     }
                     if (!mbar_wait_bounded(&W.bar, tma_phase, a.err)) mbar_wait_bounded(&W.bar, tma_phase, a.err);
                     tma_phase ^= 1u;
