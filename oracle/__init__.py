@@ -58,6 +58,10 @@ def lib():
             L.orc_hydro.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, dbl, dbl, dbl,
                                     dbl, i32, P, P, P, P, P]
             L.orc_threads.argtypes = []
+            L.orc_h_exact.argtypes = [i64, P, P, P, P, P, dbl, i32]
+            L.orc_loss_grad.argtypes = [i64, P, P, P, P, P, P, P, P, P, dbl, dbl, dbl, dbl, dbl, i32,
+                                        P, P, P, P]
+            L.orc_grad_dual.argtypes = [i64, P, P, P, P, P, P, P, P, P, dbl, dbl, dbl, dbl, dbl, P, P, P]
             _lib = L
     return _lib
 
@@ -183,3 +187,43 @@ def hydro(pos, vel, m, h, rho, f, u, targets=None, gamma=5.0 / 3.0, alpha=1.0, b
                     _p(u), nt, _p(t), gamma, alpha, beta, eps, int(use_tree), _p(ax), _p(ay),
                     _p(az), _p(dudt), _p(nn))
     return {"acc": np.stack([ax, ay, az], axis=1), "dudt": dudt, "nngb": nn}
+
+
+# ----------------------------------------------------------------------------- backward
+
+def h_exact(pos, m, h, nngb=64.0, use_tree=True):
+    """Smoothing lengths satisfying (4 pi/3) h^3 rho = nngb m exactly (from the given h)."""
+    x, y, z = _xyz(pos)
+    hh = _f64(np.array(h, dtype=np.float64, copy=True))
+    lib().orc_h_exact(len(x), _p(x), _p(y), _p(z), _p(_f64(m)), _p(hh), nngb, int(use_tree))
+    return hh
+
+
+def loss_grad(pos, vel, m, u, h, w, s, nngb=64.0, gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps=0.01,
+              use_tree=True):
+    """L = sum w.a + sum s rho and dL/d(pos, vel, m) by the hand-written FP64 adjoint
+    (h must satisfy the exact constraint, see h_exact)."""
+    x, y, z = _xyz(pos)
+    n = len(x)
+    v = _f64(np.asarray(vel).reshape(n, 3))
+    w = _f64(np.asarray(w).reshape(n, 3))
+    loss = np.zeros(1)
+    gx, gv = np.zeros((n, 3)), np.zeros((n, 3))
+    gm = np.zeros(n)
+    lib().orc_loss_grad(n, _p(x), _p(y), _p(z), _p(v), _p(_f64(m)), _p(_f64(u)), _p(_f64(h)), _p(w),
+                        _p(_f64(s)), nngb, gamma, alpha, beta, eps, int(use_tree), _p(loss), _p(gx),
+                        _p(gv), _p(gm))
+    return float(loss[0]), gx, gv, gm
+
+
+def grad_dual(pos, vel, m, u, h, w, s, nngb=64.0, gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps=0.01):
+    """The same gradient by forward-mode dual numbers (small n: one pass per input)."""
+    x, y, z = _xyz(pos)
+    n = len(x)
+    v = _f64(np.asarray(vel).reshape(n, 3))
+    w = _f64(np.asarray(w).reshape(n, 3))
+    gx, gv = np.zeros((n, 3)), np.zeros((n, 3))
+    gm = np.zeros(n)
+    lib().orc_grad_dual(n, _p(x), _p(y), _p(z), _p(v), _p(_f64(m)), _p(_f64(u)), _p(_f64(h)), _p(w),
+                        _p(_f64(s)), nngb, gamma, alpha, beta, eps, _p(gx), _p(gv), _p(gm))
+    return gx, gv, gm

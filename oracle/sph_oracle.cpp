@@ -574,3 +574,390 @@ int orc_hydro(int64_t n, const double* x, const double* y, const double* z,
 int orc_threads(void) { return n_threads(); }
 
 }  // extern "C"
+
+// =================================================================================
+// Backward (adjoint) of L = sum_i w_i . a_i + sum_i s_i rho_i with respect to the
+// positions, velocities and masses (the method's differentiated form; the paper has
+// no backward pass).  Neighbour sets are those of the given state; the smoothing
+// lengths are defined by the exact constraint G_i = (4 pi / 3) h_i^3 rho_i - N m_i = 0
+// (solved here to |G| <= 1e-13 N m), so h_i(x, m) enters through the implicit
+// function theorem; f_i enters through rho_i, dRho_i/dh_i and h_i.
+// =================================================================================
+
+namespace {
+
+// M4 kernel with the derivatives the adjoint needs:
+//   W, W_r, W_rr, W_h, W_rh, W_hh  (r = distance, h = support)
+struct K2 { double w, wr, wrr, wh, wrh, whh; };
+
+K2 m4_full(double r, double h) {
+    K2 k{0, 0, 0, 0, 0, 0};
+    double q = r / h;
+    if (q >= 1.0) return k;
+    double sigma = 8.0 / (kPi * h * h * h);
+    double w, w1, w2;  // w(q), w'(q), w''(q)
+    if (q <= 0.5) {
+        w = 1.0 - 6.0 * q * q + 6.0 * q * q * q;
+        w1 = -12.0 * q + 18.0 * q * q;
+        w2 = -12.0 + 36.0 * q;
+    } else {
+        double u = 1.0 - q;
+        w = 2.0 * u * u * u;
+        w1 = -6.0 * u * u;
+        w2 = 12.0 * u;
+    }
+    k.w = sigma * w;
+    k.wr = sigma * w1 / h;
+    k.wrr = sigma * w2 / (h * h);
+    k.wh = -sigma / h * (3.0 * w + q * w1);
+    k.wrh = -sigma / (h * h) * (4.0 * w1 + q * w2);
+    k.whh = sigma / (h * h) * (12.0 * w + 8.0 * q * w1 + q * q * w2);
+    return k;
+}
+
+struct PairList {
+    std::vector<int64_t> off;
+    std::vector<int32_t> idx;
+};
+
+// hydro neighbour lists of all particles (j != i, |r| < max(h_i, h_j)), ascending
+PairList hydro_lists(const Particles& P, const double* h, bool use_tree) {
+    Tree tree;
+    if (use_tree) build_tree(tree, P.n, P.x, P.y, P.z, h);
+    std::vector<std::vector<int32_t>> lists(P.n);
+    parallel_for(P.n, [&](int64_t i) {
+        std::vector<int32_t> cand, out;
+        neighbours(P, h, use_tree ? &tree : nullptr, i, 1, cand, out);
+        lists[i] = out;
+    });
+    PairList L;
+    L.off.assign(P.n + 1, 0);
+    for (int64_t i = 0; i < P.n; ++i) L.off[i + 1] = L.off[i] + (int64_t)lists[i].size();
+    L.idx.resize(L.off[P.n]);
+    for (int64_t i = 0; i < P.n; ++i) std::copy(lists[i].begin(), lists[i].end(), L.idx.begin() + L.off[i]);
+    return L;
+}
+
+// rho, dRho/dh, d2Rho/dh2 at h_i over the density set (j with |r| < h_i, i included);
+// every such j is i itself or in i's hydro list.
+void density3(const Particles& P, const double* m, const double* h, const PairList& L, int64_t i,
+              double& rho, double& rh, double& rhh) {
+    K2 self = m4_full(0.0, h[i]);
+    rho = m[i] * self.w;
+    rh = m[i] * self.wh;
+    rhh = m[i] * self.whh;
+    for (int64_t e = L.off[i]; e < L.off[i + 1]; ++e) {
+        int32_t j = L.idx[e];
+        double dx, dy, dz;
+        double r2 = dist2(P.x, P.y, P.z, i, j, dx, dy, dz);
+        if (!(r2 < h[i] * h[i])) continue;
+        K2 k = m4_full(std::sqrt(r2), h[i]);
+        rho += m[j] * k.w;
+        rh += m[j] * k.wh;
+        rhh += m[j] * k.whh;
+    }
+}
+
+// Newton on G(h) = (4 pi/3) h^3 rho(h) - N m at a fixed neighbour list (the lists of
+// the given state; W and W_h vanish at the support edge, so the solution is smooth in
+// the pair distances).
+double solve_h_exact(const Particles& P, const double* m, double* h, const PairList& L, int64_t i,
+                     double nngb) {
+    double hh = h[i];
+    for (int it = 0; it < 60; ++it) {
+        double rho, rh, rhh;
+        double saved = h[i];
+        h[i] = hh;
+        density3(P, m, h, L, i, rho, rh, rhh);
+        h[i] = saved;
+        double g = 4.0 * kPi / 3.0 * hh * hh * hh * rho - nngb * m[i];
+        double gp = 4.0 * kPi * hh * hh * rho + 4.0 * kPi / 3.0 * hh * hh * hh * rh;
+        double step = g / gp;
+        hh -= step;
+        if (std::fabs(step) <= 1e-15 * hh) break;
+    }
+    return hh;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Solves the exact constraint for every particle, starting from h (overwritten),
+// with the hydro neighbour lists of the starting h held fixed.
+int orc_h_exact(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                double* h, double nngb, int use_tree) {
+    Particles P{n, x, y, z};
+    std::vector<double> out(n);
+    // a few rounds: lists at the current h, exact solve, repeat until the lists hold
+    for (int round = 0; round < 4; ++round) {
+        PairList L = hydro_lists(P, h, use_tree != 0);
+        parallel_for(n, [&](int64_t i) { out[i] = solve_h_exact(P, m, h, L, i, nngb); });
+        for (int64_t i = 0; i < n; ++i) h[i] = out[i];
+    }
+    return 0;
+}
+
+// Loss and its gradient.  h: smoothing lengths satisfying the exact constraint (see
+// orc_h_exact); w: n x 3 weights of the accelerations, s: n weights of the densities.
+// Outputs: loss (scalar), gx (n x 3), gv (n x 3), gm (n).
+int orc_loss_grad(int64_t n, const double* x, const double* y, const double* z, const double* vel,
+                  const double* m, const double* u, const double* h, const double* w, const double* s,
+                  double nngb, double gamma, double alpha, double beta, double eps, int use_tree,
+                  double* loss, double* gx, double* gv, double* gm) {
+    Particles P{n, x, y, z};
+    PairList L = hydro_lists(P, h, use_tree != 0);
+    std::vector<double> rho(n), rh(n), rhh(n), f(n), A(n), c(n);
+    parallel_for(n, [&](int64_t i) {
+        density3(P, m, h, L, i, rho[i], rh[i], rhh[i]);
+        f[i] = 1.0 / (1.0 + h[i] * rh[i] / (3.0 * rho[i]));
+        A[i] = f[i] * (gamma - 1.0) * u[i] / rho[i];
+        c[i] = std::sqrt(gamma * (gamma - 1.0) * u[i]);
+    });
+    // forward accelerations (for the loss value)
+    std::vector<double> lossi(n, 0.0);
+    // adjoints
+    std::vector<double> hb(n, 0.0), rb(n, 0.0), Ab(n, 0.0);
+    parallel_for(n, [&](int64_t k) {
+        double acc[3] = {0, 0, 0}, xb[3] = {0, 0, 0}, vb[3] = {0, 0, 0};
+        double mb = 0.0, hbk = 0.0, rbk = 0.0, Abk = 0.0;
+        const double* wk = w + 3 * k;
+        for (int64_t e = L.off[k]; e < L.off[k + 1]; ++e) {
+            int32_t j = L.idx[e];
+            double dx, dy, dz;
+            double r2 = dist2(x, y, z, k, j, dx, dy, dz);
+            if (r2 == 0.0) continue;
+            double r = std::sqrt(r2);
+            double D[3] = {-dx, -dy, -dz};  // x_k - x_j
+            double rhat[3] = {D[0] / r, D[1] / r, D[2] / r};
+            K2 kk = m4_full(r, h[k]), kj = m4_full(r, h[j]);
+            double v[3] = {vel[3 * k] - vel[3 * j], vel[3 * k + 1] - vel[3 * j + 1], vel[3 * k + 2] - vel[3 * j + 2]};
+            double vr = v[0] * D[0] + v[1] * D[1] + v[2] * D[2];
+            double hbar = 0.5 * (h[k] + h[j]);
+            double Dn = r2 + eps * hbar * hbar;
+            double cbar = 0.5 * (c[k] + c[j]), rbar = 0.5 * (rho[k] + rho[j]);
+            double mu = 0.0, Pi = 0.0, Pmu = 0.0;
+            if (vr < 0.0) {
+                mu = hbar * vr / Dn;
+                Pi = (-alpha * cbar * mu + beta * mu * mu) / rbar;
+                Pmu = (-alpha * cbar + 2.0 * beta * mu) / rbar;
+            }
+            double sdw = kk.wr + kj.wr;
+            double B = A[k] * kk.wr + A[j] * kj.wr + Pi * 0.5 * sdw;
+            const double* wj = w + 3 * j;
+            double U[3], Q = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                U[a] = m[j] * wk[a] - m[k] * wj[a];
+                Q += rhat[a] * U[a];
+            }
+            // forward: a_k += -m_j B rhat
+            for (int a = 0; a < 3; ++a) acc[a] -= m[j] * B * rhat[a];
+            // dE/d(.) with E = -B Q
+            double rw = rhat[0] * wj[0] + rhat[1] * wj[1] + rhat[2] * wj[2];
+            mb += B * rw;
+            Abk += -Q * kk.wr;
+            double dmu_dh = (vr < 0.0) ? 0.5 * vr * (r2 - eps * hbar * hbar) / (Dn * Dn) : 0.0;
+            hbk += -Q * (A[k] * kk.wrh + Pi * 0.5 * kk.wrh + 0.5 * sdw * Pmu * dmu_dh);
+            rbk += Q * Pi * sdw / (4.0 * rbar);
+            if (vr < 0.0)
+                for (int a = 0; a < 3; ++a) vb[a] += -Q * 0.5 * sdw * Pmu * hbar * D[a] / Dn;
+            double dBr = A[k] * kk.wrr + A[j] * kj.wrr + Pi * 0.5 * (kk.wrr + kj.wrr);
+            for (int a = 0; a < 3; ++a) {
+                double dmu = (vr < 0.0) ? hbar * v[a] / Dn - 2.0 * hbar * vr * D[a] / (Dn * Dn) : 0.0;
+                double dB = dBr * rhat[a] + 0.5 * sdw * Pmu * dmu;
+                double dQ = (U[a] - Q * rhat[a]) / r;
+                xb[a] += -Q * dB - B * dQ;
+            }
+        }
+        lossi[k] = wk[0] * acc[0] + wk[1] * acc[1] + wk[2] * acc[2] + s[k] * rho[k];
+        for (int a = 0; a < 3; ++a) {
+            gx[3 * k + a] = xb[a];
+            gv[3 * k + a] = vb[a];
+        }
+        gm[k] = mb;
+        hb[k] = hbk;
+        rb[k] = rbk;
+        Ab[k] = Abk;
+    });
+    // per particle: A -> f, rho; f -> h, rho, rho'; rho(h), rho'(h) -> h; implicit h
+    std::vector<double> al(n), be(n);
+    for (int64_t k = 0; k < n; ++k) {
+        double rbk = rb[k] + s[k];
+        double fb = Ab[k] * (gamma - 1.0) * u[k] / rho[k];
+        rbk += -Ab[k] * A[k] / rho[k];
+        double Db = -f[k] * f[k] * fb;
+        double hbk = hb[k] + Db * rh[k] / (3.0 * rho[k]);
+        double rpb = Db * h[k] / (3.0 * rho[k]);
+        rbk += -Db * h[k] * rh[k] / (3.0 * rho[k] * rho[k]);
+        hbk += rbk * rh[k] + rpb * rhh[k];
+        double lam = hbk * f[k] / (4.0 * kPi * h[k] * h[k] * rho[k]);
+        al[k] = rbk - lam * 4.0 * kPi / 3.0 * h[k] * h[k] * h[k];
+        be[k] = rpb;
+        gm[k] += lam * nngb;
+    }
+    // density gather: rho_i and rho'_i at fixed h over (x, m)
+    parallel_for(n, [&](int64_t k) {
+        double xb[3] = {0, 0, 0};
+        double mb = al[k] * m4_full(0.0, h[k]).w + be[k] * m4_full(0.0, h[k]).wh;
+        for (int64_t e = L.off[k]; e < L.off[k + 1]; ++e) {
+            int32_t j = L.idx[e];
+            double dx, dy, dz;
+            double r2 = dist2(x, y, z, k, j, dx, dy, dz);
+            double r = std::sqrt(r2);
+            K2 kk = m4_full(r, h[k]), kj = m4_full(r, h[j]);
+            if (r2 < h[j] * h[j]) mb += al[j] * kj.w + be[j] * kj.wh;
+            if (r2 == 0.0) continue;
+            double coef = al[k] * m[j] * kk.wr + be[k] * m[j] * kk.wrh + al[j] * m[k] * kj.wr + be[j] * m[k] * kj.wrh;
+            xb[0] += coef * (-dx) / r;
+            xb[1] += coef * (-dy) / r;
+            xb[2] += coef * (-dz) / r;
+        }
+        for (int a = 0; a < 3; ++a) gx[3 * k + a] += xb[a];
+        gm[k] += mb;
+    });
+    double Ls = 0.0;
+    for (int64_t k = 0; k < n; ++k) Ls += lossi[k];
+    *loss = Ls;
+    return 0;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Forward-mode check of the adjoint on small sets: the loss with every quantity a
+// dual number (value, derivative along one seeded input), the exact constraint
+// solved by Newton in dual arithmetic (the derivative part converges to the implicit
+// derivative), neighbour lists fixed.  One pass per seeded input.
+// ---------------------------------------------------------------------------------
+namespace {
+
+struct Dual {
+    double v, d;
+};
+inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+inline Dual operator-(Dual a) { return {-a.v, -a.d}; }
+inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+inline Dual operator/(Dual a, Dual b) { return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)}; }
+inline Dual dsqrt(Dual a) {
+    double s = std::sqrt(a.v);
+    return {s, a.d / (2.0 * s)};
+}
+inline Dual C(double x) { return {x, 0.0}; }
+
+Dual m4_w(Dual r, Dual h) {
+    Dual q = r / h;
+    if (q.v >= 1.0) return C(0.0);
+    Dual sigma = C(8.0 / kPi) / (h * h * h);
+    if (q.v <= 0.5) return sigma * (C(1.0) - C(6.0) * q * q + C(6.0) * q * q * q);
+    Dual u = C(1.0) - q;
+    return sigma * C(2.0) * u * u * u;
+}
+
+Dual m4_wr(Dual r, Dual h) {
+    Dual q = r / h;
+    if (q.v >= 1.0) return C(0.0);
+    Dual sigma = C(8.0 / kPi) / (h * h * h);
+    if (q.v <= 0.5) return sigma / h * (C(-12.0) * q + C(18.0) * q * q);
+    Dual u = C(1.0) - q;
+    return sigma / h * (C(-6.0) * u * u);
+}
+
+}  // namespace
+
+extern "C" int orc_grad_dual(int64_t n, const double* x, const double* y, const double* z,
+                             const double* vel, const double* m, const double* u, const double* h0,
+                             const double* w, const double* s, double nngb, double gamma, double alpha,
+                             double beta, double eps, double* gx, double* gv, double* gm) {
+    Particles P{n, x, y, z};
+    PairList L = hydro_lists(P, h0, false);
+    // seeded input t in [0, 7n): 0..3n-1 positions, 3n..6n-1 velocities, 6n..7n-1 masses
+    parallel_for(7 * n, [&](int64_t t) {
+        auto pos = [&](int64_t i, int a) -> Dual {
+            const double* c = a == 0 ? x : (a == 1 ? y : z);
+            return {c[i], (t < 3 * n && t == 3 * i + a) ? 1.0 : 0.0};
+        };
+        auto velo = [&](int64_t i, int a) -> Dual {
+            return {vel[3 * i + a], (t >= 3 * n && t < 6 * n && t - 3 * n == 3 * i + a) ? 1.0 : 0.0};
+        };
+        auto mass = [&](int64_t i) -> Dual { return {m[i], (t >= 6 * n && t - 6 * n == i) ? 1.0 : 0.0}; };
+        auto dvec = [&](int64_t i, int64_t j, Dual* d) {  // x_i - x_j, nearest image (shift from the values)
+            for (int a = 0; a < 3; ++a) {
+                Dual dd = pos(i, a) - pos(j, a);
+                dd.v -= std::nearbyint(dd.v);
+                d[a] = dd;
+            }
+        };
+        std::vector<Dual> h(n), rho(n), f(n), A(n);
+        for (int64_t i = 0; i < n; ++i) {
+            // density as a function of h_i over the fixed lists
+            auto rho_of = [&](Dual hi, Dual& rh) {
+                Dual r0 = mass(i) * m4_w(C(0.0), hi);
+                Dual q0 = C(0.0);
+                rh = C(0.0);
+                // d/dh by a second dual: differentiate W in h numerically-exact via W_h formula
+                auto wh = [&](Dual r, Dual hh) {
+                    Dual q = r / hh;
+                    Dual w = m4_w(r, hh), wr = m4_wr(r, hh);
+                    return C(-3.0) * w / hh - q * wr;
+                };
+                rh = mass(i) * wh(C(0.0), hi);
+                for (int64_t e = L.off[i]; e < L.off[i + 1]; ++e) {
+                    int32_t j = L.idx[e];
+                    Dual d[3];
+                    dvec(i, j, d);
+                    Dual r = dsqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+                    if (!(r.v < hi.v)) continue;
+                    r0 = r0 + mass(j) * m4_w(r, hi);
+                    rh = rh + mass(j) * wh(r, hi);
+                }
+                (void)q0;
+                return r0;
+            };
+            Dual hi = {h0[i], 0.0};
+            Dual rh;
+            for (int it = 0; it < 80; ++it) {
+                Dual r = rho_of(hi, rh);
+                Dual g = C(4.0 * kPi / 3.0) * hi * hi * hi * r - C(nngb) * mass(i);
+                Dual gp = C(4.0 * kPi) * hi * hi * r + C(4.0 * kPi / 3.0) * hi * hi * hi * rh;
+                hi = hi - g / gp;
+            }
+            h[i] = hi;
+            rho[i] = rho_of(hi, rh);
+            f[i] = C(1.0) / (C(1.0) + hi * rh / (C(3.0) * rho[i]));
+            A[i] = f[i] * C((gamma - 1.0) * u[i]) / rho[i];
+        }
+        Dual loss = C(0.0);
+        for (int64_t i = 0; i < n; ++i) {
+            Dual acc[3] = {C(0.0), C(0.0), C(0.0)};
+            double ci = std::sqrt(gamma * (gamma - 1.0) * u[i]);
+            for (int64_t e = L.off[i]; e < L.off[i + 1]; ++e) {
+                int32_t j = L.idx[e];
+                Dual d[3];
+                dvec(i, j, d);
+                Dual r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2.v == 0.0) continue;
+                Dual r = dsqrt(r2);
+                Dual dwi = m4_wr(r, h[i]), dwj = m4_wr(r, h[j]);
+                Dual vr = C(0.0);
+                for (int a = 0; a < 3; ++a) vr = vr + (velo(i, a) - velo(j, a)) * d[a];
+                Dual Pi = C(0.0);
+                if (vr.v < 0.0) {
+                    Dual hb = C(0.5) * (h[i] + h[j]);
+                    Dual mu = hb * vr / (r2 + C(eps) * hb * hb);
+                    double cj = std::sqrt(gamma * (gamma - 1.0) * u[j]);
+                    Dual rb = C(0.5) * (rho[i] + rho[j]);
+                    Pi = (C(-alpha * 0.5 * (ci + cj)) * mu + C(beta) * mu * mu) / rb;
+                }
+                Dual B = A[i] * dwi + A[j] * dwj + Pi * C(0.5) * (dwi + dwj);
+                for (int a = 0; a < 3; ++a) acc[a] = acc[a] - mass(j) * B * d[a] / r;
+            }
+            for (int a = 0; a < 3; ++a) loss = loss + C(w[3 * i + a]) * acc[a];
+            loss = loss + C(s[i]) * rho[i];
+        }
+        if (t < 3 * n) gx[t] = loss.d;
+        else if (t < 6 * n) gv[t - 3 * n] = loss.d;
+        else gm[t - 6 * n] = loss.d;
+    });
+    return 0;
+}
