@@ -197,6 +197,35 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
                        const float* vel, const float* u, int mode, int group_size,
                        float* acc, float* dudt, int32_t* nngb, cudaStream_t stream);
 
+/* a9: backward (adjoint) of the density and the hydro accelerations.  The paper has
+ * no backward pass; this differentiates the a6 and a8 loops above.  For the positions
+ * x and masses m of the last sphgrp_tree_build, and the given h, vel and u, it returns
+ * the gradients with respect to x, v and m of
+ *   L = sum_k g_acc_k . a_k + sum_k g_rho_k rho_k,
+ * where rho_k is the density (a6) at h_k and a_k the hydro acceleration (a8) with
+ * rho, f = 1 / (1 + h dRho/dh / (3 rho)), A = f (gamma - 1) u / rho and
+ * c = sqrt(gamma (gamma - 1) u) taken from that density, and h_k(x, m) is the function
+ * defined by (4 pi / 3) h_k^3 rho_k = nngb m_k (the Sec. 3.2 relation between h, rho
+ * and the neighbour number, imposed exactly) through the given h: its dependence
+ * enters by the implicit function theorem, including that of f through d2Rho/dh2.
+ * The caller passes h satisfying the relation (e.g. sphgrp_density with a small
+ * nngb_tol); for other h the result is the gradient of the relation's solution near h.
+ * Neighbour sets are those of the given state, held fixed.  Every particle takes part
+ * (there is no active list).  Grouped form only: the three pair loops (density sums,
+ * hydro adjoint, density adjoint) walk the tree once per group each and recompute
+ * every pair term from the staged candidates; no pair list is stored.
+ * h:     device, n FP64, 0 < h < 0.5;
+ * vel:   device, n x 3 FP32;  u: device, n FP32 (u >= 0);
+ * g_acc: device, n x 3 FP32 (dL/da);  g_rho: device, n FP32 (dL/drho), or NULL for 0;
+ * g_pos, g_vel: device, n x 3 FP32;  g_m: device, n FP32 -- outputs in original
+ *        order, each may be NULL (not all three).
+ * group_size in [1, 128].  The first call allocates 100 bytes per particle of n_max of
+ * device workspace, kept by the context.  Errors as sphgrp_hydro_force; ESTATE
+ * without a tree. */
+int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* vel, const float* u,
+                    const float* g_acc, const float* g_rho, int group_size, float* g_pos,
+                    float* g_vel, float* g_m, cudaStream_t stream);
+
 /* Counters of the most recent search, density or hydro call. */
 int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out);
 

@@ -19,3 +19,4 @@ from .binding import (  # noqa: F401
     library_path,
     load_library,
 )
+from .autograd import SPHForces, sph_forces  # noqa: F401,E402

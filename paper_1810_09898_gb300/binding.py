@@ -28,6 +28,7 @@ EXPORTED = [
     "sphgrp_group_supersets",
     "sphgrp_density",
     "sphgrp_hydro_force",
+    "sphgrp_backward",
     "sphgrp_get_stats",
     "sphgrp_kernel_launches",
     "sphgrp_get_launch_log",
@@ -104,6 +105,7 @@ def load_library():
                                          ctypes.POINTER(I64), ctypes.POINTER(I64), P]
     L.sphgrp_density.argtypes = [P, I64, P, P, I32, I32, I32, P, P, P, P, P, P]
     L.sphgrp_hydro_force.argtypes = [P, I64, P, P, P, P, P, P, I32, I32, P, P, P, P]
+    L.sphgrp_backward.argtypes = [P, P, P, P, P, P, I32, P, P, P, P]
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     L.sphgrp_kernel_launches.argtypes = [ctypes.POINTER(I64)]
     L.sphgrp_get_launch_log.argtypes = [P, I32, P, P, P, P, P, ctypes.POINTER(I32)]
@@ -211,6 +213,11 @@ class Context:
         _check(self._L.sphgrp_hydro_force(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
                                           _ptr(fgrad), _ptr(vel), _ptr(u), mode, group_size, _ptr(acc),
                                           _ptr(dudt), _ptr(nngb), _stream()))
+
+    # -- a9
+    def backward(self, h, vel, u, g_acc, g_rho, group_size, g_pos=None, g_vel=None, g_m=None):
+        _check(self._L.sphgrp_backward(self._h, _ptr(h), _ptr(vel), _ptr(u), _ptr(g_acc), _ptr(g_rho),
+                                       int(group_size), _ptr(g_pos), _ptr(g_vel), _ptr(g_m), _stream()))
 
     def launch_log(self) -> list:
         import numpy as np

@@ -137,6 +137,10 @@ __global__ void k_members(int nu, const int32_t* __restrict__ U, const int32_t* 
     if (u < nu) out[u] = perm[U[u]];
 }
 
+}  // namespace
+
+namespace sphgrp {
+
 int finish(Ctx* c, cudaStream_t s, int rc) {
     if (rc) return rc;
     unsigned err = 0;
@@ -237,6 +241,8 @@ SearchArgs base_args(Ctx* c) {
     a.h64 = c->h64;
     a.hyd0 = c->hyd0;
     a.hyd1 = c->hyd1;
+    a.wadj = c->wadj;
+    a.dadj = c->dadj;
     a.perm = c->perm;
     a.alpha = (float)c->p.alpha;
     a.beta = (float)c->p.beta;
@@ -259,7 +265,7 @@ int check_common(Ctx* c, int64_t n_act, const int32_t* active, int mode, int gro
     return SPHGRP_OK;
 }
 
-}  // namespace
+}  // namespace sphgrp
 
 extern "C" {
 
@@ -358,6 +364,7 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
                     c->zd, c->pfix, c->poff, c->h64, c->hyd0, c->hyd1, c->act, c->act2, c->flag,
                     c->scan, c->scan_aux, c->lo, c->hi, c->acc_rho, c->acc_drho, c->acc_n,
                     c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
+                    c->acc_s2, c->wadj, c->dadj, c->adj0, c->adj1, c->adj2, c->adj3,
                     c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
                     c->tree.nlevel};
     for (void* p : ptrs)

@@ -1,4 +1,4 @@
-// Neighbour search and the SPH loops that consume it.
+// Neighbour search and the SPH loops that consume it, forward and backward.
 //
 // Two forms (Sec. 2.1 standard search, Sec. 3.1 Neighbour Recycling):
 //  * individual: one thread per active particle walks the octree depth-first with
@@ -7,14 +7,19 @@
 //  * grouped: one warp per group of consecutive active particles (key order).  The
 //    warp walks the octree cooperatively once for the group (32 nodes tested per
 //    step) with the radius that covers every member's sphere, streams the particles
-//    of the opened leaves (the common superset) through shared memory in tiles, and
-//    every member filters the tile down to its own neighbours.
+//    of the opened leaves (the common superset) through shared memory in tiles (TMA
+//    bulk copies), and every member filters the tile down to its own neighbours.
+//
+// The grouped kernel is shared by four kinds of pair loop: density (0), hydro (1),
+// and the adjoints of the hydro accelerations (2) and of the density (3); the two
+// adjoints recompute their pair terms over the same grouped candidate tiles instead
+// of storing pair lists.
 //
 // Pair decisions are taken in FP32 on coordinates relative to a fixed-point centre;
 // pairs whose FP32 r^2 falls inside the proven error band around the threshold are
 // re-decided from the FP64 positions with the oracle's exact arithmetic, so the
-// neighbour sets are those of the FP64 definition.  Sums are FP32 with compensated
-// (Kahan) accumulation.
+// neighbour sets are those of the FP64 definition.  Sums are FP32 (forward sums
+// compensated across tiles).
 #include "search_args.cuh"
 
 namespace sphgrp {
@@ -24,6 +29,7 @@ constexpr int kStackCap = 512;
 constexpr int kRangeCap = 96;
 constexpr int kTileD = 128;   // density tile (candidates)
 constexpr int kTileH = 128;   // hydro tile
+constexpr int kTileA = 128;   // adjoint tiles
 
 struct LocalCounters {
     unsigned long long nodes = 0, cands = 0, tests = 0, pairs = 0, retests = 0;
@@ -70,10 +76,6 @@ __device__ __forceinline__ float radius2_units(float r_box) {
     return __fmul_ru(r, r);
 }
 
-// ---------------------------------------------------------------------------------
-// Per-member state
-// ---------------------------------------------------------------------------------
-
 // Members farther than this many smoothing lengths from the group centre (per axis)
 // evaluate the pair physics from exact fixed-point differences: the FP32 difference of
 // two large centre-relative coordinates would lose up to |m| / h ulps of r.
@@ -83,114 +85,6 @@ constexpr float kPreciseReach = 2.0f;
 __device__ __forceinline__ float fix_diff(uint32_t Xj, float oj, uint32_t Xk, float ok) {
     return (__int2float_rn((int32_t)(Xj - Xk)) + (oj - ok)) * kUnitToBox;
 }
-
-struct DMember {
-    float mx, my, mz;
-    uint32_t X, Y, Z;   // fixed-point position (exact pair differences)
-    float ox, oy, oz;
-    bool precise;       // far from the group centre: physics from exact differences
-    float hinv;
-    float h2lo, h2hi;   // decided-inside below h2lo, candidate below h2hi
-    float thr_dot;      // phase-A threshold of |p|^2 - 2 p.m (= h2hi - |m|^2)
-    int rank;           // -1: slot empty
-    float s0, c0, s1, c1;   // compensated totals
-    float p0, p1;           // plain partial sums of the current tile
-    int n;
-    int64_t xpos;       // export write position
-};
-
-struct HMember {
-    float mx, my, mz;
-    uint32_t X, Y, Z;
-    float ox, oy, oz;
-    bool precise;
-    float h, hinv, sk;  // sk = 8 / (pi h^4): dW/dr = sk * dw/dq
-    float h2, bk;       // h^2 (FP32 of the FP64 square), band offset 8 b |m|^2
-    float bk_dot;       // bk - |m|^2: phase-A offset of the dot form
-    float vx, vy, vz, cs, A, rho;
-    int rank;
-    float sx, cx_, sy, cy_, sz, cz_, su, cu;   // compensated totals
-    float px_, py_, pz_, pu;                   // plain partial sums of the current tile
-    int n;
-    int64_t xpos;
-};
-
-__device__ __forceinline__ void dmember_init(DMember& M, const SearchArgs& a, int rank, uint32_t cx,
-                                             uint32_t cy, uint32_t cz) {
-    M.rank = rank;
-    M.s0 = M.c0 = M.s1 = M.c1 = 0.0f;
-    M.p0 = M.p1 = 0.0f;
-    M.n = 0;
-    M.xpos = 0;
-    M.precise = false;
-    if (rank < 0) {
-        M.mx = M.my = M.mz = 0.0f;
-        M.hinv = 0.0f;
-        M.h2lo = M.h2hi = -1.0f;
-        M.thr_dot = -3.0e38f;
-        return;
-    }
-    uint4 P = a.pfix[rank];
-    float4 O = a.poff[rank];
-    M.mx = rel_coord(P.x, O.x, cx);
-    M.my = rel_coord(P.y, O.y, cy);
-    M.mz = rel_coord(P.z, O.z, cz);
-    M.X = P.x; M.Y = P.y; M.Z = P.z;
-    M.ox = O.x; M.oy = O.y; M.oz = O.z;
-    double h = a.h64[rank];
-    float hf = (float)h;
-    M.hinv = 1.0f / hf;
-    M.precise = fmaxf(fabsf(M.mx), fmaxf(fabsf(M.my), fabsf(M.mz))) > kPreciseReach * hf;
-    float h2 = (float)(h * h);
-    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
-    float bk = 8.0f * kBandRel * m2;
-    M.h2hi = fmaf(h2, 1.0f + 3.0f * kBandRel, bk);
-    M.h2lo = fmaf(h2, 1.0f - 3.0f * kBandRel, -bk);
-    M.thr_dot = M.h2hi - m2;
-}
-
-__device__ __forceinline__ void hmember_init(HMember& M, const SearchArgs& a, int rank, uint32_t cx,
-                                             uint32_t cy, uint32_t cz) {
-    M.rank = rank;
-    M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = M.su = M.cu = 0.0f;
-    M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
-    M.n = 0;
-    M.xpos = 0;
-    M.precise = false;
-    if (rank < 0) {
-        M.mx = M.my = M.mz = 0.0f;
-        M.h = 0.0f; M.hinv = 0.0f; M.sk = 0.0f;
-        M.h2 = -1.0f; M.bk = -1.0f;
-        M.bk_dot = -3.0e38f;
-        M.vx = M.vy = M.vz = M.cs = M.A = M.rho = 0.0f;
-        return;
-    }
-    uint4 P = a.pfix[rank];
-    float4 O = a.poff[rank];
-    M.mx = rel_coord(P.x, O.x, cx);
-    M.my = rel_coord(P.y, O.y, cy);
-    M.mz = rel_coord(P.z, O.z, cz);
-    M.X = P.x; M.Y = P.y; M.Z = P.z;
-    M.ox = O.x; M.oy = O.y; M.oz = O.z;
-    double h = a.h64[rank];
-    M.h = (float)h;
-    M.precise = fmaxf(fabsf(M.mx), fmaxf(fabsf(M.my), fabsf(M.mz))) > kPreciseReach * M.h;
-    float4 H0 = a.hyd0[rank];
-    float4 H1 = a.hyd1[rank];
-    M.hinv = H1.z;
-    M.sk = H1.w;
-    M.h2 = (float)(h * h);
-    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
-    M.bk = 8.0f * kBandRel * m2;
-    M.bk_dot = M.bk - m2;
-    M.vx = H0.x; M.vy = H0.y; M.vz = H0.z; M.cs = H0.w;
-    M.A = H1.x;
-    M.rho = H1.y;
-}
-
-// ---------------------------------------------------------------------------------
-// Pair physics shared by both forms
-// ---------------------------------------------------------------------------------
 
 // Difference of two coordinates relative to one centre.  Both lie in [-1/2, 1/2); when
 // a group can reach half the box (WRAP) the difference is brought back to the nearest
@@ -202,131 +96,15 @@ __device__ __forceinline__ float rel_diff(float p, float m) {
     return d;
 }
 
-// Plain per-tile partial sums are folded into the compensated totals after every
-// tile (or leaf): a few tens of terms in plain FP32, Kahan across blocks.
-__device__ __forceinline__ void dflush(DMember& M) {
-    kahan_add(M.s0, M.c0, M.p0);
-    kahan_add(M.s1, M.c1, M.p1);
-    M.p0 = M.p1 = 0.0f;
+// M4 shape w(q), w'(q), w''(q) (zero for q >= 1)
+__device__ __forceinline__ void m4_shape2(float q, float& w, float& dw, float& d2w) {
+    float u = 1.0f - q;
+    bool inner = q <= 0.5f;
+    w = inner ? fmaf(q * q, 6.0f * q - 6.0f, 1.0f) : 2.0f * u * u * u;
+    dw = inner ? q * (18.0f * q - 12.0f) : -6.0f * u * u;
+    d2w = inner ? fmaf(36.0f, q, -12.0f) : 12.0f * u;
+    if (q >= 1.0f) { w = 0.0f; dw = 0.0f; d2w = 0.0f; }
 }
-
-__device__ __forceinline__ void hflush(HMember& M) {
-    kahan_add(M.sx, M.cx_, M.px_);
-    kahan_add(M.sy, M.cy_, M.py_);
-    kahan_add(M.sz, M.cz_, M.pz_);
-    kahan_add(M.su, M.cu, M.pu);
-    M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
-}
-
-// density pair: p = candidate's coordinates relative to the member's centre, m_j its mass
-template <int MODE, bool WRAP = false>
-__device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, float4 p, float mj, int crank,
-                                             LocalCounters& lc) {
-    float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    bool in = r2 < M.h2lo;
-    if (!in) {
-        if (!(r2 < M.h2hi)) return;
-        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
-        double h = a.h64[M.rank];
-        in = e < __dmul_rn(h, h);
-        lc.retests++;
-    }
-    if (!in) return;
-    M.n++;
-    if (MODE == kAcc) {
-        if (M.precise) {
-            uint4 Q = a.pfix[crank];
-            float4 O = a.poff[crank];
-            dx = fix_diff(Q.x, O.x, M.X, M.ox);
-            dy = fix_diff(Q.y, O.y, M.Y, M.oy);
-            dz = fix_diff(Q.z, O.z, M.Z, M.oz);
-            r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        }
-        float q = r2 * rsqrtf(fmaxf(r2, 1.0e-30f)) * M.hinv;
-        float w, dw;
-        m4_shape(q, w, dw);
-        M.p0 = fmaf(mj, w, M.p0);
-        M.p1 = fmaf(mj, fmaf(q, dw, 3.0f * w), M.p1);
-    } else if (MODE == kFill) {
-        int64_t q = M.xpos++;
-        if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
-        else atomicOr(a.err, kErrCap);
-    }
-}
-
-// hydro pair: p = relative coordinates, q = {h_j^2, m_j, -, -}, v = {vx, vy, vz, c_j},
-// hh = {A_j, rho_j, 1/h_j, s_j}
-template <int MODE, bool WRAP = false>
-__device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 q,
-                                           float4 v, float4 hh, int crank, LocalCounters& lc) {
-    if (crank == M.rank) return;
-    float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float H2 = fmaxf(M.h2, q.x);
-    bool in = r2 < fmaf(H2, 1.0f - 3.0f * kBandRel, -M.bk);
-    if (!in) {
-        if (!(r2 < fmaf(H2, 1.0f + 3.0f * kBandRel, M.bk))) return;
-        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
-        double hi = a.h64[M.rank], hj = a.h64[crank];
-        in = e < fmax(__dmul_rn(hi, hi), __dmul_rn(hj, hj));
-        lc.retests++;
-    }
-    if (!in) return;
-    M.n++;
-    if (MODE == kFill) {
-        int64_t q = M.xpos++;
-        if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
-        else atomicOr(a.err, kErrCap);
-        return;
-    }
-    if (MODE != kAcc) return;
-    if (M.precise) {
-        uint4 Q = a.pfix[crank];
-        float4 O = a.poff[crank];
-        dx = fix_diff(Q.x, O.x, M.X, M.ox);
-        dy = fix_diff(Q.y, O.y, M.Y, M.oy);
-        dz = fix_diff(Q.z, O.z, M.Z, M.oz);
-        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    }
-    if (r2 == 0.0f) return;  // coincident: the kernel gradient vanishes
-    float rinv = rsqrtf(r2);
-    float r = r2 * rinv;
-    float wi, dwi, wj, dwj;
-    m4_shape(r * M.hinv, wi, dwi);
-    m4_shape(r * hh.z, wj, dwj);
-    float dWi = M.sk * dwi;
-    float dWj = hh.w * dwj;
-    float rx = -dx, ry = -dy, rz = -dz;  // r_ij = x_i - x_j
-    float vx = M.vx - v.x, vy = M.vy - v.y, vz = M.vz - v.z;
-    float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
-    float visc = 0.0f;
-    if (vr < 0.0f) {
-        float hb = 0.5f * fmaf(q.x, hh.z, M.h);
-        float mu = hb * vr / fmaf(a.eps * hb, hb, r2);
-        float cb = 0.5f * (M.cs + v.w);
-        float rb = 0.5f * (M.rho + hh.y);
-        visc = fmaf(-a.alpha * cb, mu, a.beta * mu * mu) / rb;
-    }
-    float gbar = 0.5f * (dWi + dWj);
-    float coef = q.y * fmaf(M.A, dWi, fmaf(hh.x, dWj, visc * gbar)) * rinv;
-    M.px_ = fmaf(coef, dx, M.px_);
-    M.py_ = fmaf(coef, dy, M.py_);
-    M.pz_ = fmaf(coef, dz, M.pz_);
-    M.pu = fmaf(q.y * fmaf(M.A, dWi, 0.5f * visc * gbar) * rinv, vr, M.pu);
-}
-
-// ---------------------------------------------------------------------------------
-// Grouped form: one warp per group
-// ---------------------------------------------------------------------------------
-
-struct alignas(16) WalkSmem {
-    unsigned long long bar;      // mbarrier of the tile copies
-    uint32_t stack[kStackCap];   // node ranges: (first child << 3) | (count - 1)
-    int2 ranges[kRangeCap];      // pending leaf ranges (first rank, count)
-    int rpre[kRangeCap + 1];     // prefix of the pending counts
-    int nodes[32];
-};
 
 // ---------------------------------------------------------------------------------
 // TMA bulk copies (global -> shared) completing on an mbarrier
@@ -379,12 +157,190 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint3
     return false;
 }
 
+// ---------------------------------------------------------------------------------
+// Per-member state of the four pair loops
+// ---------------------------------------------------------------------------------
+
+// position part shared by all members: centre-relative coordinates, fixed point
+struct MemberPos {
+    float mx, my, mz;
+    uint32_t X, Y, Z;   // fixed-point position (exact pair differences)
+    float ox, oy, oz;
+    bool precise;       // far from the group centre: physics from exact differences
+    int rank;           // -1: slot empty
+    int n;              // neighbours found
+    int64_t xpos;       // export write position
+};
+
+__device__ __forceinline__ bool pos_init(MemberPos& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                         uint32_t cz, float hf) {
+    M.rank = rank;
+    M.n = 0;
+    M.xpos = 0;
+    M.precise = false;
+    if (rank < 0) {
+        M.mx = M.my = M.mz = 0.0f;
+        M.X = M.Y = M.Z = 0u;
+        M.ox = M.oy = M.oz = 0.0f;
+        return false;
+    }
+    uint4 P = a.pfix[rank];
+    float4 O = a.poff[rank];
+    M.mx = rel_coord(P.x, O.x, cx);
+    M.my = rel_coord(P.y, O.y, cy);
+    M.mz = rel_coord(P.z, O.z, cz);
+    M.X = P.x; M.Y = P.y; M.Z = P.z;
+    M.ox = O.x; M.oy = O.y; M.oz = O.z;
+    M.precise = fmaxf(fabsf(M.mx), fmaxf(fabsf(M.my), fabsf(M.mz))) > kPreciseReach * hf;
+    return true;
+}
+
+// density member
+struct DMember : MemberPos {
+    float hinv;
+    float h2lo, h2hi;   // decided-inside below h2lo, candidate below h2hi
+    float thr_dot;      // phase-A threshold of |p|^2 - 2 p.m (= h2hi - |m|^2)
+    float s0, c0, s1, c1, s2, c2;   // compensated totals: sum m w, sum m (3w + q w'), sum of the W_hh shape
+    float p0, p1, p2;               // plain partial sums of the current tile
+};
+
+// members of the symmetric criterion |r| < max(h_i, h_j) (hydro and both adjoints)
+struct SymMember : MemberPos {
+    float h, hinv, sk;  // sk = 8 / (pi h^4): dW/dr = sk * dw/dq
+    float h2, bk;       // h^2 (FP32 of the FP64 square), band offset 8 b |m|^2
+    float bk_dot;       // bk - |m|^2: phase-A offset of the dot form
+};
+
+struct HMember : SymMember {
+    float vx, vy, vz, cs, A, rho;
+    float sx, cx_, sy, cy_, sz, cz_, su, cu;   // compensated totals
+    float px_, py_, pz_, pu;                   // plain partial sums of the current tile
+};
+
+// hydro-adjoint member: the forward hydro state, the weights w_k = dL/da_k, and the
+// adjoint sums of x, v, m, h, rho and A = f P / rho^2
+struct HAMember : SymMember {
+    float vx, vy, vz, cs, A, rho, m;
+    float wx, wy, wz;
+    float xb[3], vb[3], mb, hb, rb, Ab;
+};
+
+// density-adjoint member: the coefficients alpha = adjoint of rho at fixed h (with the
+// implicit-h term) and beta = adjoint of dRho/dh
+struct DAMember : SymMember {
+    float alpha, beta, m;
+    float xb[3], mb;
+};
+
+__device__ __forceinline__ void member_init(DMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    M.s0 = M.c0 = M.s1 = M.c1 = M.s2 = M.c2 = 0.0f;
+    M.p0 = M.p1 = M.p2 = 0.0f;
+    double h = rank >= 0 ? a.h64[rank] : 1.0;
+    float hf = (float)h;
+    if (!pos_init(M, a, rank, cx, cy, cz, hf)) {
+        M.hinv = 0.0f;
+        M.h2lo = M.h2hi = -1.0f;
+        M.thr_dot = -3.0e38f;
+        return;
+    }
+    M.hinv = 1.0f / hf;
+    float h2 = (float)(h * h);
+    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
+    float bk = 8.0f * kBandRel * m2;
+    M.h2hi = fmaf(h2, 1.0f + 3.0f * kBandRel, bk);
+    M.h2lo = fmaf(h2, 1.0f - 3.0f * kBandRel, -bk);
+    M.thr_dot = M.h2hi - m2;
+}
+
+__device__ __forceinline__ bool sym_init(SymMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                         uint32_t cz) {
+    double h = rank >= 0 ? a.h64[rank] : 1.0;
+    M.h = (float)h;
+    if (!pos_init(M, a, rank, cx, cy, cz, M.h)) {
+        M.h = 0.0f; M.hinv = 0.0f; M.sk = 0.0f;
+        M.h2 = -1.0f; M.bk = -1.0f;
+        M.bk_dot = -3.0e38f;
+        return false;
+    }
+    M.h2 = (float)(h * h);
+    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
+    M.bk = 8.0f * kBandRel * m2;
+    M.bk_dot = M.bk - m2;
+    return true;
+}
+
+__device__ __forceinline__ void member_init(HMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = M.su = M.cu = 0.0f;
+    M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
+    M.vx = M.vy = M.vz = M.cs = M.A = M.rho = 0.0f;
+    if (!sym_init(M, a, rank, cx, cy, cz)) return;
+    float4 H0 = a.hyd0[rank];
+    float4 H1 = a.hyd1[rank];
+    M.hinv = H1.z;
+    M.sk = H1.w;
+    M.vx = H0.x; M.vy = H0.y; M.vz = H0.z; M.cs = H0.w;
+    M.A = H1.x;
+    M.rho = H1.y;
+}
+
+__device__ __forceinline__ void member_init(HAMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    for (int k = 0; k < 3; ++k) M.xb[k] = M.vb[k] = 0.0f;
+    M.mb = M.hb = M.rb = M.Ab = 0.0f;
+    M.vx = M.vy = M.vz = M.cs = M.A = M.rho = M.m = 0.0f;
+    M.wx = M.wy = M.wz = 0.0f;
+    if (!sym_init(M, a, rank, cx, cy, cz)) return;
+    float4 H0 = a.hyd0[rank];
+    float4 H1 = a.hyd1[rank];
+    float4 Wt = a.wadj[rank];
+    M.hinv = H1.z;
+    M.sk = H1.w;
+    M.vx = H0.x; M.vy = H0.y; M.vz = H0.z; M.cs = H0.w;
+    M.A = H1.x;
+    M.rho = H1.y;
+    M.m = a.poff[rank].w;
+    M.wx = Wt.x; M.wy = Wt.y; M.wz = Wt.z;
+}
+
+__device__ __forceinline__ void member_init(DAMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    for (int k = 0; k < 3; ++k) M.xb[k] = 0.0f;
+    M.mb = 0.0f;
+    M.alpha = M.beta = M.m = 0.0f;
+    if (!sym_init(M, a, rank, cx, cy, cz)) return;
+    float4 D = a.dadj[rank];
+    M.alpha = D.x;
+    M.beta = D.y;
+    M.hinv = D.z;
+    M.sk = D.w;
+    M.m = a.poff[rank].w;
+}
+
+// walk radius ingredients: density R_s = max(|m| + h); symmetric R_g = max |m|, hmax_g
+__device__ __forceinline__ void radius_terms(const DMember& M, float& rl, float& hl) {
+    if (M.rank < 0) return;
+    float mr = sqrtf(M.mx * M.mx + M.my * M.my + M.mz * M.mz);
+    rl = fmaxf(rl, mr + 1.0f / M.hinv);
+}
+
+__device__ __forceinline__ void radius_terms(const SymMember& M, float& rl, float& hl) {
+    if (M.rank < 0) return;
+    float mr = sqrtf(M.mx * M.mx + M.my * M.my + M.mz * M.mz);
+    rl = fmaxf(rl, mr);
+    hl = fmaxf(hl, M.h);
+}
+
+// ---------------------------------------------------------------------------------
 // Candidate tiles in shared memory.  The raw key-ordered records of a tile's leaf
 // ranges land here by TMA bulk copies (cp.async.bulk, global -> shared, completion
 // on an mbarrier); the fixed-point positions are then converted in place to FP32
 // coordinates relative to the group centre, {px, py, pz, |p|^2}.  With S slices the
 // lane of slice s filters positions s, s + S, s + 2S, ...; positions beyond the tile's
 // candidates, up to whole chunks of 32 per slice, hold NaN dummies.
+// ---------------------------------------------------------------------------------
+
 struct DensTile {
     float4 p[kTileD];   // raw pfix -> {px, py, pz, |p|^2}
     float4 o[kTileD];   // raw poff {ox, oy, oz, m}
@@ -401,10 +357,441 @@ struct HydroTile {
     uint32_t masks[kTileH];
 };
 
-template <int KIND>
-struct TileOf { using T = DensTile; static constexpr int cap = kTileD; };
-template <>
-struct TileOf<1> { using T = HydroTile; static constexpr int cap = kTileH; };
+struct HAdjTile {
+    float4 p[kTileA];
+    float4 o[kTileA];   // -> {h^2, m, -, -}
+    float4 v[kTileA];   // hyd0 {vx, vy, vz, c}
+    float4 h[kTileA];   // hyd1 {A, rho, 1/h, 8/(pi h^4)}
+    float4 w[kTileA];   // wadj {wx, wy, wz, -}
+    int r[kTileA];
+    uint32_t masks[kTileA];
+};
+
+struct DAdjTile {
+    float4 p[kTileA];
+    float4 o[kTileA];   // -> {h^2, m, -, -}
+    float4 d[kTileA];   // dadj {alpha, beta, 1/h, 8/(pi h^4)}
+    int r[kTileA];
+    uint32_t masks[kTileA];
+};
+
+// kind policies
+struct KDens {
+    static constexpr int id = 0;
+    static constexpr bool sym = false;
+    static constexpr int cap = kTileD;
+    static constexpr uint32_t bytes = 32u;
+    using Member = DMember;
+    using Tile = DensTile;
+};
+struct KHydro {
+    static constexpr int id = 1;
+    static constexpr bool sym = true;
+    static constexpr int cap = kTileH;
+    static constexpr uint32_t bytes = 64u;
+    using Member = HMember;
+    using Tile = HydroTile;
+};
+struct KHAdj {
+    static constexpr int id = 2;
+    static constexpr bool sym = true;
+    static constexpr int cap = kTileA;
+    static constexpr uint32_t bytes = 80u;
+    using Member = HAMember;
+    using Tile = HAdjTile;
+};
+struct KDAdj {
+    static constexpr int id = 3;
+    static constexpr bool sym = true;
+    static constexpr int cap = kTileA;
+    static constexpr uint32_t bytes = 48u;
+    using Member = DAMember;
+    using Tile = DAdjTile;
+};
+
+// bulk copies of one run of candidates into the tile
+__device__ __forceinline__ void stage_run(DensTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
+                                          unsigned long long* bar) {
+    bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
+    bulk_to_smem(&T.o[dst], a.poff + src, b, bar);
+}
+__device__ __forceinline__ void stage_run(HydroTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
+                                          unsigned long long* bar) {
+    bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
+    bulk_to_smem(&T.o[dst], a.poff + src, b, bar);
+    bulk_to_smem(&T.v[dst], a.hyd0 + src, b, bar);
+    bulk_to_smem(&T.h[dst], a.hyd1 + src, b, bar);
+}
+__device__ __forceinline__ void stage_run(HAdjTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
+                                          unsigned long long* bar) {
+    bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
+    bulk_to_smem(&T.o[dst], a.poff + src, b, bar);
+    bulk_to_smem(&T.v[dst], a.hyd0 + src, b, bar);
+    bulk_to_smem(&T.h[dst], a.hyd1 + src, b, bar);
+    bulk_to_smem(&T.w[dst], a.wadj + src, b, bar);
+}
+__device__ __forceinline__ void stage_run(DAdjTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
+                                          unsigned long long* bar) {
+    bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
+    bulk_to_smem(&T.o[dst], a.poff + src, b, bar);
+    bulk_to_smem(&T.d[dst], a.dadj + src, b, bar);
+}
+
+// ---------------------------------------------------------------------------------
+// Pair physics
+// ---------------------------------------------------------------------------------
+
+// Plain per-tile partial sums are folded into the compensated totals after every
+// tile (or leaf): a few tens of terms in plain FP32, Kahan across blocks.
+__device__ __forceinline__ void flush(DMember& M) {
+    kahan_add(M.s0, M.c0, M.p0);
+    kahan_add(M.s1, M.c1, M.p1);
+    kahan_add(M.s2, M.c2, M.p2);
+    M.p0 = M.p1 = M.p2 = 0.0f;
+}
+
+__device__ __forceinline__ void flush(HMember& M) {
+    kahan_add(M.sx, M.cx_, M.px_);
+    kahan_add(M.sy, M.cy_, M.py_);
+    kahan_add(M.sz, M.cz_, M.pz_);
+    kahan_add(M.su, M.cu, M.pu);
+    M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
+}
+
+__device__ __forceinline__ void flush(HAMember&) {}
+__device__ __forceinline__ void flush(DAMember&) {}
+
+template <class Mem>
+__device__ __forceinline__ void precise_diff(const Mem& M, const SearchArgs& a, int crank, float& dx, float& dy,
+                                             float& dz, float& r2) {
+    uint4 Q = a.pfix[crank];
+    float4 O = a.poff[crank];
+    dx = fix_diff(Q.x, O.x, M.X, M.ox);
+    dy = fix_diff(Q.y, O.y, M.Y, M.oy);
+    dz = fix_diff(Q.z, O.z, M.Z, M.oz);
+    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// density pair: p = candidate's coordinates relative to the member's centre, m_j its mass
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, float4 p, float mj, int crank,
+                                             LocalCounters& lc) {
+    float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    bool in = r2 < M.h2lo;
+    if (!in) {
+        if (!(r2 < M.h2hi)) return;
+        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
+        double h = a.h64[M.rank];
+        in = e < __dmul_rn(h, h);
+        lc.retests++;
+    }
+    if (!in) return;
+    M.n++;
+    if (MODE == kAcc) {
+        if (M.precise) precise_diff(M, a, crank, dx, dy, dz, r2);
+        float q = r2 * rsqrtf(fmaxf(r2, 1.0e-30f)) * M.hinv;
+        if (a.o_s2) {
+            float w, dw, d2w;
+            m4_shape2(q, w, dw, d2w);
+            M.p0 = fmaf(mj, w, M.p0);
+            M.p1 = fmaf(mj, fmaf(q, dw, 3.0f * w), M.p1);
+            M.p2 = fmaf(mj, fmaf(q * q, d2w, fmaf(8.0f * q, dw, 12.0f * w)), M.p2);
+        } else {
+            float w, dw;
+            m4_shape(q, w, dw);
+            M.p0 = fmaf(mj, w, M.p0);
+            M.p1 = fmaf(mj, fmaf(q, dw, 3.0f * w), M.p1);
+        }
+    } else if (MODE == kFill) {
+        int64_t q = M.xpos++;
+        if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
+        else atomicOr(a.err, kErrCap);
+    }
+}
+
+// decision of the symmetric criterion |r| < max(h_i, h_j) with the FP64 band re-test
+template <bool WRAP, class Mem>
+__device__ __forceinline__ bool sym_decide(const Mem& M, const SearchArgs& a, float4 p, float hj2, int crank,
+                                           LocalCounters& lc, float& dx, float& dy, float& dz, float& r2) {
+    dx = rel_diff<WRAP>(p.x, M.mx);
+    dy = rel_diff<WRAP>(p.y, M.my);
+    dz = rel_diff<WRAP>(p.z, M.mz);
+    r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    float H2 = fmaxf(M.h2, hj2);
+    bool in = r2 < fmaf(H2, 1.0f - 3.0f * kBandRel, -M.bk);
+    if (!in) {
+        if (!(r2 < fmaf(H2, 1.0f + 3.0f * kBandRel, M.bk))) return false;
+        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
+        double hi = a.h64[M.rank], hj = a.h64[crank];
+        in = e < fmax(__dmul_rn(hi, hi), __dmul_rn(hj, hj));
+        lc.retests++;
+    }
+    return in;
+}
+
+// hydro pair: p = relative coordinates, q = {h_j^2, m_j, -, -}, v = {vx, vy, vz, c_j},
+// hh = {A_j, rho_j, 1/h_j, s_j}
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 q,
+                                           float4 v, float4 hh, int crank, LocalCounters& lc) {
+    if (crank == M.rank) return;
+    float dx, dy, dz, r2;
+    if (!sym_decide<WRAP>(M, a, p, q.x, crank, lc, dx, dy, dz, r2)) return;
+    M.n++;
+    if (MODE == kFill) {
+        int64_t k = M.xpos++;
+        if (k < a.x_cap) a.x_idx[k] = a.perm[crank];
+        else atomicOr(a.err, kErrCap);
+        return;
+    }
+    if (MODE != kAcc) return;
+    if (M.precise) precise_diff(M, a, crank, dx, dy, dz, r2);
+    if (r2 == 0.0f) return;  // coincident: the kernel gradient vanishes
+    float rinv = rsqrtf(r2);
+    float r = r2 * rinv;
+    float wi, dwi, wj, dwj;
+    m4_shape(r * M.hinv, wi, dwi);
+    m4_shape(r * hh.z, wj, dwj);
+    float dWi = M.sk * dwi;
+    float dWj = hh.w * dwj;
+    float rx = -dx, ry = -dy, rz = -dz;  // r_ij = x_i - x_j
+    float vx = M.vx - v.x, vy = M.vy - v.y, vz = M.vz - v.z;
+    float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
+    float visc = 0.0f;
+    if (vr < 0.0f) {
+        float hb = 0.5f * fmaf(q.x, hh.z, M.h);
+        float mu = hb * vr / fmaf(a.eps * hb, hb, r2);
+        float cb = 0.5f * (M.cs + v.w);
+        float rb = 0.5f * (M.rho + hh.y);
+        visc = fmaf(-a.alpha * cb, mu, a.beta * mu * mu) / rb;
+    }
+    float gbar = 0.5f * (dWi + dWj);
+    float coef = q.y * fmaf(M.A, dWi, fmaf(hh.x, dWj, visc * gbar)) * rinv;
+    M.px_ = fmaf(coef, dx, M.px_);
+    M.py_ = fmaf(coef, dy, M.py_);
+    M.pz_ = fmaf(coef, dz, M.pz_);
+    M.pu = fmaf(q.y * fmaf(M.A, dWi, 0.5f * visc * gbar) * rinv, vr, M.pu);
+}
+
+// Adjoint of sum_i w_i . a_i over one pair, gathered at member k.  The pair enters
+// a_k and a_j through the symmetric factor B = A_k W'_k + A_j W'_j + Pi (W'_k + W'_j)/2
+// (W' = dW/dr at h_k, h_j); their weighted sum is E = -B Q with
+// Q = rhat . (m_j w_k - m_k w_j), rhat = (x_k - x_j) / r.  Accumulated: dE/d of x_k,
+// v_k, m_k, h_k, rho_k (through the viscosity) and A_k.
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void hydro_adj_pair(HAMember& M, const SearchArgs& a, float4 p, float4 q, float4 v,
+                                               float4 hh, float4 wj, int crank, LocalCounters& lc) {
+    if (crank == M.rank) return;
+    float dx, dy, dz, r2;
+    if (!sym_decide<WRAP>(M, a, p, q.x, crank, lc, dx, dy, dz, r2)) return;
+    M.n++;
+    if (MODE != kAcc) return;
+    if (M.precise) precise_diff(M, a, crank, dx, dy, dz, r2);
+    if (r2 == 0.0f) return;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float D0 = -dx, D1 = -dy, D2 = -dz;   // x_k - x_j
+    const float e0 = D0 * rinv, e1 = D1 * rinv, e2 = D2 * rinv;
+    float wk_, dwk, d2wk, wj_, dwj, d2wj;
+    const float qk = r * M.hinv, qj = r * hh.z;
+    m4_shape2(qk, wk_, dwk, d2wk);
+    m4_shape2(qj, wj_, dwj, d2wj);
+    const float Wr_k = M.sk * dwk, Wr_j = hh.w * dwj;
+    const float Wrr_k = M.sk * M.hinv * d2wk, Wrr_j = hh.w * hh.z * d2wj;
+    const float Wrh_k = -M.sk * M.hinv * fmaf(qk, d2wk, 4.0f * dwk);
+    const float v0 = M.vx - v.x, v1 = M.vy - v.y, v2 = M.vz - v.z;
+    const float vr = fmaf(v0, D0, fmaf(v1, D1, v2 * D2));
+    const float hbar = 0.5f * fmaf(q.x, hh.z, M.h);
+    const float Dn = fmaf(a.eps * hbar, hbar, r2);
+    const float rbar = 0.5f * (M.rho + hh.y);
+    float Pi = 0.0f, Pmu = 0.0f;
+    if (vr < 0.0f) {
+        const float cbar = 0.5f * (M.cs + v.w);
+        const float mu = hbar * vr / Dn;
+        Pi = fmaf(-a.alpha * cbar, mu, a.beta * mu * mu) / rbar;
+        Pmu = fmaf(2.0f * a.beta, mu, -a.alpha * cbar) / rbar;
+    }
+    const float sdw = Wr_k + Wr_j;
+    const float B = fmaf(M.A, Wr_k, fmaf(hh.x, Wr_j, 0.5f * Pi * sdw));
+    const float mj = q.y;
+    const float U0 = mj * M.wx - M.m * wj.x, U1 = mj * M.wy - M.m * wj.y, U2 = mj * M.wz - M.m * wj.z;
+    const float Q = fmaf(e0, U0, fmaf(e1, U1, e2 * U2));
+    M.mb = fmaf(B, fmaf(e0, wj.x, fmaf(e1, wj.y, e2 * wj.z)), M.mb);
+    M.Ab = fmaf(-Q, Wr_k, M.Ab);
+    float dmu_dh = 0.0f;
+    if (vr < 0.0f) dmu_dh = 0.5f * vr * fmaf(-a.eps * hbar, hbar, r2) / (Dn * Dn);
+    M.hb = fmaf(-Q, fmaf(M.A, Wrh_k, fmaf(0.5f * Pi, Wrh_k, 0.5f * sdw * Pmu * dmu_dh)), M.hb);
+    M.rb = fmaf(Q * Pi, sdw / (4.0f * rbar), M.rb);
+    const float cm = 0.5f * sdw * Pmu;
+    if (vr < 0.0f) {
+        const float cv = -Q * cm * hbar / Dn;
+        M.vb[0] = fmaf(cv, D0, M.vb[0]);
+        M.vb[1] = fmaf(cv, D1, M.vb[1]);
+        M.vb[2] = fmaf(cv, D2, M.vb[2]);
+    }
+    const float dBr = fmaf(M.A, Wrr_k, fmaf(hh.x, Wrr_j, 0.5f * Pi * (Wrr_k + Wrr_j)));
+    const float ca = (vr < 0.0f) ? hbar / Dn : 0.0f;
+    const float cb2 = (vr < 0.0f) ? -2.0f * hbar * vr / (Dn * Dn) : 0.0f;
+    {
+        const float dB = fmaf(dBr, e0, cm * fmaf(ca, v0, cb2 * D0));
+        const float dQ = (U0 - Q * e0) * rinv;
+        M.xb[0] = fmaf(-Q, dB, fmaf(-B, dQ, M.xb[0]));
+    }
+    {
+        const float dB = fmaf(dBr, e1, cm * fmaf(ca, v1, cb2 * D1));
+        const float dQ = (U1 - Q * e1) * rinv;
+        M.xb[1] = fmaf(-Q, dB, fmaf(-B, dQ, M.xb[1]));
+    }
+    {
+        const float dB = fmaf(dBr, e2, cm * fmaf(ca, v2, cb2 * D2));
+        const float dQ = (U2 - Q * e2) * rinv;
+        M.xb[2] = fmaf(-Q, dB, fmaf(-B, dQ, M.xb[2]));
+    }
+}
+
+// Adjoint of sum_i (alpha_i rho_i + beta_i dRho_i/dh_i) at fixed h, gathered at member k:
+// rho_k's own sum (x_k moves every pair) and the sums of every j with k in N_j (x_k and
+// m_k enter as a neighbour).  q = {h_j^2, m_j, -, -}, d = {alpha_j, beta_j, 1/h_j, s_j}.
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void dens_adj_pair(DAMember& M, const SearchArgs& a, float4 p, float4 q, float4 d,
+                                              int crank, LocalCounters& lc) {
+    if (crank == M.rank) {
+        // self: W(0, h) = sigma = s h, dW/dh(0, h) = -3 sigma / h = -3 s
+        M.n++;
+        if (MODE == kAcc) M.mb = fmaf(M.alpha * M.sk, M.h, fmaf(-3.0f * M.beta, M.sk, M.mb));
+        return;
+    }
+    float dx, dy, dz, r2;
+    if (!sym_decide<WRAP>(M, a, p, q.x, crank, lc, dx, dy, dz, r2)) return;
+    M.n++;
+    if (MODE != kAcc) return;
+    if (M.precise) precise_diff(M, a, crank, dx, dy, dz, r2);
+    const float rinv = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
+    const float r = r2 * rinv;
+    float wk_, dwk, d2wk, wj_, dwj, d2wj;
+    const float qk = r * M.hinv, qj = r * d.z;
+    m4_shape2(qk, wk_, dwk, d2wk);
+    m4_shape2(qj, wj_, dwj, d2wj);
+    // k as a neighbour of j: rho_j gains m_k W(r, h_j), dRho_j/dh_j gains m_k W_h(r, h_j)
+    const float hj = q.x * d.z;
+    M.mb = fmaf(d.x * d.w, hj * wj_, fmaf(-d.y * d.w, fmaf(qj, dwj, 3.0f * wj_), M.mb));
+    if (r2 == 0.0f) return;
+    const float Wr_k = M.sk * dwk, Wr_j = d.w * dwj;
+    const float Whr_k = -M.sk * M.hinv * fmaf(qk, d2wk, 4.0f * dwk);
+    const float Whr_j = -d.w * d.z * fmaf(qj, d2wj, 4.0f * dwj);
+    const float coef = fmaf(M.alpha * q.y, Wr_k, fmaf(M.beta * q.y, Whr_k, fmaf(d.x * M.m, Wr_j, d.y * M.m * Whr_j)));
+    const float c = -coef * rinv;   // rhat = (x_k - x_j) / r = -d / r
+    M.xb[0] = fmaf(c, dx, M.xb[0]);
+    M.xb[1] = fmaf(c, dy, M.xb[1]);
+    M.xb[2] = fmaf(c, dz, M.xb[2]);
+}
+
+// phase B dispatch
+template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(DMember& M, const SearchArgs& a, const DensTile& T, int j,
+                                          LocalCounters& lc) {
+    density_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.r[j], lc);
+}
+template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(HMember& M, const SearchArgs& a, const HydroTile& T, int j,
+                                          LocalCounters& lc) {
+    hydro_pair<MODE, WRAP>(M, a, T.p[j], T.o[j], T.v[j], T.h[j], T.r[j], lc);
+}
+template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(HAMember& M, const SearchArgs& a, const HAdjTile& T, int j,
+                                          LocalCounters& lc) {
+    hydro_adj_pair<MODE, WRAP>(M, a, T.p[j], T.o[j], T.v[j], T.h[j], T.w[j], T.r[j], lc);
+}
+template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(DAMember& M, const SearchArgs& a, const DAdjTile& T, int j,
+                                          LocalCounters& lc) {
+    dens_adj_pair<MODE, WRAP>(M, a, T.p[j], T.o[j], T.d[j], T.r[j], lc);
+}
+
+// phase A threshold of the dot form |p|^2 - 2 p.m (density) and of the difference
+// form (WRAP); symmetric kinds read h_j^2 from the tile
+__device__ __forceinline__ float thr_dot(const DMember& M, float) { return M.thr_dot; }
+__device__ __forceinline__ float thr_dot(const SymMember& M, float hj2) {
+    return fmaf(fmaxf(M.h2, hj2), 1.0f + 3.0f * kBandRel, M.bk_dot);
+}
+__device__ __forceinline__ float thr_diff(const DMember& M, float) { return M.h2hi; }
+__device__ __forceinline__ float thr_diff(const SymMember& M, float hj2) {
+    return fmaf(fmaxf(M.h2, hj2), 1.0f + 3.0f * kBandRel, M.bk);
+}
+
+// combine the slice copies of a member (lanes k, k+g, k+2g, ...)
+__device__ __forceinline__ float xsum(float v, int o) { return v + __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ void slice_add(DMember& M, int o) {
+    M.s0 = xsum(M.s0, o); M.c0 = xsum(M.c0, o); M.s1 = xsum(M.s1, o); M.c1 = xsum(M.c1, o);
+    M.s2 = xsum(M.s2, o); M.c2 = xsum(M.c2, o);
+    M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
+}
+__device__ __forceinline__ void slice_add(HMember& M, int o) {
+    M.sx = xsum(M.sx, o); M.cx_ = xsum(M.cx_, o); M.sy = xsum(M.sy, o); M.cy_ = xsum(M.cy_, o);
+    M.sz = xsum(M.sz, o); M.cz_ = xsum(M.cz_, o); M.su = xsum(M.su, o); M.cu = xsum(M.cu, o);
+    M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
+}
+__device__ __forceinline__ void slice_add(HAMember& M, int o) {
+    for (int k = 0; k < 3; ++k) { M.xb[k] = xsum(M.xb[k], o); M.vb[k] = xsum(M.vb[k], o); }
+    M.mb = xsum(M.mb, o); M.hb = xsum(M.hb, o); M.rb = xsum(M.rb, o); M.Ab = xsum(M.Ab, o);
+    M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
+}
+__device__ __forceinline__ void slice_add(DAMember& M, int o) {
+    for (int k = 0; k < 3; ++k) M.xb[k] = xsum(M.xb[k], o);
+    M.mb = xsum(M.mb, o);
+    M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
+}
+
+// results of a member
+template <int MODE>
+__device__ __forceinline__ void write_result(const DMember& D, const SearchArgs& a) {
+    if (MODE == kAcc) {
+        a.o_s0[D.rank] = D.s0 - D.c0;
+        a.o_s1[D.rank] = D.s1 - D.c1;
+        if (a.o_s2) a.o_s2[D.rank] = D.s2 - D.c2;
+        a.o_n[D.rank] = D.n;
+    } else if (MODE == kCount) {
+        a.x_cnt[a.perm[D.rank]] = D.n;
+    }
+}
+template <int MODE>
+__device__ __forceinline__ void write_result(const HMember& H, const SearchArgs& a) {
+    int orig = a.perm[H.rank];
+    if (MODE == kAcc) {
+        a.o_acc[3 * (int64_t)orig] = H.sx - H.cx_;
+        a.o_acc[3 * (int64_t)orig + 1] = H.sy - H.cy_;
+        a.o_acc[3 * (int64_t)orig + 2] = H.sz - H.cz_;
+        a.o_dudt[orig] = H.su - H.cu;
+        if (a.o_nh) a.o_nh[orig] = H.n;
+    } else if (MODE == kCount) {
+        a.x_cnt[orig] = H.n;
+    }
+}
+template <int MODE>
+__device__ __forceinline__ void write_result(const HAMember& H, const SearchArgs& a) {
+    if (MODE != kAcc) return;
+    a.o_adj0[H.rank] = make_float4(H.xb[0], H.xb[1], H.xb[2], H.mb);
+    a.o_adj1[H.rank] = make_float4(H.vb[0], H.vb[1], H.vb[2], 0.0f);
+    a.o_adj2[H.rank] = make_float4(H.hb, H.rb, H.Ab, (float)H.n);
+}
+template <int MODE>
+__device__ __forceinline__ void write_result(const DAMember& D, const SearchArgs& a) {
+    if (MODE != kAcc) return;
+    a.o_adj3[D.rank] = make_float4(D.xb[0], D.xb[1], D.xb[2], D.mb);
+}
+
+// ---------------------------------------------------------------------------------
+// Grouped form: one warp per group
+// ---------------------------------------------------------------------------------
+
+struct alignas(16) WalkSmem {
+    unsigned long long bar;      // mbarrier of the tile copies
+    uint32_t stack[kStackCap];   // node ranges: (first child << 3) | (count - 1)
+    int2 ranges[kRangeCap];      // pending leaf ranges (first rank, count)
+    int rpre[kRangeCap + 1];     // prefix of the pending counts
+    int nodes[32];
+};
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
@@ -451,10 +838,10 @@ __device__ __forceinline__ int member_of(const Layout& L, int lane, int mm, int 
 // tested in dot-product form |p|^2 - 2 p.m < h^2 - |m|^2 (three FMAs; its rounding
 // stays inside the FP64 decision band).  Phase B: every lane walks its own set bits
 // across all chunks (no per-chunk wait for the slowest lane) for the exact decision
-// and the physics; plain partial sums are folded into the compensated totals after
-// the tile.
-template <int KIND, int MODE, int M, bool WRAP, class Tile>
-__device__ __forceinline__ void filter_tile(Tile& T, const Layout& L, DMember* dm, HMember* hm, int nt,
+// and the pair terms; forward partial sums are folded into the compensated totals
+// after the tile.
+template <class K, int MODE, int M, bool WRAP>
+__device__ __forceinline__ void filter_tile(typename K::Tile& T, const Layout& L, typename K::Member* mem, int nt,
                                             const SearchArgs& a, LocalCounters& lc, int lane) {
     const int S = L.S;
     if (L.slice >= S) return;
@@ -462,43 +849,31 @@ __device__ __forceinline__ void filter_tile(Tile& T, const Layout& L, DMember* d
     const int nch = ((nt + S - 1) / S + 31) >> 5;
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) {
-        float ax, ay, az, mx, my, mz;
-        int rk;
-        if constexpr (KIND == 0) {
-            mx = dm[mm].mx; my = dm[mm].my; mz = dm[mm].mz; rk = dm[mm].rank;
-        } else {
-            mx = hm[mm].mx; my = hm[mm].my; mz = hm[mm].mz; rk = hm[mm].rank;
-        }
-        ax = -2.0f * mx; ay = -2.0f * my; az = -2.0f * mz;
+        auto& Mb = mem[mm];
+        const float mx = Mb.mx, my = Mb.my, mz = Mb.mz;
+        const float ax = -2.0f * mx, ay = -2.0f * my, az = -2.0f * mz;
         for (int c = 0; c < nch; ++c) {
             uint32_t mask = 0u;
-            const float4* P = T.p + L.slice + S * (c << 5);
+            const int j0 = L.slice + S * (c << 5);
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
-                const float4 cp = P[q * S];
+                const int j = j0 + q * S;
+                const float4 cp = T.p[j];
+                float hj2 = 0.0f;
+                if constexpr (K::sym) hj2 = T.o[j].x;
                 bool pass;
                 if constexpr (!WRAP) {
                     float t = fmaf(cp.x, ax, fmaf(cp.y, ay, fmaf(cp.z, az, cp.w)));
-                    if constexpr (KIND == 0) {
-                        pass = t < dm[mm].thr_dot;
-                    } else {
-                        const float hj2 = T.o[L.slice + S * ((c << 5) + q)].x;
-                        pass = t < fmaf(fmaxf(hm[mm].h2, hj2), 1.0f + 3.0f * kBandRel, hm[mm].bk_dot);
-                    }
+                    pass = t < thr_dot(Mb, hj2);
                 } else {
                     float dx = rel_diff<true>(cp.x, mx), dy = rel_diff<true>(cp.y, my), dz = rel_diff<true>(cp.z, mz);
                     float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if constexpr (KIND == 0) {
-                        pass = r2 < dm[mm].h2hi;
-                    } else {
-                        const float hj2 = T.o[L.slice + S * ((c << 5) + q)].x;
-                        pass = r2 < fmaf(fmaxf(hm[mm].h2, hj2), 1.0f + 3.0f * kBandRel, hm[mm].bk);
-                    }
+                    pass = r2 < thr_diff(Mb, hj2);
                 }
                 mask |= (pass ? 1u : 0u) << q;
             }
             T.masks[(c << 5) + lane] = mask;
-            if (rk >= 0) lc.tests += min(32, cnt_slice - (c << 5));
+            if (Mb.rank >= 0) lc.tests += min(32, cnt_slice - (c << 5));
         }
         int c = 0;
         uint32_t cur = T.masks[lane];
@@ -510,25 +885,18 @@ __device__ __forceinline__ void filter_tile(Tile& T, const Layout& L, DMember* d
             if (cur == 0u) break;
             const int q = __ffs(cur) - 1;
             cur &= cur - 1u;
-            const int j = L.slice + S * ((c << 5) + q);
-            if constexpr (KIND == 0) {
-                density_pair<MODE, WRAP>(dm[mm], a, T.p[j], T.o[j].w, T.r[j], lc);
-            } else {
-                hydro_pair<MODE, WRAP>(hm[mm], a, T.p[j], T.o[j], T.v[j], T.h[j], T.r[j], lc);
-            }
+            tile_pair<MODE, WRAP>(Mb, a, T, L.slice + S * ((c << 5) + q), lc);
         }
-        if (MODE == kAcc) {
-            if constexpr (KIND == 0) dflush(dm[mm]);
-            else hflush(hm[mm]);
-        }
+        if (MODE == kAcc) flush(Mb);
     }
 }
 
-template <int KIND, int MODE, int M>
+template <class K, int MODE, int M>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_group(SearchArgs a) {
-    using Tile = typename TileOf<KIND>::T;
-    constexpr int TCAP = TileOf<KIND>::cap;
+    using Tile = typename K::Tile;
+    using Member = typename K::Member;
+    constexpr int TCAP = K::cap;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -595,51 +963,33 @@ k_group(SearchArgs a) {
             cz += (uint32_t)(int32_t)(((int64_t)loz + hiz) >> 1);
         }
 
-        DMember dm[KIND == 0 ? M : 1];
-        HMember hm[KIND == 1 ? M : 1];
+        Member mem[M];
         float rlane = 0.0f, hlane = 0.0f;   // walk radius ingredients of this lane
 #pragma unroll
         for (int mm = 0; mm < M; ++mm) {
             int k = member_of(L, lane, mm, a.g);
             int rank = (k >= 0 && k < gcnt) ? a.U[gbase + k] : -1;
-            if (KIND == 0) {
-                dmember_init(dm[mm], a, rank, cx, cy, cz);
-                if (rank >= 0) {
-                    float mr = sqrtf(dm[mm].mx * dm[mm].mx + dm[mm].my * dm[mm].my + dm[mm].mz * dm[mm].mz);
-                    rlane = fmaxf(rlane, mr + (float)a.h64[rank]);
-                }
-            } else {
-                hmember_init(hm[mm], a, rank, cx, cy, cz);
-                if (rank >= 0) {
-                    float mr = sqrtf(hm[mm].mx * hm[mm].mx + hm[mm].my * hm[mm].my + hm[mm].mz * hm[mm].mz);
-                    rlane = fmaxf(rlane, mr);
-                    hlane = fmaxf(hlane, hm[mm].h);
-                }
-            }
+            member_init(mem[mm], a, rank, cx, cy, cz);
+            radius_terms(mem[mm], rlane, hlane);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             rlane = fmaxf(rlane, __shfl_xor_sync(0xffffffffu, rlane, o));
             hlane = fmaxf(hlane, __shfl_xor_sync(0xffffffffu, hlane, o));
         }
-        // density: R_s = max_k (|m_k| + h_k); hydro: R_g = max_k |m_k|, hmax_g
+        // density: R_s = max_k (|m_k| + h_k); symmetric: R_g = max_k |m_k|, hmax_g
         const float Rd2 = radius2_units(rlane);
         const float Rg = rlane, hmax_g = hlane;
         // every relevant pair difference is already the nearest image when the group's
-        // reach stays below half the box (hydro: with the largest h of all particles)
-        const float reach = KIND == 0 ? rlane : Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[0].w));
+        // reach stays below half the box (symmetric: with the largest h of all particles)
+        const float reach = K::sym ? Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[0].w)) : rlane;
         const bool wrap_safe = reach < 0.49f;
 
         // export: write positions of every slot
         if (MODE == kFill) {
 #pragma unroll
-            for (int mm = 0; mm < M; ++mm) {
-                int rk = KIND == 0 ? dm[mm].rank : hm[mm].rank;
-                if (rk >= 0) {
-                    int64_t p = a.x_off[a.perm[rk]];
-                    if (KIND == 0) dm[mm].xpos = p; else hm[mm].xpos = p;
-                }
-            }
+            for (int mm = 0; mm < M; ++mm)
+                if (mem[mm].rank >= 0) mem[mm].xpos = a.x_off[a.perm[mem[mm].rank]];
         }
         int64_t sup_pos = 0, sup_n = 0;
         if (MODE == kSupFill) sup_pos = a.x_off[gid];
@@ -681,7 +1031,7 @@ k_group(SearchArgs a) {
                     nch = __float_as_int(ext.w);
                     float gap2 = node_gap2(cen, ext, cx, cy, cz);
                     float R2;
-                    if (KIND == 0) R2 = Rd2;
+                    if constexpr (!K::sym) R2 = Rd2;
                     else R2 = radius2_units(Rg + fmaxf(hmax_g, __uint_as_float(cen.w)));
                     open = gap2 <= R2;
                     leaf = lk.z < 0;
@@ -751,11 +1101,10 @@ k_group(SearchArgs a) {
                         }
                         continue;
                     }
-                    // the tile's piece of every range: one bulk copy per SoA array, by one lane
-                    constexpr uint32_t kBytesPer = (KIND == 0) ? 32u : 64u;
+                    // the tile's piece of every range: bulk copies of every SoA array
                     fence_proxy_async_smem();
                     __syncwarp();
-                    if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * kBytesPer);
+                    if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * K::bytes);
                     __syncwarp();
                     // Ranges adjacent in memory (consecutive leaves of the walk usually are)
                     // are merged into one copy: the first range of a run (or of a 32-range
@@ -790,14 +1139,8 @@ k_group(SearchArgs a) {
                         const int nxt = above ? __ffs(above) - 1 : 0;
                         const int nxt_dst = __shfl_sync(0xffffffffu, dst, nxt);
                         if (head) {
-                            const int run = (above ? nxt_dst : chunk_end) - dst;
-                            const uint32_t bytes = (uint32_t)run * 16u;
-                            bulk_to_smem(&T.p[dst], a.pfix + src, bytes, &W.bar);
-                            bulk_to_smem(&T.o[dst], a.poff + src, bytes, &W.bar);
-                            if constexpr (KIND == 1) {
-                                bulk_to_smem(&T.v[dst], a.hyd0 + src, bytes, &W.bar);
-                                bulk_to_smem(&T.h[dst], a.hyd1 + src, bytes, &W.bar);
-                            }
+                            const int runlen = (above ? nxt_dst : chunk_end) - dst;
+                            stage_run(T, a, dst, src, (uint32_t)runlen * 16u, &W.bar);
                         }
                         if (vmask != 0xffffffffu) break;
                     }
@@ -810,7 +1153,7 @@ k_group(SearchArgs a) {
                         const float px = rel_coord(P.x, O.x, cx), py = rel_coord(P.y, O.y, cy),
                                     pz = rel_coord(P.z, O.z, cz);
                         T.p[t] = make_float4(px, py, pz, fmaf(px, px, fmaf(py, py, pz * pz)));
-                        if constexpr (KIND == 1) {
+                        if constexpr (K::sym) {
                             const float hj = __uint_as_float(P.w);
                             T.o[t] = make_float4(hj * hj, O.w, 0.0f, 0.0f);
                         }
@@ -822,10 +1165,8 @@ k_group(SearchArgs a) {
                         for (int t = nt + lane; t < padded; t += 32) T.p[t] = make_float4(nanv, nanv, nanv, nanv);
                     }
                     __syncwarp();
-                    if (!kSup) {
-                        if (wrap_safe) filter_tile<KIND, MODE, M, false>(T, L, dm, hm, nt, a, lc, lane);
-                        else filter_tile<KIND, MODE, M, true>(T, L, dm, hm, nt, a, lc, lane);
-                    }
+                    if (wrap_safe) filter_tile<K, MODE, M, false>(T, L, mem, nt, a, lc, lane);
+                    else filter_tile<K, MODE, M, true>(T, L, mem, nt, a, lc, lane);
                     __syncwarp();
                 }
                 if (kSup) sup_n += total;
@@ -834,68 +1175,23 @@ k_group(SearchArgs a) {
             }
             if (sp == 0) break;
         }
-        lc.max_stack = max(lc.max_stack, 0);
 
         // ---- results
 #pragma unroll
-        for (int mm = 0; mm < M; ++mm) lc.pairs += (KIND == 0) ? dm[mm].n : hm[mm].n;
+        for (int mm = 0; mm < M; ++mm) lc.pairs += mem[mm].n;
         if (kSup) {
             if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
             continue;
         }
         if (L.S > 1) {
-            // combine the slices of every member (lanes k, k+g, k+2g, ...)
 #pragma unroll
-            for (int mm = 0; mm < M; ++mm) {
-                for (int o = a.g; o < 32; o <<= 1) {
-                    if constexpr (KIND == 0) {
-                        dm[mm].s0 += __shfl_xor_sync(0xffffffffu, dm[mm].s0, o);
-                        dm[mm].c0 += __shfl_xor_sync(0xffffffffu, dm[mm].c0, o);
-                        dm[mm].s1 += __shfl_xor_sync(0xffffffffu, dm[mm].s1, o);
-                        dm[mm].c1 += __shfl_xor_sync(0xffffffffu, dm[mm].c1, o);
-                        dm[mm].n += __shfl_xor_sync(0xffffffffu, dm[mm].n, o);
-                    } else {
-                        hm[mm].sx += __shfl_xor_sync(0xffffffffu, hm[mm].sx, o);
-                        hm[mm].cx_ += __shfl_xor_sync(0xffffffffu, hm[mm].cx_, o);
-                        hm[mm].sy += __shfl_xor_sync(0xffffffffu, hm[mm].sy, o);
-                        hm[mm].cy_ += __shfl_xor_sync(0xffffffffu, hm[mm].cy_, o);
-                        hm[mm].sz += __shfl_xor_sync(0xffffffffu, hm[mm].sz, o);
-                        hm[mm].cz_ += __shfl_xor_sync(0xffffffffu, hm[mm].cz_, o);
-                        hm[mm].su += __shfl_xor_sync(0xffffffffu, hm[mm].su, o);
-                        hm[mm].cu += __shfl_xor_sync(0xffffffffu, hm[mm].cu, o);
-                        hm[mm].n += __shfl_xor_sync(0xffffffffu, hm[mm].n, o);
-                    }
-                }
-            }
+            for (int mm = 0; mm < M; ++mm)
+                for (int o = a.g; o < 32; o <<= 1) slice_add(mem[mm], o);
         }
         if (L.slice == 0) {
 #pragma unroll
-            for (int mm = 0; mm < M; ++mm) {
-                if constexpr (KIND == 0) {
-                    const DMember& D = dm[mm];
-                    if (D.rank < 0) continue;
-                    if (MODE == kAcc) {
-                        a.o_s0[D.rank] = D.s0 - D.c0;
-                        a.o_s1[D.rank] = D.s1 - D.c1;
-                        a.o_n[D.rank] = D.n;
-                    } else if (MODE == kCount) {
-                        a.x_cnt[a.perm[D.rank]] = D.n;
-                    }
-                } else {
-                    const HMember& H = hm[mm];
-                    if (H.rank < 0) continue;
-                    int orig = a.perm[H.rank];
-                    if (MODE == kAcc) {
-                        a.o_acc[3 * (int64_t)orig] = H.sx - H.cx_;
-                        a.o_acc[3 * (int64_t)orig + 1] = H.sy - H.cy_;
-                        a.o_acc[3 * (int64_t)orig + 2] = H.sz - H.cz_;
-                        a.o_dudt[orig] = H.su - H.cu;
-                        if (a.o_nh) a.o_nh[orig] = H.n;
-                    } else if (MODE == kCount) {
-                        a.x_cnt[orig] = H.n;
-                    }
-                }
-            }
+            for (int mm = 0; mm < M; ++mm)
+                if (mem[mm].rank >= 0) write_result<MODE>(mem[mm], a);
         }
     }
     flush_counters(a, lc, lane);
@@ -918,11 +1214,11 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
         HMember hm;
         float Rbox;
         if (KIND == 0) {
-            dmember_init(dm, a, rank, cx, cy, cz);
+            member_init(dm, a, rank, cx, cy, cz);
             Rbox = (float)a.h64[rank];
             if (MODE == kFill) dm.xpos = a.x_off[a.perm[rank]];
         } else {
-            hmember_init(hm, a, rank, cx, cy, cz);
+            member_init(hm, a, rank, cx, cy, cz);
             Rbox = hm.h;
             if (MODE == kFill) hm.xpos = a.x_off[a.perm[rank]];
         }
@@ -958,8 +1254,8 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
                         }
                     }
                     if (MODE == kAcc) {
-                        if (KIND == 0) dflush(dm);
-                        else hflush(hm);
+                        if (KIND == 0) flush(dm);
+                        else flush(hm);
                     }
                     node = lk.w;
                 } else {
@@ -970,26 +1266,8 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
             }
         }
         lc.pairs += (KIND == 0) ? dm.n : hm.n;
-        if (KIND == 0) {
-            if (MODE == kAcc) {
-                a.o_s0[rank] = dm.s0 - dm.c0;
-                a.o_s1[rank] = dm.s1 - dm.c1;
-                a.o_n[rank] = dm.n;
-            } else if (MODE == kCount) {
-                a.x_cnt[a.perm[rank]] = dm.n;
-            }
-        } else {
-            int orig = a.perm[rank];
-            if (MODE == kAcc) {
-                a.o_acc[3 * (int64_t)orig] = hm.sx - hm.cx_;
-                a.o_acc[3 * (int64_t)orig + 1] = hm.sy - hm.cy_;
-                a.o_acc[3 * (int64_t)orig + 2] = hm.sz - hm.cz_;
-                a.o_dudt[orig] = hm.su - hm.cu;
-                if (a.o_nh) a.o_nh[orig] = hm.n;
-            } else if (MODE == kCount) {
-                a.x_cnt[orig] = hm.n;
-            }
-        }
+        if (KIND == 0) write_result<MODE>(dm, a);
+        else write_result<MODE>(hm, a);
     }
     flush_counters(a, lc, lane);
 }
@@ -997,10 +1275,7 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
 // ---------------------------------------------------------------------------------
 // Grouping: chunks of g consecutive entries of the work list, each split in halves
 // (recursively) while the group's search sphere, ((sqrt(3)/2) box width + h_min)^3,
-// exceeds split * (members) member spheres h_min^3.  The
-// work list follows the key order, so chunks of a dense list are compact; chunks of a
-// sparse list (the last smoothing-length passes, scattered active sets) would give
-// search spheres spanning much of the box and are cut down instead.
+// exceeds split * (members) member spheres h_min^3.
 // ---------------------------------------------------------------------------------
 
 __global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, float split,
@@ -1075,15 +1350,15 @@ int launch_gather_groups(int nch, int g, const int2* tmp, const int32_t* cnt, co
 // Launchers
 // ---------------------------------------------------------------------------------
 
-template <int KIND>
+template <class K>
 static size_t group_smem() {
-    return kWarpsPerBlock * (sizeof(WalkSmem) + sizeof(typename TileOf<KIND>::T));
+    return kWarpsPerBlock * (sizeof(WalkSmem) + sizeof(typename K::Tile));
 }
 
-template <int KIND, int MODE, int M>
+template <class K, int MODE, int M>
 static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
-    auto kern = k_group<KIND, MODE, M>;
-    size_t sh = group_smem<KIND>();
+    auto kern = k_group<K, MODE, M>;
+    size_t sh = group_smem<K>();
     static bool configured = false;
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
@@ -1100,37 +1375,42 @@ static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
     return check_cuda(cudaGetLastError(), "grouped search kernel");
 }
 
-template <int KIND, int MODE>
+template <class K, int MODE>
 static int launch_group_m(const SearchArgs& a, int sm_count, cudaStream_t s) {
     int M = (a.g + 31) / 32;
-    if (M <= 1) return launch_group_t<KIND, MODE, 1>(a, sm_count, s);
-    if (M <= 2) return launch_group_t<KIND, MODE, 2>(a, sm_count, s);
-    if (M <= 4) return launch_group_t<KIND, MODE, 4>(a, sm_count, s);
+    if (M <= 1) return launch_group_t<K, MODE, 1>(a, sm_count, s);
+    if (M <= 2) return launch_group_t<K, MODE, 2>(a, sm_count, s);
+    if (M <= 4) return launch_group_t<K, MODE, 4>(a, sm_count, s);
     return set_error(SPHGRP_EINVAL, "group_size must be <= 128");
+}
+
+template <class K>
+static int launch_group_k(const SearchArgs& a, int mode, int sm_count, cudaStream_t s) {
+    switch (mode) {
+        case kAcc: return launch_group_m<K, kAcc>(a, sm_count, s);
+        case kCount: return launch_group_m<K, kCount>(a, sm_count, s);
+        case kFill: return launch_group_m<K, kFill>(a, sm_count, s);
+        case kSupCount: return launch_group_m<K, kSupCount>(a, sm_count, s);
+        case kSupFill: return launch_group_m<K, kSupFill>(a, sm_count, s);
+    }
+    return set_error(SPHGRP_EINVAL, "bad search mode");
 }
 
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s) {
     if (a.nu <= 0) return SPHGRP_OK;
     if (grouped) {
         cudaMemsetAsync(a.work, 0, sizeof(int), s);
-        if (kind == 0) {
-            switch (mode) {
-                case kAcc: return launch_group_m<0, kAcc>(a, sm_count, s);
-                case kCount: return launch_group_m<0, kCount>(a, sm_count, s);
-                case kFill: return launch_group_m<0, kFill>(a, sm_count, s);
-                case kSupCount: return launch_group_m<0, kSupCount>(a, sm_count, s);
-                case kSupFill: return launch_group_m<0, kSupFill>(a, sm_count, s);
-            }
-        } else {
-            switch (mode) {
-                case kAcc: return launch_group_m<1, kAcc>(a, sm_count, s);
-                case kCount: return launch_group_m<1, kCount>(a, sm_count, s);
-                case kFill: return launch_group_m<1, kFill>(a, sm_count, s);
-                case kSupCount: return launch_group_m<1, kSupCount>(a, sm_count, s);
-                case kSupFill: return launch_group_m<1, kSupFill>(a, sm_count, s);
-            }
+        switch (kind) {
+            case 0: return launch_group_k<KDens>(a, mode, sm_count, s);
+            case 1: return launch_group_k<KHydro>(a, mode, sm_count, s);
+            case 2:
+                if (mode != kAcc) return set_error(SPHGRP_EINVAL, "adjoint kernels accumulate only");
+                return launch_group_m<KHAdj, kAcc>(a, sm_count, s);
+            case 3:
+                if (mode != kAcc) return set_error(SPHGRP_EINVAL, "adjoint kernels accumulate only");
+                return launch_group_m<KDAdj, kAcc>(a, sm_count, s);
         }
-        return set_error(SPHGRP_EINVAL, "bad search mode");
+        return set_error(SPHGRP_EINVAL, "bad kind");
     }
     int blocks = blocks_for(a.nu, 128);
     if (kind == 0) {
@@ -1138,11 +1418,13 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
         else if (mode == kCount) k_indiv<0, kCount><<<blocks, 128, 0, s>>>(a);
         else if (mode == kFill) k_indiv<0, kFill><<<blocks, 128, 0, s>>>(a);
         else return set_error(SPHGRP_EINVAL, "bad search mode");
-    } else {
+    } else if (kind == 1) {
         if (mode == kAcc) k_indiv<1, kAcc><<<blocks, 128, 0, s>>>(a);
         else if (mode == kCount) k_indiv<1, kCount><<<blocks, 128, 0, s>>>(a);
         else if (mode == kFill) k_indiv<1, kFill><<<blocks, 128, 0, s>>>(a);
         else return set_error(SPHGRP_EINVAL, "bad search mode");
+    } else {
+        return set_error(SPHGRP_EINVAL, "the adjoint kernels exist in the grouped form only");
     }
     note_launch();
     return check_cuda(cudaGetLastError(), "individual search kernel");

@@ -8,6 +8,9 @@ namespace sphgrp {
 
 enum Mode { kAcc = 0, kCount = 1, kFill = 2, kSupCount = 3, kSupFill = 4 };
 
+// pair loops of the search kernels: SPHGRP_DENSITY (0), SPHGRP_HYDRO (1) and the adjoints
+enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3 };
+
 struct SearchArgs {
     // octree
     const uint4* ncen;
@@ -20,6 +23,8 @@ struct SearchArgs {
     const double* h64;
     const float4* hyd0;   // {vx, vy, vz, c}
     const float4* hyd1;   // {A, rho, hinv, s}
+    const float4* wadj;   // {wx, wy, wz, -}: weights dL/da of the hydro adjoint
+    const float4* dadj;   // {alpha, beta, hinv, s}: coefficients of the density adjoint
     const int32_t* perm;
     // work list: ranks of the particles to process, in key order
     const int32_t* U;
@@ -31,7 +36,13 @@ struct SearchArgs {
     // density pass results (rank space)
     float* o_s0;
     float* o_s1;
+    float* o_s2;          // optional: d2Rho/dh2 sum (backward)
     int32_t* o_n;
+    // adjoint results (rank space)
+    float4* o_adj0;       // hydro adjoint {xb, mb}
+    float4* o_adj1;       // hydro adjoint {vb, -}
+    float4* o_adj2;       // hydro adjoint {hb, rhob, Ab, n}
+    float4* o_adj3;       // density adjoint {xb, mb}
     // hydro results (original order)
     float* o_acc;
     float* o_dudt;
@@ -85,5 +96,13 @@ int launch_gather_groups(int nch, int g, const int2* tmp, const int32_t* cnt, co
 int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s);
 int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
                        cudaStream_t s);
+
+// call orchestration shared by the entry points (api.cu)
+int finish(Ctx* c, cudaStream_t s, int rc);
+void reset_flags(Ctx* c, cudaStream_t s);
+int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s, int* nu);
+int make_groups(Ctx* c, SearchArgs* a, const int32_t* U, int nu, int g, cudaStream_t s);
+SearchArgs base_args(Ctx* c);
+int check_common(Ctx* c, int64_t n_act, const int32_t* active, int mode, int group_size);
 
 }  // namespace sphgrp

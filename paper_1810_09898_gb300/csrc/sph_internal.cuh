@@ -107,6 +107,14 @@ struct Ctx {
     int2* groups_tmp = nullptr;
     int32_t* grp_cnt = nullptr;
     int32_t* grp_off = nullptr;
+    // backward (allocated by the first backward call)
+    float* acc_s2 = nullptr;       // per-rank d2Rho/dh2 sums
+    float4* wadj = nullptr;        // weights of the accelerations, rank order
+    float4* dadj = nullptr;        // density-adjoint coefficients {alpha, beta, 1/h, s}
+    float4* adj0 = nullptr;        // hydro adjoint {xb, mb}
+    float4* adj1 = nullptr;        // hydro adjoint {vb, mb of the implicit h}
+    float4* adj2 = nullptr;        // hydro adjoint {hb, rhob, Ab, n}
+    float4* adj3 = nullptr;        // density adjoint {xb, mb}
     // tree
     Tree tree;
     // counters and error flags
