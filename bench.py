@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-individual", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--backward-n", type=int, default=1 << 21, help="particles of the backward workload")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--profile-pass", action="store_true",
                     help="after set-up run one grouped and one per-particle density+hydro pass inside "
                          "the NVTX range 'pass' (for ncu --nvtx-include pass/) and exit")
@@ -372,6 +374,86 @@ def measured_traffic(kind: str, members_per_launch: float):
     return None if per is None else per * members_per_launch
 
 
+def backward_leg(a, rank: int, steps: int, warmup: int):
+    """Forward + backward step on the clustered 2^21-particle workload: keys, sort,
+    tree, density at converged h, hydro forces, then the adjoint of
+    L = sum w.a + sum s rho (three grouped pair loops and the per-particle chain)."""
+    import torch
+
+    import paper_1810_09898_gb300 as sg
+    import sphgen
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = a.backward_n
+    d = sphgen.make("clustered", n, config=4, seed_salt=rank)
+    f32 = dict(dtype=torch.float32, device=dev)
+    pos = torch.from_numpy(d["pos"]).to(dev)
+    m = torch.from_numpy(d["m"].astype(np.float32)).to(dev)
+    vel = torch.from_numpy(d["vel"].astype(np.float32)).to(dev)
+    u = torch.from_numpy(d["u"].astype(np.float32)).to(dev)
+    rng = np.random.default_rng(sphgen.SEED_BASE + 4 + rank)
+    w = torch.from_numpy(rng.standard_normal((n, 3)).astype(np.float32)).to(dev)
+    s = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(dev)
+    ctx = sg.Context(n, nngb_tol=1e-3)
+    act = torch.arange(n, dtype=torch.int32, device=dev)
+    h = torch.full((n,), d["h0"], dtype=torch.float64, device=dev)
+    rho, drho, fg = (torch.zeros(n, **f32) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=dev)
+    acc, dudt = torch.zeros((n, 3), **f32), torch.zeros(n, **f32)
+    gx, gv = torch.zeros((n, 3), **f32), torch.zeros((n, 3), **f32)
+    gm = torch.zeros(n, **f32)
+    ctx.sfc_keys_sort(pos)
+    ctx.tree_build(pos, m)
+    try:  # h close to the exact relation (4 pi/3) h^3 rho = 64 m
+        ctx.density(act, h, 1, sg.GROUPED, 16, rho, drho, fg, nn)
+    except sg.SphgrpError as e:
+        if e.code != -3:
+            raise
+    g = a.group
+    bw = {"ms": 0.0, "search_ms": 0.0, "launches": [0.0, 0.0, 0.0]}
+
+    def step(collect):
+        ctx.sfc_keys_sort(pos)
+        ctx.tree_build(pos, m)
+        ctx.density(act, h, 0, sg.GROUPED, g, rho, drho, fg, nn)
+        ctx.hydro_force(act, h, rho, fg, vel, u, sg.GROUPED, g, acc, dudt)
+        ctx.backward(h, vel, u, w, s, g, gx, gv, gm)
+        if collect is not None:
+            log = ctx.launch_log()
+            bw["search_ms"] += sum(e["ms"] for e in log)
+            for k, e in enumerate(log[:3]):
+                bw["launches"][k] += e["ms"]
+
+    for _ in range(warmup):
+        step(None)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step(bw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # the backward call alone
+    for _ in range(2):
+        ctx.backward(h, vel, u, w, s, g, gx, gv, gm)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.backward(h, vel, u, w, s, g, gx, gv, gm)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / steps
+    ctx.close()
+    names = ("density_sums", "hydro_adjoint", "density_adjoint")
+    return {"workload": f"clustered N={n} (2^{n.bit_length() - 1}), all active, group {g}, "
+                        "L = sum w.a + sum s rho, w and s standard normal",
+            "value": n / (ms / 1e3), "unit": "particles/s (forward + backward step)", "ms_per_step": ms,
+            "backward_value": n / (ms_b / 1e3), "backward_ms": ms_b,
+            "backward_search_ms": {k: v / steps for k, v in zip(names, bw["launches"])}}
+
+
 def measured_peak_hbm() -> float:
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -434,6 +516,9 @@ def run_ours(a):
         h2d, d2h = P.io_bytes()
         e2e = {"value": world * P.n_act / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e}
+    back = None
+    if not a.no_backward:
+        back = backward_leg(a, rank, steps, warmup)
     peak = measured_peak_hbm()
     roof, detail = roofline(col_g, peak)
     cpu = None
@@ -464,6 +549,7 @@ def run_ours(a):
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "backward": back,
     }
     if ms_i is not None:
         _, di = roofline(col_i, peak)

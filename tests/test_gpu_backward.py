@@ -84,6 +84,20 @@ def test_backward_larger_clustered(cuda_device):
         print(what, "%.2e / %.2e" % _compare(got, ref, what))
 
 
+def test_backward_clustered_2m(cuda_device):
+    """The backward workload's size: 2^21 clustered particles, all elements."""
+    n = 1 << 21
+    d, m, h, w, s = _problem("clustered", n, 4)
+    _, ox, ov, om = _oracle_grad("clustered", n, 4)
+    g = Gpu(d["pos"], d["m32"])
+    gx, gv, gm = _gpu_grad(g, d, h, w, s, 16)
+    for got, ref, what in ((gx, ox, "dL/dx"), (gv, ov, "dL/dv"), (gm, om, "dL/dm")):
+        print(what, "%.2e / %.2e" % _compare(got, ref, what))
+    g.ctx.close()
+    _oracle_grad.cache_clear()
+    _problem.cache_clear()
+
+
 def test_backward_without_density_weights(cuda_device):
     d, m, h, w, s = _problem("clustered", 24001, 4)
     ref = oracle.loss_grad(d["pos"], d["vel32"].astype(np.float64), m, d["u32"].astype(np.float64), h,
