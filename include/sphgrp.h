@@ -226,6 +226,90 @@ int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* vel, const fl
                     const float* g_acc, const float* g_rho, int group_size, float* g_pos,
                     float* g_vel, float* g_m, cudaStream_t stream);
 
+/* a10: batched solve of many independent periodic boxes.  The paper treats one
+ * simulation box; serving many small and large boxes at once is a deployment pattern
+ * of the same method.  The boxes' particles are concatenated: box k holds the rows
+ * [box_off[k], box_off[k+1]) of every per-particle array, positions in its own unit
+ * cube.  One call runs, for all boxes together:
+ *   keys + a stable sort by (box, key); a forest of one octree per box; grouping of
+ *   every box's active particles (groups never cross a box); the density with the
+ *   smoothing-length iteration (Sec. 3.2) inside one persistent work-queue kernel
+ *   over every box's groups (each group iterates its members until they converge;
+ *   no host loop); the hydro forces in a second persistent kernel; and, with
+ *   SPHGRP_BATCH_BACKWARD, the adjoint of sphgrp_backward over every particle of every
+ *   box (its hydro-adjoint items share the hydro kernel's work queue).
+ * Every count stays on the device, so the whole call can be captured in one CUDA graph
+ * (SPHGRP_BATCH_GRAPH: captured on a private stream by the first call, replayed by the
+ * following calls with the same io pointers and flags, re-captured otherwise).
+ * Per box, the group size, the slice limit (member copies per warp that split a
+ * candidate tile) and the group split factor come from the box's class (box_class,
+ * e.g. 0 = uniform, 1 = clustered); sphgrp_batch_tune picks them per class by timing. */
+#define SPHGRP_BATCH_CLASSES 8
+enum {
+    SPHGRP_BATCH_BACKWARD = 1, /* also compute g_pos, g_vel, g_m */
+    SPHGRP_BATCH_GRAPH = 2     /* capture / replay the call as a CUDA graph */
+};
+
+typedef struct sphgrp_batch sphgrp_batch;
+
+/* Per-particle arrays of a batch call: device pointers, n_total rows (the sum of the
+ * box sizes), original (concatenated) order. */
+typedef struct sphgrp_batch_io {
+    const double* pos;      /* n x 3 FP64 in [0,1) of the particle's box */
+    const float* m;         /* masses */
+    const float* vel;       /* n x 3 */
+    const float* u;         /* specific internal energy, >= 0 */
+    double* h;              /* in: smoothing lengths (first guess for active particles);
+                               out: converged h of the active particles */
+    const uint8_t* active;  /* nonzero = active, or NULL: every particle active */
+    float* rho;             /* in/out: density (inactive entries are inputs to the hydro) */
+    float* drhodh;          /* out (active) */
+    float* fgrad;           /* in/out, as rho */
+    int32_t* nngb;          /* out (active): neighbour count */
+    float* acc;             /* out (active): n x 3 hydro accelerations */
+    float* dudt;            /* out (active) */
+    const float* g_acc;     /* backward: n x 3 dL/da (every particle) */
+    const float* g_rho;     /* backward: n dL/drho, or NULL */
+    float* g_pos;           /* backward outputs (each may be NULL, not all three) */
+    float* g_vel;
+    float* g_m;
+} sphgrp_batch_io;
+
+/* box_off: host, nbox + 1 ascending offsets, box_off[0] = 0, every box non-empty,
+ * box_off[nbox] <= 2^30; box_class: host, nbox classes in [0, SPHGRP_BATCH_CLASSES),
+ * or NULL (all class 0).  Allocates the device workspace for box_off[nbox] particles
+ * (about 0.5 KB per particle with the backward buffers). */
+int sphgrp_batch_create(sphgrp_batch** out, const sphgrp_params* params, int nbox,
+                        const int64_t* box_off, const int32_t* box_class);
+int sphgrp_batch_destroy(sphgrp_batch* b);
+
+/* One batched step (see above).  flags: SPHGRP_BATCH_BACKWARD | SPHGRP_BATCH_GRAPH.
+ * Synchronises the stream to read the device-side status.  Errors: EINVAL (a position
+ * or h out of range), ENOCONV (a particle did not converge within max_iter passes;
+ * its last values are written), EOVERFLOW (forest capacity or walk stack; results
+ * invalid), ETIMEOUT, ECUDA. */
+int sphgrp_batch_run(sphgrp_batch* b, const sphgrp_batch_io* io, int flags, cudaStream_t stream);
+
+/* Autotuner: runs one step (updating io like sphgrp_batch_run), then for every class
+ * present times a density + hydro pass over that class's boxes for every candidate
+ * (group size 4..64, slice limit, split factor) and keeps the fastest.  Drops the
+ * captured graph. */
+int sphgrp_batch_tune(sphgrp_batch* b, const sphgrp_batch_io* io, cudaStream_t stream);
+
+/* Read / set the configuration of one class (group_size in [1, 128], max_slices in
+ * {1, 2, 4}, group_split >= 0; 0 = no splitting).  Setting drops the captured graph. */
+int sphgrp_batch_get_config(sphgrp_batch* b, int cls, int* group_size, int* max_slices,
+                            double* group_split);
+int sphgrp_batch_set_config(sphgrp_batch* b, int cls, int group_size, int max_slices,
+                            double group_split);
+
+/* Counters of the last sphgrp_batch_run (no device work): walks and members summed
+ * over its grouped launches (density, hydro, and the backward's three), candidates,
+ * pair tests, pairs, FP64 re-tests and nodes tested over all of them, the deepest walk
+ * stack, search_launches = kernels the call launched (graph nodes when replayed), and
+ * iterations = 1 when the call replayed a captured graph, else 0. */
+int sphgrp_batch_stats(sphgrp_batch* b, sphgrp_stats* out);
+
 /* Counters of the most recent search, density or hydro call. */
 int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out);
 

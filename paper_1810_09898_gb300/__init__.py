@@ -7,7 +7,10 @@ calls raise.
 """
 
 from .binding import (  # noqa: F401
+    BATCH_BACKWARD,
+    BATCH_GRAPH,
     CENTRE_BOX,
+    Batch,
     CENTRE_FIRST,
     DENSITY,
     GROUPED,

@@ -33,7 +33,19 @@ EXPORTED = [
     "sphgrp_kernel_launches",
     "sphgrp_get_launch_log",
     "sphgrp_sfc_keys_sort_static",
+    "sphgrp_batch_create",
+    "sphgrp_batch_destroy",
+    "sphgrp_batch_run",
+    "sphgrp_batch_tune",
+    "sphgrp_batch_get_config",
+    "sphgrp_batch_set_config",
+    "sphgrp_batch_stats",
 ]
+
+BATCH_BACKWARD, BATCH_GRAPH = 1, 2
+BATCH_CLASSES = 8
+_IO_FIELDS = ("pos", "m", "vel", "u", "h", "active", "rho", "drhodh", "fgrad", "nngb", "acc", "dudt",
+              "g_acc", "g_rho", "g_pos", "g_vel", "g_m")
 
 _ERRORS = {
     -1: "SPHGRP_EINVAL",
@@ -65,6 +77,10 @@ class Params(ctypes.Structure):
         ("group_centre", ctypes.c_int),
         ("group_split", ctypes.c_double),
     ]
+
+
+class BatchIO(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in _IO_FIELDS]
 
 
 class Stats(ctypes.Structure):
@@ -110,6 +126,14 @@ def load_library():
     L.sphgrp_kernel_launches.argtypes = [ctypes.POINTER(I64)]
     L.sphgrp_get_launch_log.argtypes = [P, I32, P, P, P, P, P, ctypes.POINTER(I32)]
     L.sphgrp_sfc_keys_sort_static.argtypes = [I64, P, P, P, P]
+    L.sphgrp_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(Params), I32, P, P]
+    L.sphgrp_batch_destroy.argtypes = [P]
+    L.sphgrp_batch_run.argtypes = [P, ctypes.POINTER(BatchIO), I32, P]
+    L.sphgrp_batch_tune.argtypes = [P, ctypes.POINTER(BatchIO), P]
+    L.sphgrp_batch_get_config.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                          ctypes.POINTER(ctypes.c_double)]
+    L.sphgrp_batch_set_config.argtypes = [P, I32, I32, I32, ctypes.c_double]
+    L.sphgrp_batch_stats.argtypes = [P, ctypes.POINTER(Stats)]
     for name in EXPORTED:
         if name not in ("sphgrp_default_params", "sphgrp_last_error"):
             getattr(L, name).restype = I32
@@ -236,3 +260,73 @@ class Context:
         s = Stats()
         _check(self._L.sphgrp_get_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
+
+
+class Batch:
+    """One sphgrp_batch: many independent periodic boxes solved together (a10).
+
+    box_off: nbox + 1 offsets of the boxes' rows in the concatenated particle arrays;
+    box_class: nbox class indices (autotuned configuration per class)."""
+
+    def __init__(self, box_off, box_class=None, **params):
+        import numpy as np
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("sphgrp needs a CUDA device")
+        self._L = load_library()
+        self.params = default_params(**params)
+        self.box_off = np.ascontiguousarray(box_off, dtype=np.int64)
+        self.nbox = len(self.box_off) - 1
+        cls = None if box_class is None else np.ascontiguousarray(box_class, dtype=np.int32)
+        self._cls = cls
+        self._h = ctypes.c_void_p()
+        _check(self._L.sphgrp_batch_create(ctypes.byref(self._h), ctypes.byref(self.params), self.nbox,
+                                           self.box_off.ctypes.data_as(ctypes.c_void_p),
+                                           None if cls is None else cls.ctypes.data_as(ctypes.c_void_p)))
+        self.n = int(self.box_off[-1])
+
+    def close(self):
+        if self._h:
+            self._L.sphgrp_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _io(arrays: dict) -> BatchIO:
+        unknown = set(arrays) - set(_IO_FIELDS)
+        if unknown:
+            raise KeyError(f"unknown io arrays: {sorted(unknown)}")
+        io = BatchIO()
+        for f in _IO_FIELDS:
+            t = arrays.get(f)
+            setattr(io, f, None if t is None else t.data_ptr())
+        return io
+
+    def run(self, arrays: dict, backward: bool = False, graph: bool = False):
+        flags = (BATCH_BACKWARD if backward else 0) | (BATCH_GRAPH if graph else 0)
+        io = self._io(arrays)
+        _check(self._L.sphgrp_batch_run(self._h, ctypes.byref(io), flags, _stream()))
+
+    def tune(self, arrays: dict):
+        io = self._io(arrays)
+        _check(self._L.sphgrp_batch_tune(self._h, ctypes.byref(io), _stream()))
+
+    def get_config(self, cls: int) -> dict:
+        g, sm = ctypes.c_int(), ctypes.c_int()
+        sp = ctypes.c_double()
+        _check(self._L.sphgrp_batch_get_config(self._h, cls, ctypes.byref(g), ctypes.byref(sm), ctypes.byref(sp)))
+        return {"group_size": g.value, "max_slices": sm.value, "group_split": sp.value}
+
+    def set_config(self, cls: int, group_size: int, max_slices: int, group_split: float):
+        _check(self._L.sphgrp_batch_set_config(self._h, cls, group_size, max_slices, float(group_split)))
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(self._L.sphgrp_batch_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()

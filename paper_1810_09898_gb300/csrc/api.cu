@@ -15,6 +15,7 @@ static thread_local std::string g_last_error = "no error";
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void timer_begin(Ctx* c, cudaStream_t s) {
     if (c->ntimed < Ctx::kMaxTimed) cudaEventRecord(c->tev[2 * c->ntimed], s);
@@ -140,6 +141,22 @@ __global__ void k_members(int nu, const int32_t* __restrict__ U, const int32_t* 
 }  // namespace
 
 namespace sphgrp {
+
+// smoothing lengths (original order) -> h64 and the FP32 copy in pfix.w
+int launch_gather_h(Ctx* c, const double* h, cudaStream_t s) {
+    k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "gather h");
+}
+
+// hydro inputs of every particle in key order (hyd0, hyd1, h64, pfix.w)
+int launch_hydro_prep(Ctx* c, const double* h, const float* rho, const float* fgrad, const float* vel,
+                      const float* u, cudaStream_t s) {
+    k_hydro_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, rho, fgrad, vel, u, (float)c->p.gamma,
+                                                      c->h64, c->pfix, c->hyd0, c->hyd1, c->err);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "hydro prep");
+}
 
 int finish(Ctx* c, cudaStream_t s, int rc) {
     if (rc) return rc;

@@ -114,8 +114,10 @@ __global__ void k_bwd_combine(int64_t n, const int32_t* __restrict__ perm, const
     if (g_m) g_m[i] = a.w + b.w + c.w;
 }
 
+}  // namespace
+
 template <typename T>
-int lazy_alloc(T** p, int64_t count) {
+static int lazy_alloc(T** p, int64_t count) {
     if (*p) return SPHGRP_OK;
     return check_cuda(cudaMalloc(reinterpret_cast<void**>(p), (size_t)(count < 1 ? 1 : count) * sizeof(T)),
                       "cudaMalloc (backward buffers)");
@@ -130,6 +132,29 @@ int backward_buffers(Ctx* c) {
         if ((rc = lazy_alloc(b, n))) return rc;
     return SPHGRP_OK;
 }
+
+int launch_bwd_prep(Ctx* c, const float* vel, const float* u, const float* g_acc, float4* hyd0, float4* hyd1,
+                    cudaStream_t s) {
+    k_bwd_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, c->h64, c->acc_rho, c->acc_drho, vel, u, g_acc,
+                                                     c->p.gamma, hyd0, hyd1, c->wadj);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "backward prep");
+}
+
+int launch_bwd_chain(Ctx* c, const float* u, const float* g_rho, cudaStream_t s) {
+    k_bwd_chain<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, c->h64, c->acc_rho, c->acc_drho, c->acc_s2, u,
+                                                      g_rho, c->adj2, c->p.gamma, c->p.nngb, c->dadj, c->adj1);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "backward chain");
+}
+
+int launch_bwd_combine(Ctx* c, float* g_pos, float* g_vel, float* g_m, cudaStream_t s) {
+    k_bwd_combine<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, c->adj0, c->adj1, c->adj3, g_pos, g_vel, g_m);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "backward combine");
+}
+
+namespace {
 
 __global__ void k_gather_h_all(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
                                double* __restrict__ h64, uint4* __restrict__ pfix, unsigned* err) {
@@ -186,9 +211,7 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     rc = launch_search(ad, kKindDensity, kAcc, true, c->sm_count, s);
     timer_end(c, s, nu);
     if (rc) return rc;
-    k_bwd_prep<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->h64, c->acc_rho, c->acc_drho, vel, u, g_acc,
-                                                  c->p.gamma, c->hyd0, c->hyd1, c->wadj);
-    note_launch();
+    if ((rc = launch_bwd_prep(c, vel, u, g_acc, c->hyd0, c->hyd1, s))) return rc;
     // 2. adjoint of sum w . a over every hydro pair
     SearchArgs ah = a;
     ah.o_adj0 = c->adj0;
@@ -199,9 +222,7 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     timer_end(c, s, nu);
     if (rc) return rc;
     // 3. per particle: A, f, rho, h and the implicit h
-    k_bwd_chain<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->h64, c->acc_rho, c->acc_drho, c->acc_s2, u,
-                                                   g_rho, c->adj2, c->p.gamma, c->p.nngb, c->dadj, c->adj1);
-    note_launch();
+    if ((rc = launch_bwd_chain(c, u, g_rho, s))) return rc;
     // 4. adjoint of rho and rho' at fixed h over every density pair
     SearchArgs aa = a;
     aa.o_adj3 = c->adj3;
@@ -209,8 +230,7 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     rc = launch_search(aa, kKindDensityAdj, kAcc, true, c->sm_count, s);
     timer_end(c, s, nu);
     if (rc) return rc;
-    k_bwd_combine<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->adj0, c->adj1, c->adj3, g_pos, g_vel, g_m);
-    note_launch();
+    if ((rc = launch_bwd_combine(c, g_pos, g_vel, g_m, s))) return rc;
     rc = check_cuda(cudaGetLastError(), "backward kernels");
     c->last.walks = 3 * (int64_t)a.ngroups;
     c->last.members = 3 * (int64_t)nu;

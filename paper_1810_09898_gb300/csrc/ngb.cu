@@ -891,307 +891,497 @@ __device__ __forceinline__ void filter_tile(typename K::Tile& T, const Layout& L
     }
 }
 
+// Work item of the grouped kernels: members U[base, base + cnt), the walk's start node
+// (a root of the forest), the group size of the member layout and the slice limit.
+struct GroupDesc {
+    int base, cnt, root, g, smax;
+};
+
+__device__ __forceinline__ GroupDesc group_desc(const SearchArgs& a, int gid) {
+    GroupDesc d;
+    d.root = 0;
+    d.g = a.g;
+    d.smax = 32;
+    if (a.groups4) {
+        const int4 G = a.groups4[gid];
+        d.base = G.x;
+        d.cnt = G.y;
+        d.root = G.z;
+        d.g = G.w & 0xff;
+        d.smax = G.w >> 8;
+    } else if (a.groups) {
+        const int2 G = a.groups[gid];
+        d.base = G.x;
+        d.cnt = G.y;
+    } else {
+        d.base = gid * a.g;
+        d.cnt = min(a.g, a.nu - d.base);
+    }
+    return d;
+}
+
+__device__ __forceinline__ int group_count(const SearchArgs& a) {
+    return a.ngroups_dev ? *a.ngroups_dev : a.ngroups;
+}
+
+// Group centre: the fixed-point position of the first member (lowest slot of the
+// lowest lane), or the centre of the members' bounding box (offsets from the first
+// member are exact minimum-image integers).  Ranks < 0 are empty slots.  Returns
+// false when the group has no member.
+template <int M>
+__device__ __forceinline__ bool group_centre(const SearchArgs& a, const int (&rk)[M], uint32_t& cx, uint32_t& cy,
+                                             uint32_t& cz) {
+    int ref = -1;
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) {
+        const unsigned b = __ballot_sync(0xffffffffu, rk[mm] >= 0);
+        const int cand = __shfl_sync(0xffffffffu, rk[mm], b ? __ffs(b) - 1 : 0);
+        if (ref < 0 && b) ref = cand;
+    }
+    if (ref < 0) return false;
+    const uint4 P0 = a.pfix[ref];
+    cx = P0.x;
+    cy = P0.y;
+    cz = P0.z;
+    if (a.centre_box) {
+        int lox = 0, loy = 0, loz = 0, hix = 0, hiy = 0, hiz = 0;
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) {
+            if (rk[mm] >= 0) {
+                const uint4 P = a.pfix[rk[mm]];
+                const int dx = (int32_t)(P.x - cx), dy = (int32_t)(P.y - cy), dz = (int32_t)(P.z - cz);
+                lox = min(lox, dx); hix = max(hix, dx);
+                loy = min(loy, dy); hiy = max(hiy, dy);
+                loz = min(loz, dz); hiz = max(hiz, dz);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lox = min(lox, __shfl_xor_sync(0xffffffffu, lox, o));
+            loy = min(loy, __shfl_xor_sync(0xffffffffu, loy, o));
+            loz = min(loz, __shfl_xor_sync(0xffffffffu, loz, o));
+            hix = max(hix, __shfl_xor_sync(0xffffffffu, hix, o));
+            hiy = max(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
+            hiz = max(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
+        }
+        cx += (uint32_t)(int32_t)(((int64_t)lox + hix) >> 1);
+        cy += (uint32_t)(int32_t)(((int64_t)loy + hiy) >> 1);
+        cz += (uint32_t)(int32_t)(((int64_t)loz + hiz) >> 1);
+    }
+    return true;
+}
+
+// One group's walk from node `root` and the member x candidate filter of every staged
+// tile (the members are initialised relative to the centre C).  kSupFill writes the
+// superset at sup_pos + sup_n; sup_n accumulates the candidates.
+template <class K, int MODE, int M>
+__device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, typename K::Tile& T, const Layout& L,
+                                             typename K::Member (&mem)[M], uint32_t cx, uint32_t cy, uint32_t cz,
+                                             int root, LocalCounters& lc, uint32_t& tma_phase, int lane,
+                                             int64_t sup_pos, int64_t& sup_n) {
+    constexpr int TCAP = K::cap;
+    constexpr bool kSup = (MODE == kSupCount || MODE == kSupFill);
+    const uint32_t lt = (1u << lane) - 1u;
+    float rlane = 0.0f, hlane = 0.0f;   // walk radius ingredients of this lane
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) radius_terms(mem[mm], rlane, hlane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rlane = fmaxf(rlane, __shfl_xor_sync(0xffffffffu, rlane, o));
+        hlane = fmaxf(hlane, __shfl_xor_sync(0xffffffffu, hlane, o));
+    }
+    // density: R_s = max_k (|m_k| + h_k); symmetric: R_g = max_k |m_k|, hmax_g
+    const float Rd2 = radius2_units(rlane);
+    const float Rg = rlane, hmax_g = hlane;
+    // every relevant pair difference is already the nearest image when the group's
+    // reach stays below half the box (symmetric: with the largest h of the tree)
+    const float reach = K::sym ? Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[root].w)) : rlane;
+    const bool wrap_safe = reach < 0.49f;
+
+    int sp = 1;
+    if (lane == 0) W.stack[0] = (uint32_t)root << 3;   // one node
+    int nr = 0, pending = 0;
+    __syncwarp();
+    for (;;) {
+        while (sp > 0 && pending < TCAP && nr <= kRangeCap - 32) {
+            // take range entries from the top of the stack, up to 32 nodes
+            uint32_t ent = 0;
+            int ecnt = 0;
+            if (lane < sp) {
+                ent = W.stack[sp - 1 - lane];
+                ecnt = (int)(ent & 7u) + 1;
+            }
+            int incl = warp_incl_scan(ecnt, lane);
+            bool take = (lane < sp) && (incl <= 32);
+            unsigned tm = __ballot_sync(0xffffffffu, take);
+            int nent = __popc(tm);
+            int nnodes = __shfl_sync(0xffffffffu, incl, nent - 1);
+            if (take) {
+                int first = (int)(ent >> 3), ex = incl - ecnt;
+                for (int q = 0; q < ecnt; ++q) W.nodes[ex + q] = first + q;
+            }
+            sp -= nent;
+            __syncwarp();
+            int node = lane < nnodes ? W.nodes[lane] : -1;
+            __syncwarp();
+            bool open = false, leaf = false;
+            int4 lk = make_int4(0, 0, -1, 0);
+            int nch = 0;
+            if (node >= 0) {
+                uint4 cen = a.ncen[node];
+                float4 ext = a.next[node];
+                lk = a.nlink[node];
+                nch = __float_as_int(ext.w);
+                float gap2 = node_gap2(cen, ext, cx, cy, cz);
+                float R2;
+                if constexpr (!K::sym) R2 = Rd2;
+                else R2 = radius2_units(Rg + fmaxf(hmax_g, __uint_as_float(cen.w)));
+                open = gap2 <= R2;
+                leaf = lk.z < 0;
+            }
+            lc.nodes += (lane == 0) ? nnodes : 0;
+            bool emit = open && leaf && lk.y > 0;
+            unsigned em = __ballot_sync(0xffffffffu, emit);
+            if (emit) {
+                int pos = nr + __popc(em & lt);
+                W.ranges[pos] = make_int2(lk.x, lk.y);
+            }
+            nr += __popc(em);
+            int add = emit ? lk.y : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+            pending += add;
+            bool push = open && !leaf;
+            unsigned pm = __ballot_sync(0xffffffffu, push);
+            if (push) {
+                int pos = sp + __popc(pm & lt);
+                if (pos < kStackCap) W.stack[pos] = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
+                else atomicOr(a.err, kErrStack);
+            }
+            sp = min(sp + __popc(pm), kStackCap);
+            lc.max_stack = max(lc.max_stack, sp);
+            __syncwarp();
+        }
+        if (nr > 0) {
+            // ---- flush the pending leaf ranges in tiles
+            int run = 0;
+            for (int e0 = 0; e0 < nr; e0 += 32) {
+                int e = e0 + lane;
+                int c = e < nr ? W.ranges[e].y : 0;
+                int inc = warp_incl_scan(c, lane);
+                if (e < nr) W.rpre[e] = run + inc - c;
+                run += __shfl_sync(0xffffffffu, inc, 31);
+            }
+            if (lane == 0) W.rpre[nr] = run;
+            __syncwarp();
+            const int total = run;
+            lc.cands += (lane == 0) ? total : 0;
+            for (int t0 = 0; t0 < total; t0 += TCAP) {
+                const int nt = min(TCAP, total - t0);
+                // first range reaching into this tile
+                int e0 = 0;
+                {
+                    int lo = 0, hi = nr;
+                    while (hi - lo > 1) {
+                        int mid = (lo + hi) >> 1;
+                        if (W.rpre[mid] <= t0) lo = mid; else hi = mid;
+                    }
+                    e0 = lo;
+                }
+                if (kSup) {
+                    if (MODE == kSupFill) {
+                        for (int e = e0 + (lane >> 4); e < nr; e += 2) {
+                            const int rb = W.rpre[e];
+                            if (rb >= t0 + nt) break;
+                            const int2 R = W.ranges[e];
+                            const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
+                            for (int gt = lo + (lane & 15); gt < hi; gt += 16) {
+                                int64_t p = sup_pos + sup_n + gt;
+                                if (p < a.x_cap) a.x_idx[p] = a.perm[R.x + (gt - rb)];
+                                else atomicOr(a.err, kErrCap);
+                            }
+                        }
+                    }
+                    continue;
+                }
+                // the tile's piece of every range: bulk copies of every SoA array
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * K::bytes);
+                __syncwarp();
+                // Ranges adjacent in memory (consecutive leaves of the walk usually are)
+                // are merged into one copy: the first range of a run (or of a 32-range
+                // chunk) issues the copy of the whole run.
+                for (int eb = e0; eb < nr; eb += 32) {
+                    const int e = eb + lane;
+                    int rb = 0, src = 0, dst = 0, cnt = 0;
+                    bool valid = false, cont = false;
+                    if (e < nr) {
+                        rb = W.rpre[e];
+                        valid = rb < t0 + nt;
+                    }
+                    if (valid) {
+                        const int2 R = W.ranges[e];
+                        const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
+                        src = R.x + (lo - rb);
+                        dst = lo - t0;
+                        cnt = hi - lo;
+                        if (lane > 0 && e > e0) {
+                            const int2 Q = W.ranges[e - 1];
+                            cont = Q.x + Q.y == R.x;
+                        }
+                        for (int k = 0; k < cnt; ++k) T.r[dst + k] = src + k;
+                    }
+                    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+                    if (vmask == 0u) break;
+                    const bool head = valid && !cont;
+                    const unsigned hmask = __ballot_sync(0xffffffffu, head);
+                    const int last = 31 - __clz(vmask);
+                    const int chunk_end = __shfl_sync(0xffffffffu, dst + cnt, last);
+                    const unsigned above = (lane == 31) ? 0u : (hmask >> (lane + 1)) << (lane + 1);
+                    const int nxt = above ? __ffs(above) - 1 : 0;
+                    const int nxt_dst = __shfl_sync(0xffffffffu, dst, nxt);
+                    if (head) {
+                        const int runlen = (above ? nxt_dst : chunk_end) - dst;
+                        stage_run(T, a, dst, src, (uint32_t)runlen * 16u, &W.bar);
+                    }
+                    if (vmask != 0xffffffffu) break;
+                }
+                if (!mbar_wait_bounded(&W.bar, tma_phase, a.err)) mbar_wait_bounded(&W.bar, tma_phase, a.err);
+                tma_phase ^= 1u;
+                // in place: fixed point -> coordinates relative to the centre
+                for (int t = lane; t < nt; t += 32) {
+                    const uint4 P = *reinterpret_cast<const uint4*>(&T.p[t]);
+                    const float4 O = T.o[t];
+                    const float px = rel_coord(P.x, O.x, cx), py = rel_coord(P.y, O.y, cy),
+                                pz = rel_coord(P.z, O.z, cz);
+                    T.p[t] = make_float4(px, py, pz, fmaf(px, px, fmaf(py, py, pz * pz)));
+                    if constexpr (K::sym) {
+                        const float hj = __uint_as_float(P.w);
+                        T.o[t] = make_float4(hj * hj, O.w, 0.0f, 0.0f);
+                    }
+                }
+                {
+                    // NaN dummies up to whole chunks of 32 in every slice
+                    const int padded = L.S * ((((nt + L.S - 1) / L.S) + 31) >> 5) * 32;
+                    const float nanv = __int_as_float(0x7fffffff);
+                    for (int t = nt + lane; t < padded; t += 32) T.p[t] = make_float4(nanv, nanv, nanv, nanv);
+                }
+                __syncwarp();
+                if (wrap_safe) filter_tile<K, MODE, M, false>(T, L, mem, nt, a, lc, lane);
+                else filter_tile<K, MODE, M, true>(T, L, mem, nt, a, lc, lane);
+                __syncwarp();
+            }
+            if (kSup) sup_n += total;
+            nr = 0;
+            pending = 0;
+        }
+        if (sp == 0) break;
+    }
+}
+
+// One work item of the grouped kernels: set-up, search, results.
+template <class K, int MODE, int M>
+__device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, typename K::Tile& T, int gid,
+                                              LocalCounters& lc, uint32_t& tma_phase, int lane) {
+    using Member = typename K::Member;
+    constexpr bool kSup = (MODE == kSupCount || MODE == kSupFill);
+    const GroupDesc d = group_desc(a, gid);
+    const Layout L = make_layout(d.g, lane, MODE == kAcc, min(K::cap / 32, d.smax));
+    int rk[M];
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) {
+        const int k = member_of(L, lane, mm, d.g);
+        rk[mm] = (k >= 0 && k < d.cnt) ? a.U[d.base + k] : -1;
+    }
+    uint32_t cx = 0, cy = 0, cz = 0;
+    if (!group_centre<M>(a, rk, cx, cy, cz)) return;
+    Member mem[M];
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) member_init(mem[mm], a, rk[mm], cx, cy, cz);
+    // export: write positions of every slot
+    if (MODE == kFill) {
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm)
+            if (mem[mm].rank >= 0) mem[mm].xpos = a.x_off[a.perm[mem[mm].rank]];
+    }
+    int64_t sup_pos = 0, sup_n = 0;
+    if (MODE == kSupFill) sup_pos = a.x_off[gid];
+    group_search<K, MODE, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, sup_pos, sup_n);
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) lc.pairs += mem[mm].n;
+    if (kSup) {
+        if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
+        return;
+    }
+    if (L.S > 1) {
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm)
+            for (int o = d.g; o < 32; o <<= 1) slice_add(mem[mm], o);
+    }
+    if (L.slice == 0) {
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm)
+            if (mem[mm].rank >= 0) write_result<MODE>(mem[mm], a);
+    }
+}
+
+__device__ __forceinline__ int next_item(const SearchArgs& a, int lane) {
+    int gid = 0;
+    if (lane == 0) gid = atomicAdd(a.work, 1);
+    return __shfl_sync(0xffffffffu, gid, 0);
+}
+
 template <class K, int MODE, int M>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_group(SearchArgs a) {
-    using Tile = typename K::Tile;
-    using Member = typename K::Member;
-    constexpr int TCAP = K::cap;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     WalkSmem& W = reinterpret_cast<WalkSmem*>(smem_raw)[wib];
-    Tile& T = reinterpret_cast<Tile*>(smem_raw + kWarpsPerBlock * sizeof(WalkSmem))[wib];
-    constexpr bool kSup = (MODE == kSupCount || MODE == kSupFill);
-    const bool allow_slices = (MODE == kAcc);
-    const Layout L = make_layout(a.g, lane, allow_slices, TCAP / 32);
+    auto& T = reinterpret_cast<typename K::Tile*>(smem_raw + kWarpsPerBlock * sizeof(WalkSmem))[wib];
     LocalCounters lc;
-    const uint32_t lt = (1u << lane) - 1u;
     uint32_t tma_phase = 0u;
     if (lane == 0) mbar_init(&W.bar, 1u);
     __syncwarp();
-
+    const int ng = group_count(a);
     for (;;) {
-        int gid = 0;
-        if (lane == 0) gid = atomicAdd(a.work, 1);
-        gid = __shfl_sync(0xffffffffu, gid, 0);
-        if (gid >= a.ngroups) break;
-        int gbase, gcnt;
-        if (a.groups) {
-            int2 G = a.groups[gid];
-            gbase = G.x;
-            gcnt = G.y;
-        } else {
-            gbase = gid * a.g;
-            gcnt = min(a.g, a.nu - gbase);
-        }
-        // ---- group set-up: centre = fixed-point position of the first member, or the
-        // centre of the members' bounding box (offsets from the first member are exact
-        // minimum-image integers)
-        uint32_t cx = 0, cy = 0, cz = 0;
-        if (lane == 0) {
-            uint4 P = a.pfix[a.U[gbase]];
-            cx = P.x; cy = P.y; cz = P.z;
-        }
-        cx = __shfl_sync(0xffffffffu, cx, 0);
-        cy = __shfl_sync(0xffffffffu, cy, 0);
-        cz = __shfl_sync(0xffffffffu, cz, 0);
-        if (a.centre_box) {
-            int lox = 0, loy = 0, loz = 0, hix = 0, hiy = 0, hiz = 0;
-#pragma unroll
-            for (int mm = 0; mm < M; ++mm) {
-                int k = member_of(L, lane, mm, a.g);
-                if (k >= 0 && k < gcnt) {
-                    uint4 P = a.pfix[a.U[gbase + k]];
-                    int dx = (int32_t)(P.x - cx), dy = (int32_t)(P.y - cy), dz = (int32_t)(P.z - cz);
-                    lox = min(lox, dx); hix = max(hix, dx);
-                    loy = min(loy, dy); hiy = max(hiy, dy);
-                    loz = min(loz, dz); hiz = max(hiz, dz);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lox = min(lox, __shfl_xor_sync(0xffffffffu, lox, o));
-                loy = min(loy, __shfl_xor_sync(0xffffffffu, loy, o));
-                loz = min(loz, __shfl_xor_sync(0xffffffffu, loz, o));
-                hix = max(hix, __shfl_xor_sync(0xffffffffu, hix, o));
-                hiy = max(hiy, __shfl_xor_sync(0xffffffffu, hiy, o));
-                hiz = max(hiz, __shfl_xor_sync(0xffffffffu, hiz, o));
-            }
-            cx += (uint32_t)(int32_t)(((int64_t)lox + hix) >> 1);
-            cy += (uint32_t)(int32_t)(((int64_t)loy + hiy) >> 1);
-            cz += (uint32_t)(int32_t)(((int64_t)loz + hiz) >> 1);
-        }
+        const int gid = next_item(a, lane);
+        if (gid >= ng) break;
+        process_group<K, MODE, M>(a, W, T, gid, lc, tma_phase, lane);
+    }
+    flush_counters(a, lc, lane);
+}
 
-        Member mem[M];
-        float rlane = 0.0f, hlane = 0.0f;   // walk radius ingredients of this lane
+// Two kinds of work item in one persistent queue: the groups of a0 (kind K0) first,
+// then those of a1 (kind K1).  Both share the work counter of a0.
+template <class K0, class K1, int M>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_group_pair(SearchArgs a0, SearchArgs a1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr size_t kTileBytes = sizeof(typename K0::Tile) > sizeof(typename K1::Tile) ? sizeof(typename K0::Tile)
+                                                                                        : sizeof(typename K1::Tile);
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WalkSmem& W = reinterpret_cast<WalkSmem*>(smem_raw)[wib];
+    unsigned char* tile = smem_raw + kWarpsPerBlock * sizeof(WalkSmem) + wib * kTileBytes;
+    LocalCounters lc;
+    uint32_t tma_phase = 0u;
+    if (lane == 0) mbar_init(&W.bar, 1u);
+    __syncwarp();
+    const int n0 = group_count(a0), n1 = group_count(a1);
+    for (;;) {
+        const int gid = next_item(a0, lane);
+        if (gid >= n0 + n1) break;
+        if (gid < n0)
+            process_group<K0, kAcc, M>(a0, W, *reinterpret_cast<typename K0::Tile*>(tile), gid, lc, tma_phase, lane);
+        else
+            process_group<K1, kAcc, M>(a1, W, *reinterpret_cast<typename K1::Tile*>(tile), gid - n0, lc, tma_phase,
+                                       lane);
+    }
+    flush_counters(a0, lc, lane);
+}
+
+// Density with the smoothing-length iteration inside the group (no host loop, no
+// regrouping): after every walk + filter the members update h in FP64 (the same
+// Newton / bisection step as k_hsml_update); converged members leave the group, the
+// centre and radius are recomputed over the remaining ones and the group walks again,
+// until every member has converged or reached max_iter passes.  A particle's density
+// at h depends only on the positions and its own h, so the iterates equal those of the
+// pass-by-pass iteration (up to the order of the FP32 sums).
+__device__ __forceinline__ bool hsml_step(const SearchArgs& a, const IterArgs& it, int r, double& h, double& lo,
+                                          double& hi, float s0, float s1, int nngb, int pass, bool writer) {
+    const double kPi = 3.14159265358979323846;
+    const double m = (double)a.poff[r].w;
+    const double sigma = 8.0 / (kPi * h * h * h);
+    const double rho = sigma * (double)s0;
+    const double drho = -sigma / h * (double)s1;
+    const double neff = 4.0 * kPi / 3.0 * h * h * h * rho / m;
+    const bool done = fabs(neff - it.nngb) <= it.tol;
+    if (done || pass >= it.max_iter) {
+        if (writer) {
+            const int orig = a.perm[r];
+            it.rho[orig] = (float)rho;
+            it.drhodh[orig] = (float)drho;
+            it.fgrad[orig] = (float)(1.0 / (1.0 + h / (3.0 * rho) * drho));
+            it.nngb_out[orig] = nngb;
+            if (it.iters) it.iters[orig] = pass;
+            it.h_out[orig] = h;
+            if (!done) atomicAdd(it.nfail, 1);
+        }
+        return true;
+    }
+    if (neff < it.nngb) lo = h; else hi = h;
+    const double g = 4.0 * kPi / 3.0 * h * h * h * rho - it.nngb * m;
+    const double gp = 4.0 * kPi * h * h * rho + 4.0 * kPi / 3.0 * h * h * h * drho;
+    double hn = h - g / gp;
+    const double cbrt2 = 1.2599210498948731647672106;
+    if (!(hn > lo && hn < hi) || !isfinite(hn)) {
+        if (isinf(hi)) hn = h * cbrt2;
+        else if (lo == 0.0) hn = h / cbrt2;
+        else hn = cbrt(0.5 * (lo * lo * lo + hi * hi * hi));
+    }
+    hn = fmin(hn, 0.49);   // the minimum image needs h < 1/2 (such a particle cannot converge)
+    h = hn;
+    if (writer) {
+        it.h64[r] = hn;
+        it.pfix[r].w = __float_as_uint((float)hn);
+    }
+    return false;
+}
+
+template <int M>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_group_dens_iter(SearchArgs a, IterArgs it) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WalkSmem& W = reinterpret_cast<WalkSmem*>(smem_raw)[wib];
+    DensTile& T = reinterpret_cast<DensTile*>(smem_raw + kWarpsPerBlock * sizeof(WalkSmem))[wib];
+    LocalCounters lc;
+    uint32_t tma_phase = 0u;
+    if (lane == 0) mbar_init(&W.bar, 1u);
+    __syncwarp();
+    const int ng = group_count(a);
+    for (;;) {
+        const int gid = next_item(a, lane);
+        if (gid >= ng) break;
+        const GroupDesc d = group_desc(a, gid);
+        const Layout L = make_layout(d.g, lane, true, min(kTileD / 32, d.smax));
+        int rk[M];
+        double hc[M], lo[M], hi[M];
 #pragma unroll
         for (int mm = 0; mm < M; ++mm) {
-            int k = member_of(L, lane, mm, a.g);
-            int rank = (k >= 0 && k < gcnt) ? a.U[gbase + k] : -1;
-            member_init(mem[mm], a, rank, cx, cy, cz);
-            radius_terms(mem[mm], rlane, hlane);
+            const int k = member_of(L, lane, mm, d.g);
+            rk[mm] = (k >= 0 && k < d.cnt) ? a.U[d.base + k] : -1;
+            hc[mm] = rk[mm] >= 0 ? a.h64[rk[mm]] : 1.0;
+            lo[mm] = 0.0;
+            hi[mm] = __longlong_as_double(0x7ff0000000000000ll);
         }
+        for (int pass = 1;; ++pass) {
+            uint32_t cx = 0, cy = 0, cz = 0;
+            if (!group_centre<M>(a, rk, cx, cy, cz)) break;
+            DMember mem[M];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            rlane = fmaxf(rlane, __shfl_xor_sync(0xffffffffu, rlane, o));
-            hlane = fmaxf(hlane, __shfl_xor_sync(0xffffffffu, hlane, o));
-        }
-        // density: R_s = max_k (|m_k| + h_k); symmetric: R_g = max_k |m_k|, hmax_g
-        const float Rd2 = radius2_units(rlane);
-        const float Rg = rlane, hmax_g = hlane;
-        // every relevant pair difference is already the nearest image when the group's
-        // reach stays below half the box (symmetric: with the largest h of all particles)
-        const float reach = K::sym ? Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[0].w)) : rlane;
-        const bool wrap_safe = reach < 0.49f;
-
-        // export: write positions of every slot
-        if (MODE == kFill) {
+            for (int mm = 0; mm < M; ++mm) member_init(mem[mm], a, rk[mm], cx, cy, cz);
+            int64_t sup_n = 0;
+            group_search<KDens, kAcc, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, 0, sup_n);
 #pragma unroll
-            for (int mm = 0; mm < M; ++mm)
-                if (mem[mm].rank >= 0) mem[mm].xpos = a.x_off[a.perm[mem[mm].rank]];
-        }
-        int64_t sup_pos = 0, sup_n = 0;
-        if (MODE == kSupFill) sup_pos = a.x_off[gid];
-
-        // ---- walk
-        int sp = 1;
-        if (lane == 0) W.stack[0] = 0u;   // root: node 0, one node
-        int nr = 0, pending = 0;
-        __syncwarp();
-        for (;;) {
-            while (sp > 0 && pending < TCAP && nr <= kRangeCap - 32) {
-                // take range entries from the top of the stack, up to 32 nodes
-                uint32_t ent = 0;
-                int ecnt = 0;
-                if (lane < sp) {
-                    ent = W.stack[sp - 1 - lane];
-                    ecnt = (int)(ent & 7u) + 1;
-                }
-                int incl = warp_incl_scan(ecnt, lane);
-                bool take = (lane < sp) && (incl <= 32);
-                unsigned tm = __ballot_sync(0xffffffffu, take);
-                int nent = __popc(tm);
-                int nnodes = __shfl_sync(0xffffffffu, incl, nent - 1);
-                if (take) {
-                    int first = (int)(ent >> 3), ex = incl - ecnt;
-                    for (int q = 0; q < ecnt; ++q) W.nodes[ex + q] = first + q;
-                }
-                sp -= nent;
-                __syncwarp();
-                int node = lane < nnodes ? W.nodes[lane] : -1;
-                __syncwarp();
-                bool open = false, leaf = false;
-                int4 lk = make_int4(0, 0, -1, 0);
-                int nch = 0;
-                if (node >= 0) {
-                    uint4 cen = a.ncen[node];
-                    float4 ext = a.next[node];
-                    lk = a.nlink[node];
-                    nch = __float_as_int(ext.w);
-                    float gap2 = node_gap2(cen, ext, cx, cy, cz);
-                    float R2;
-                    if constexpr (!K::sym) R2 = Rd2;
-                    else R2 = radius2_units(Rg + fmaxf(hmax_g, __uint_as_float(cen.w)));
-                    open = gap2 <= R2;
-                    leaf = lk.z < 0;
-                }
-                lc.nodes += (lane == 0) ? nnodes : 0;
-                bool emit = open && leaf && lk.y > 0;
-                unsigned em = __ballot_sync(0xffffffffu, emit);
-                if (emit) {
-                    int pos = nr + __popc(em & lt);
-                    W.ranges[pos] = make_int2(lk.x, lk.y);
-                }
-                nr += __popc(em);
-                int add = emit ? lk.y : 0;
+            for (int mm = 0; mm < M; ++mm) lc.pairs += mem[mm].n;
+            if (L.S > 1) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
-                pending += add;
-                bool push = open && !leaf;
-                unsigned pm = __ballot_sync(0xffffffffu, push);
-                if (push) {
-                    int pos = sp + __popc(pm & lt);
-                    if (pos < kStackCap) W.stack[pos] = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
-                    else atomicOr(a.err, kErrStack);
-                }
-                sp = min(sp + __popc(pm), kStackCap);
-                lc.max_stack = max(lc.max_stack, sp);
-                __syncwarp();
+                for (int mm = 0; mm < M; ++mm)
+                    for (int o = d.g; o < 32; o <<= 1) slice_add(mem[mm], o);
             }
-            if (nr > 0) {
-                // ---- flush the pending leaf ranges in tiles
-                int run = 0;
-                for (int e0 = 0; e0 < nr; e0 += 32) {
-                    int e = e0 + lane;
-                    int c = e < nr ? W.ranges[e].y : 0;
-                    int inc = warp_incl_scan(c, lane);
-                    if (e < nr) W.rpre[e] = run + inc - c;
-                    run += __shfl_sync(0xffffffffu, inc, 31);
-                }
-                if (lane == 0) W.rpre[nr] = run;
-                __syncwarp();
-                const int total = run;
-                lc.cands += (lane == 0) ? total : 0;
-                for (int t0 = 0; t0 < total; t0 += TCAP) {
-                    const int nt = min(TCAP, total - t0);
-                    // first range reaching into this tile
-                    int e0 = 0;
-                    {
-                        int lo = 0, hi = nr;
-                        while (hi - lo > 1) {
-                            int mid = (lo + hi) >> 1;
-                            if (W.rpre[mid] <= t0) lo = mid; else hi = mid;
-                        }
-                        e0 = lo;
-                    }
-                    if (kSup) {
-                        if (MODE == kSupFill) {
-                            for (int e = e0 + (lane >> 4); e < nr; e += 2) {
-                                const int rb = W.rpre[e];
-                                if (rb >= t0 + nt) break;
-                                const int2 R = W.ranges[e];
-                                const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
-                                for (int gt = lo + (lane & 15); gt < hi; gt += 16) {
-                                    int64_t p = sup_pos + sup_n + gt;
-                                    if (p < a.x_cap) a.x_idx[p] = a.perm[R.x + (gt - rb)];
-                                    else atomicOr(a.err, kErrCap);
-                                }
-                            }
-                        }
-                        continue;
-                    }
-                    // the tile's piece of every range: bulk copies of every SoA array
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * K::bytes);
-                    __syncwarp();
-                    // Ranges adjacent in memory (consecutive leaves of the walk usually are)
-                    // are merged into one copy: the first range of a run (or of a 32-range
-                    // chunk) issues the copy of the whole run.
-                    for (int eb = e0; eb < nr; eb += 32) {
-                        const int e = eb + lane;
-                        int rb = 0, src = 0, dst = 0, cnt = 0;
-                        bool valid = false, cont = false;
-                        if (e < nr) {
-                            rb = W.rpre[e];
-                            valid = rb < t0 + nt;
-                        }
-                        if (valid) {
-                            const int2 R = W.ranges[e];
-                            const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
-                            src = R.x + (lo - rb);
-                            dst = lo - t0;
-                            cnt = hi - lo;
-                            if (lane > 0 && e > e0) {
-                                const int2 Q = W.ranges[e - 1];
-                                cont = Q.x + Q.y == R.x;
-                            }
-                            for (int k = 0; k < cnt; ++k) T.r[dst + k] = src + k;
-                        }
-                        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-                        if (vmask == 0u) break;
-                        const bool head = valid && !cont;
-                        const unsigned hmask = __ballot_sync(0xffffffffu, head);
-                        const int last = 31 - __clz(vmask);
-                        const int chunk_end = __shfl_sync(0xffffffffu, dst + cnt, last);
-                        const unsigned above = (lane == 31) ? 0u : (hmask >> (lane + 1)) << (lane + 1);
-                        const int nxt = above ? __ffs(above) - 1 : 0;
-                        const int nxt_dst = __shfl_sync(0xffffffffu, dst, nxt);
-                        if (head) {
-                            const int runlen = (above ? nxt_dst : chunk_end) - dst;
-                            stage_run(T, a, dst, src, (uint32_t)runlen * 16u, &W.bar);
-                        }
-                        if (vmask != 0xffffffffu) break;
-                    }
-                    if (!mbar_wait_bounded(&W.bar, tma_phase, a.err)) mbar_wait_bounded(&W.bar, tma_phase, a.err);
-                    tma_phase ^= 1u;
-                    // in place: fixed point -> coordinates relative to the centre
-                    for (int t = lane; t < nt; t += 32) {
-                        const uint4 P = *reinterpret_cast<const uint4*>(&T.p[t]);
-                        const float4 O = T.o[t];
-                        const float px = rel_coord(P.x, O.x, cx), py = rel_coord(P.y, O.y, cy),
-                                    pz = rel_coord(P.z, O.z, cz);
-                        T.p[t] = make_float4(px, py, pz, fmaf(px, px, fmaf(py, py, pz * pz)));
-                        if constexpr (K::sym) {
-                            const float hj = __uint_as_float(P.w);
-                            T.o[t] = make_float4(hj * hj, O.w, 0.0f, 0.0f);
-                        }
-                    }
-                    {
-                        // NaN dummies up to whole chunks of 32 in every slice
-                        const int padded = L.S * ((((nt + L.S - 1) / L.S) + 31) >> 5) * 32;
-                        const float nanv = __int_as_float(0x7fffffff);
-                        for (int t = nt + lane; t < padded; t += 32) T.p[t] = make_float4(nanv, nanv, nanv, nanv);
-                    }
-                    __syncwarp();
-                    if (wrap_safe) filter_tile<K, MODE, M, false>(T, L, mem, nt, a, lc, lane);
-                    else filter_tile<K, MODE, M, true>(T, L, mem, nt, a, lc, lane);
-                    __syncwarp();
-                }
-                if (kSup) sup_n += total;
-                nr = 0;
-                pending = 0;
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+                if (rk[mm] >= 0 &&
+                    hsml_step(a, it, rk[mm], hc[mm], lo[mm], hi[mm], mem[mm].s0 - mem[mm].c0, mem[mm].s1 - mem[mm].c1,
+                              mem[mm].n, pass, L.slice == 0))
+                    rk[mm] = -1;
             }
-            if (sp == 0) break;
-        }
-
-        // ---- results
-#pragma unroll
-        for (int mm = 0; mm < M; ++mm) lc.pairs += mem[mm].n;
-        if (kSup) {
-            if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
-            continue;
-        }
-        if (L.S > 1) {
-#pragma unroll
-            for (int mm = 0; mm < M; ++mm)
-                for (int o = a.g; o < 32; o <<= 1) slice_add(mem[mm], o);
-        }
-        if (L.slice == 0) {
-#pragma unroll
-            for (int mm = 0; mm < M; ++mm)
-                if (mem[mm].rank >= 0) write_result<MODE>(mem[mm], a);
+            // the new h (global memory) is read by the next pass's FP64 re-tests
+            __syncwarp();
         }
     }
     flush_counters(a, lc, lane);
@@ -1355,11 +1545,11 @@ static size_t group_smem() {
     return kWarpsPerBlock * (sizeof(WalkSmem) + sizeof(typename K::Tile));
 }
 
-template <class K, int MODE, int M>
-static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
-    auto kern = k_group<K, MODE, M>;
-    size_t sh = group_smem<K>();
-    static bool configured = false;
+// Persistent grid: every resident block slot of the GPU (at most one block per four
+// groups when the group count is known on the host).
+template <typename Kern, typename... Args>
+static int launch_persistent(Kern kern, bool& configured, size_t sh, int64_t ngroups_host, int sm_count,
+                             cudaStream_t s, const char* what, Args... args) {
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
         configured = true;
@@ -1367,12 +1557,19 @@ static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, sh);
     if (per_sm < 1) per_sm = 1;
-    int64_t want = (a.ngroups + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    int64_t grid = std::min<int64_t>((int64_t)per_sm * sm_count, want);
+    int64_t grid = (int64_t)per_sm * sm_count;
+    if (ngroups_host >= 0) grid = std::min<int64_t>(grid, (ngroups_host + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, kWarpsPerBlock * 32, sh, s>>>(a);
+    kern<<<(unsigned)grid, kWarpsPerBlock * 32, sh, s>>>(args...);
     note_launch();
-    return check_cuda(cudaGetLastError(), "grouped search kernel");
+    return check_cuda(cudaGetLastError(), what);
+}
+
+template <class K, int MODE, int M>
+static int launch_group_t(const SearchArgs& a, int sm_count, cudaStream_t s) {
+    static bool configured = false;
+    return launch_persistent(k_group<K, MODE, M>, configured, group_smem<K>(), a.ngroups_dev ? -1 : a.ngroups,
+                             sm_count, s, "grouped search kernel", a);
 }
 
 template <class K, int MODE>
@@ -1394,6 +1591,66 @@ static int launch_group_k(const SearchArgs& a, int mode, int sm_count, cudaStrea
         case kSupFill: return launch_group_m<K, kSupFill>(a, sm_count, s);
     }
     return set_error(SPHGRP_EINVAL, "bad search mode");
+}
+
+static int members_per_lane(int max_g) { return max_g <= 32 ? 1 : (max_g <= 64 ? 2 : 4); }
+
+int launch_search_dev(const SearchArgs& a, int kind, int max_g, int sm_count, cudaStream_t s) {
+    if (max_g < 1 || max_g > 128) return set_error(SPHGRP_EINVAL, "group size outside [1, 128]");
+    cudaMemsetAsync(a.work, 0, sizeof(int), s);
+    SearchArgs b = a;
+    b.g = max_g;   // selects the member slots per lane; groups4 carries every group's size
+    switch (kind) {
+        case kKindDensity: return launch_group_m<KDens, kAcc>(b, sm_count, s);
+        case kKindHydro: return launch_group_m<KHydro, kAcc>(b, sm_count, s);
+        case kKindHydroAdj: return launch_group_m<KHAdj, kAcc>(b, sm_count, s);
+        case kKindDensityAdj: return launch_group_m<KDAdj, kAcc>(b, sm_count, s);
+    }
+    return set_error(SPHGRP_EINVAL, "bad kind");
+}
+
+template <int M>
+static int launch_iter_t(const SearchArgs& a, const IterArgs& it, int sm_count, cudaStream_t s) {
+    static bool configured = false;
+    return launch_persistent(k_group_dens_iter<M>, configured, group_smem<KDens>(), a.ngroups_dev ? -1 : a.ngroups,
+                             sm_count, s, "grouped density iteration kernel", a, it);
+}
+
+int launch_density_iter(const SearchArgs& a, const IterArgs& it, int max_g, int sm_count, cudaStream_t s) {
+    if (max_g < 1 || max_g > 128) return set_error(SPHGRP_EINVAL, "group size outside [1, 128]");
+    cudaMemsetAsync(a.work, 0, sizeof(int), s);
+    switch (members_per_lane(max_g)) {
+        case 1: return launch_iter_t<1>(a, it, sm_count, s);
+        case 2: return launch_iter_t<2>(a, it, sm_count, s);
+        default: return launch_iter_t<4>(a, it, sm_count, s);
+    }
+}
+
+template <class K0, class K1, int M>
+static int launch_pair_t(const SearchArgs& a0, const SearchArgs& a1, int sm_count, cudaStream_t s) {
+    static bool configured = false;
+    constexpr size_t tile = sizeof(typename K0::Tile) > sizeof(typename K1::Tile) ? sizeof(typename K0::Tile)
+                                                                                  : sizeof(typename K1::Tile);
+    const size_t sh = kWarpsPerBlock * (sizeof(WalkSmem) + tile);
+    return launch_persistent(k_group_pair<K0, K1, M>, configured, sh, -1, sm_count, s, "paired search kernel", a0,
+                             a1);
+}
+
+template <class K0, class K1>
+static int launch_pair_m(const SearchArgs& a0, const SearchArgs& a1, int max_g, int sm_count, cudaStream_t s) {
+    switch (members_per_lane(max_g)) {
+        case 1: return launch_pair_t<K0, K1, 1>(a0, a1, sm_count, s);
+        case 2: return launch_pair_t<K0, K1, 2>(a0, a1, sm_count, s);
+        default: return launch_pair_t<K0, K1, 4>(a0, a1, sm_count, s);
+    }
+}
+
+int launch_search_pair(const SearchArgs& a0, int kind0, const SearchArgs& a1, int kind1, int max_g, int sm_count,
+                       cudaStream_t s) {
+    if (max_g < 1 || max_g > 128) return set_error(SPHGRP_EINVAL, "group size outside [1, 128]");
+    cudaMemsetAsync(a0.work, 0, sizeof(int), s);
+    if (kind0 == kKindHydro && kind1 == kKindHydroAdj) return launch_pair_m<KHydro, KHAdj>(a0, a1, max_g, sm_count, s);
+    return set_error(SPHGRP_EINVAL, "unsupported kind pair");
 }
 
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s) {

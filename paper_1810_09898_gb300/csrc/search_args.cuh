@@ -33,6 +33,8 @@ struct SearchArgs {
     int ngroups;
     bool centre_box; // group sphere centred on the members' box (else on the first member)
     const int2* groups; // (first entry of U, count) per group; null: chunks of g
+    const int4* groups4; // batch groups: (first entry of U, count, root node, g | max_slices << 8)
+    const int* ngroups_dev; // device group count (graph-capturable launches); null: ngroups
     // density pass results (rank space)
     float* o_s0;
     float* o_s1;
@@ -87,7 +89,28 @@ struct UpdateArgs {
     int* nfail;
 };
 
+// smoothing-length iteration inside the grouped density kernel (batch path)
+struct IterArgs {
+    double nngb, tol;
+    int max_iter;
+    double* h64;          // rank order, updated in place
+    uint4* pfix;          // .w = FP32 copy of h
+    // results (original order)
+    double* h_out;
+    float* rho;
+    float* drhodh;
+    float* fgrad;
+    int32_t* nngb_out;
+    int32_t* iters;
+    int* nfail;
+};
+
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s);
+// persistent launches over a device-side group count (a.ngroups_dev), graph-capturable
+int launch_search_dev(const SearchArgs& a, int kind, int max_g, int sm_count, cudaStream_t s);
+int launch_density_iter(const SearchArgs& a, const IterArgs& it, int max_g, int sm_count, cudaStream_t s);
+int launch_search_pair(const SearchArgs& a0, int kind0, const SearchArgs& a1, int kind1, int max_g, int sm_count,
+                       cudaStream_t s);
 int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
 int launch_split_groups(const int32_t* U, int nu, int g, float split, const uint4* pfix, const double* h64,
                         int2* tmp, int32_t* cnt, cudaStream_t s);
@@ -96,6 +119,16 @@ int launch_gather_groups(int nch, int g, const int2* tmp, const int32_t* cnt, co
 int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s);
 int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
                        cudaStream_t s);
+
+// per-particle kernels shared by the entry points (api.cu, backward.cu)
+int launch_gather_h(Ctx* c, const double* h, cudaStream_t s);
+int launch_hydro_prep(Ctx* c, const double* h, const float* rho, const float* fgrad, const float* vel,
+                      const float* u, cudaStream_t s);
+int backward_buffers(Ctx* c);
+int launch_bwd_prep(Ctx* c, const float* vel, const float* u, const float* g_acc, float4* hyd0, float4* hyd1,
+                    cudaStream_t s);
+int launch_bwd_chain(Ctx* c, const float* u, const float* g_rho, cudaStream_t s);
+int launch_bwd_combine(Ctx* c, float* g_pos, float* g_vel, float* g_m, cudaStream_t s);
 
 // call orchestration shared by the entry points (api.cu)
 int finish(Ctx* c, cudaStream_t s, int rc);

@@ -2,6 +2,8 @@
 // exclusive scan (Sec. 2.2: Gadget3 orders its particles along the Hilbert curve).
 #include <cooperative_groups.h>
 
+#include <utility>
+
 #include "sph_internal.cuh"
 
 namespace sphgrp {
@@ -307,6 +309,155 @@ int sort_keys(Ctx* c, int64_t n, const double* pos, cudaStream_t s) {
     k_invert_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->rank_of);
     note_launch();
     return check_cuda(cudaGetLastError(), "sort");
+}
+
+// ---------------------------------------------------------------------------------
+// Scan over a count held in device memory (n = *n_hi - *n_lo, at most n_bound), for
+// graph-captured sequences: the grids cover n_bound; tiles beyond n contribute zero.
+// ---------------------------------------------------------------------------------
+
+__device__ __forceinline__ int64_t dev_count(const int32_t* n_hi, const int32_t* n_lo, int64_t n_bound) {
+    int64_t n = (int64_t)*n_hi - (n_lo ? (int64_t)*n_lo : 0);
+    return n < 0 ? 0 : (n > n_bound ? n_bound : n);
+}
+
+template <typename T>
+__global__ void k_scan_reduce_dev(const T* __restrict__ in, const int32_t* n_hi, const int32_t* n_lo,
+                                  int64_t n_bound, T* __restrict__ sums) {
+    __shared__ T wt[33];
+    const int64_t n = dev_count(n_hi, n_lo, n_bound);
+    const int64_t tile0 = blockIdx.x * (int64_t)kScanTile;
+    if (tile0 >= n) {   // block-uniform
+        if (threadIdx.x == 0) sums[blockIdx.x] = T(0);
+        return;
+    }
+    int64_t base = tile0 + threadIdx.x * kScanItems;
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    T tot;
+    block_exclusive<T>(s, wt, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename T>
+__global__ void k_scan_down_dev(const T* in, T* out, const int32_t* n_hi, const int32_t* n_lo, int64_t n_bound,
+                                const T* __restrict__ carry, T* total) {
+    __shared__ T wt[33];
+    const int64_t n = dev_count(n_hi, n_lo, n_bound);
+    const int64_t tile0 = blockIdx.x * (int64_t)kScanTile;
+    const bool last_block = blockIdx.x == gridDim.x - 1;
+    if (tile0 >= n && !last_block) return;   // block-uniform
+    int64_t base = tile0 + threadIdx.x * kScanItems;
+    T v[kScanItems];
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (base + k < n) ? in[base + k] : T(0);
+        s += v[k];
+    }
+    T tot;
+    T ex = block_exclusive<T>(s, wt, tot);
+    T c = carry ? carry[blockIdx.x] : T(0);
+    T run = c + ex;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (total && last_block && threadIdx.x == blockDim.x - 1) *total = c + tot;
+}
+
+int exclusive_scan_i32_dev(Ctx* c, const int32_t* in, int32_t* out, const int32_t* n_hi, const int32_t* n_lo,
+                           int64_t n_bound, int32_t* total_dev, cudaStream_t s) {
+    if (n_bound <= 0) n_bound = 1;
+    const int64_t nb = (n_bound + kScanTile - 1) / kScanTile;
+    if (nb <= 1) {
+        k_scan_down_dev<int32_t><<<1, kScanThreads, 0, s>>>(in, out, n_hi, n_lo, n_bound, nullptr, total_dev);
+        note_launch();
+        return check_cuda(cudaGetLastError(), "scan (device count)");
+    }
+    if (scan_aux_need(nb) + nb > c->scan_aux_cap) return set_error(SPHGRP_EOVERFLOW, "scan scratch too small");
+    k_scan_reduce_dev<int32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n_hi, n_lo, n_bound, c->scan_aux);
+    note_launch();
+    scan_rec<int32_t>(c->scan_aux, c->scan_aux, nb, c->scan_aux + nb, nullptr, s);
+    k_scan_down_dev<int32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n_hi, n_lo, n_bound, c->scan_aux,
+                                                                    total_dev);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "scan (device count)");
+}
+
+// ---------------------------------------------------------------------------------
+// Sort of several boxes at once: keys as above, then one stable pass per byte of the
+// box index, so that the order is (box, key); the context's keys and perm end in
+// that order and box_of_rank holds every rank's box.
+// ---------------------------------------------------------------------------------
+
+__global__ void k_box_digit(int64_t n, const int32_t* __restrict__ perm, const int64_t* __restrict__ box_off,
+                            int nbox, uint64_t* __restrict__ dkey) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t i = perm[r];
+    int lo = 0, hi = nbox;   // box_off[lo] <= i < box_off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (box_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    dkey[r] = (uint64_t)lo;
+}
+
+__global__ void k_box_gather(int64_t n, const int32_t* __restrict__ src, const uint64_t* __restrict__ keys,
+                             const int32_t* __restrict__ perm, const uint64_t* __restrict__ dkey,
+                             uint64_t* __restrict__ keys_out, int32_t* __restrict__ perm_out,
+                             int32_t* __restrict__ box_of_rank) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int32_t r = src[p];
+    keys_out[p] = keys[r];
+    perm_out[p] = perm[r];
+    box_of_rank[p] = (int32_t)dkey[p];
+}
+
+int sort_keys_boxed(Ctx* c, int64_t n, const double* pos, const int64_t* box_off_dev, int nbox, uint64_t* tmp64a,
+                    uint64_t* tmp64b, int32_t* tmp32a, int32_t* tmp32b, int32_t* box_of_rank, cudaStream_t s) {
+    int rc = sort_keys(c, n, pos, s);
+    if (rc) return rc;
+    if (nbox <= 1) {
+        cudaMemsetAsync(box_of_rank, 0, n * sizeof(int32_t), s);
+        return check_cuda(cudaGetLastError(), "box sort");
+    }
+    k_box_digit<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, box_off_dev, nbox, tmp64a);
+    note_launch();
+    const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
+    const int64_t nh = (int64_t)256 * nblocks;
+    if (nh > c->hist_cap) return set_error(SPHGRP_EOVERFLOW, "radix histogram scratch too small");
+    const int passes = nbox > 256 ? 2 : 1;
+    uint64_t* kin = tmp64a;
+    uint64_t* kout = tmp64b;
+    const int32_t* vin = nullptr;
+    int32_t* vout = tmp32a;
+    for (int pass = 0; pass < passes; ++pass) {
+        k_radix_hist<<<nblocks, kSortThreads, 0, s>>>(kin, n, 8 * pass, c->hist, nblocks);
+        note_launch();
+        if ((rc = exclusive_scan_i32(c, reinterpret_cast<const int32_t*>(c->hist), reinterpret_cast<int32_t*>(c->hist),
+                                     nh, nullptr, s)))
+            return rc;
+        k_radix_scatter<<<nblocks, kSortThreads, 0, s>>>(kin, vin, kout, vout, n, 8 * pass, c->hist, nblocks);
+        note_launch();
+        std::swap(kin, kout);
+        vin = vout;
+        vout = (vout == tmp32a) ? tmp32b : tmp32a;
+    }
+    // kin: box digits in (box, key) order; vin: the rank in key order of every position
+    k_box_gather<<<blocks_for(n, 256), 256, 0, s>>>(n, vin, c->keys, c->perm, kin, c->keys_alt, c->perm_alt,
+                                                     box_of_rank);
+    note_launch();
+    std::swap(c->keys, c->keys_alt);
+    std::swap(c->perm, c->perm_alt);
+    k_invert_perm<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, c->rank_of);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "box sort");
 }
 
 // The same keys + stable radix sort on caller-provided buffers: the sorted keys and

@@ -206,5 +206,15 @@ int exclusive_scan_i32(Ctx* c, const int32_t* in, int32_t* out, int64_t n,
                        int32_t* total_dev, cudaStream_t s);                        // sort.cu
 int build_tree(Ctx* c, cudaStream_t s);                                            // tree.cu
 int refresh_hmax(Ctx* c, cudaStream_t s);                                          // tree.cu
+int exclusive_scan_i32_dev(Ctx* c, const int32_t* in, int32_t* out, const int32_t* n_hi, const int32_t* n_lo,
+                           int64_t n_bound, int32_t* total_dev, cudaStream_t s);            // sort.cu
+int sort_keys_boxed(Ctx* c, int64_t n, const double* pos, const int64_t* box_off_dev, int nbox, uint64_t* tmp64a,
+                    uint64_t* tmp64b, int32_t* tmp32a, int32_t* tmp32b, int32_t* box_of_rank,
+                    cudaStream_t s);                                                        // sort.cu
+int alloc_forest(Ctx* c, int64_t cap);                                                     // tree.cu
+int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uint4* blo, uint4* bhi,
+                 int32_t* tot, cudaStream_t s);                                            // tree.cu
+int refresh_hmax_forest(Ctx* c, const int32_t* lvl, cudaStream_t s);                       // tree.cu
+void note_launches(long long k);                                                           // api.cu
 
 }  // namespace sphgrp

@@ -265,6 +265,215 @@ int refresh_hmax(Ctx* c, cudaStream_t s) {
     return check_cuda(cudaGetLastError(), "hmax refresh");
 }
 
+// ---------------------------------------------------------------------------------
+// Forest of one octree per box (batch path).  Box k's particles are the ranks
+// [box_off[k], box_off[k+1]) (sorted by box, then key); node k < nbox is box k's
+// root.  Levels are built as above, but every count stays on the device (the level
+// table lvl, lvl[L] = first node of level L), so that the whole build can be captured
+// in a CUDA graph: the kernels of a level run over a grid-stride range read from lvl.
+// ---------------------------------------------------------------------------------
+
+constexpr int kForestGrid = 1024;   // blocks of the grid-stride kernels
+
+__global__ void k_forest_roots(int nbox, const int64_t* __restrict__ box_off, int4* __restrict__ nlink,
+                               float4* __restrict__ next, int32_t* __restrict__ nlevel, int32_t* __restrict__ lvl) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nbox) {
+        nlink[k] = make_int4((int)box_off[k], (int)(box_off[k + 1] - box_off[k]), -1, -1);
+        next[k] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
+        nlevel[k] = 0;
+    }
+    if (k <= kKeyLevels + 2) lvl[k] = (k == 0) ? 0 : nbox;
+}
+
+__global__ void k_split_count_dev(const uint64_t* __restrict__ keys, const int4* __restrict__ nlink,
+                                  const int32_t* __restrict__ lvl, int level, int leaf_size,
+                                  int32_t* __restrict__ nchild) {
+    const int a = lvl[level], nf = lvl[level + 1] - a;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        int4 L = nlink[a + k];
+        int cnt = 0;
+        if (L.y > leaf_size && level < kKeyLevels) {
+            int shift = 3 * (kKeyLevels - 1 - level);
+            int lo = L.x, hi = L.x + L.y;
+            int prev = lo;
+            for (int d = 1; d <= 8; ++d) {
+                int b = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
+                if (b > prev) ++cnt;
+                prev = b;
+            }
+        }
+        nchild[k] = cnt;
+    }
+}
+
+// children of one level; nodes beyond the capacity are not created (their parent stays
+// a leaf, the error flag is set and the results of the call are invalid)
+__global__ void k_split_write_dev(const uint64_t* __restrict__ keys, int4* __restrict__ nlink,
+                                  float4* __restrict__ next, int32_t* __restrict__ nlevel, int32_t* lvl, int level,
+                                  const int32_t* __restrict__ nchild, const int32_t* __restrict__ coff,
+                                  const int32_t* __restrict__ total, int64_t cap, unsigned* err) {
+    const int a = lvl[level], b = lvl[level + 1], nf = b - a;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        const int nc = nchild[k];
+        int4 L = nlink[a + k];
+        const int child0 = b + coff[k];
+        if (nc == 0 || (int64_t)child0 + nc > cap) {
+            if (nc > 0) atomicOr(err, kErrNodes);
+            next[a + k].w = __int_as_float(0);
+            continue;
+        }
+        next[a + k].w = __int_as_float(nc);
+        const int shift = 3 * (kKeyLevels - 1 - level);
+        const int lo = L.x, hi = L.x + L.y;
+        int prev = lo, c = 0;
+        for (int d = 1; d <= 8; ++d) {
+            const int e = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
+            if (e > prev) {
+                const int id = child0 + c;
+                const int skip = (c + 1 < nc) ? id + 1 : L.w;
+                nlink[id] = make_int4(prev, e - prev, -1, skip);
+                next[id] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
+                nlevel[id] = level + 1;
+                ++c;
+            }
+            prev = e;
+        }
+        L.z = child0;
+        nlink[a + k] = L;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) lvl[level + 2] = (int)min((int64_t)b + *total, cap);
+}
+
+__global__ void k_box_level_dev(const int32_t* __restrict__ lvl, int level, const int4* __restrict__ nlink,
+                                const float4* __restrict__ next, const uint4* __restrict__ pfix,
+                                uint4* __restrict__ blo, uint4* __restrict__ bhi, uint4* __restrict__ ncen) {
+    const int a = lvl[level], nf = lvl[level + 1] - a;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        const int id = a + k;
+        const int4 L = nlink[id];
+        uint32_t lx = 0xffffffffu, ly = 0xffffffffu, lz = 0xffffffffu, hx = 0, hy = 0, hz = 0;
+        float hm = 0.0f;
+        const int nc = __float_as_int(next[id].w);
+        if (nc == 0) {
+            for (int q = L.x; q < L.x + L.y; ++q) {
+                const uint4 P = pfix[q];
+                lx = min(lx, P.x); ly = min(ly, P.y); lz = min(lz, P.z);
+                hx = max(hx, P.x); hy = max(hy, P.y); hz = max(hz, P.z);
+                hm = fmaxf(hm, __uint_as_float(P.w));
+            }
+        } else {
+            for (int c = L.z; c < L.z + nc; ++c) {
+                const uint4 l = blo[c], h = bhi[c];
+                lx = min(lx, l.x); ly = min(ly, l.y); lz = min(lz, l.z);
+                hx = max(hx, h.x); hy = max(hy, h.y); hz = max(hz, h.z);
+                hm = fmaxf(hm, __uint_as_float(ncen[c].w));
+            }
+        }
+        if (L.y == 0) lx = ly = lz = hx = hy = hz = 0u;   // an empty box
+        blo[id] = make_uint4(lx, ly, lz, 0u);
+        bhi[id] = make_uint4(hx, hy, hz, 0u);
+        ncen[id].w = __float_as_uint(hm);
+    }
+}
+
+__global__ void k_box_final_dev(const int32_t* __restrict__ lvl, const uint4* __restrict__ blo,
+                                const uint4* __restrict__ bhi, uint4* __restrict__ ncen, float4* __restrict__ next) {
+    const int64_t nn = lvl[kKeyLevels + 1];
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < nn; id += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 l = blo[id], h = bhi[id];
+        uint4 C = ncen[id];
+        const uint64_t wx = (uint64_t)h.x - l.x + 1, wy = (uint64_t)h.y - l.y + 1, wz = (uint64_t)h.z - l.z + 1;
+        C.x = l.x + (uint32_t)(wx >> 1);
+        C.y = l.y + (uint32_t)(wy >> 1);
+        C.z = l.z + (uint32_t)(wz >> 1);
+        ncen[id] = C;
+        float4 E = next[id];
+        E.x = __fmul_ru(__ull2float_ru(wx + 1), 0.5f);
+        E.y = __fmul_ru(__ull2float_ru(wy + 1), 0.5f);
+        E.z = __fmul_ru(__ull2float_ru(wz + 1), 0.5f);
+        next[id] = E;
+    }
+}
+
+__global__ void k_hmax_level_dev(const int32_t* __restrict__ lvl, int level, const int4* __restrict__ nlink,
+                                 const float4* __restrict__ next, const uint4* __restrict__ pfix,
+                                 uint4* __restrict__ ncen) {
+    const int a = lvl[level], nf = lvl[level + 1] - a;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        const int id = a + k;
+        const int4 L = nlink[id];
+        const int nc = __float_as_int(next[id].w);
+        float hm = 0.0f;
+        if (nc == 0) {
+            for (int q = L.x; q < L.x + L.y; ++q) hm = fmaxf(hm, __uint_as_float(pfix[q].w));
+        } else {
+            for (int c = L.z; c < L.z + nc; ++c) hm = fmaxf(hm, __uint_as_float(ncen[c].w));
+        }
+        ncen[id].w = __float_as_uint(hm);
+    }
+}
+
+int alloc_forest(Ctx* c, int64_t cap) {
+    Tree& t = c->tree;
+    if (t.cap >= cap) return SPHGRP_OK;
+    if (t.ncen) {
+        cudaFree(t.ncen);
+        cudaFree(t.next);
+        cudaFree(t.nlink);
+        cudaFree(t.nlevel);
+        t.ncen = nullptr;
+        t.next = nullptr;
+        t.nlink = nullptr;
+        t.nlevel = nullptr;
+        t.cap = 0;
+    }
+    if (cudaMalloc(&t.ncen, cap * sizeof(uint4)) != cudaSuccess ||
+        cudaMalloc(&t.next, cap * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&t.nlink, cap * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&t.nlevel, cap * sizeof(int32_t)) != cudaSuccess)
+        return set_error(SPHGRP_ENOMEM, "forest allocation failed");
+    t.cap = cap;
+    return SPHGRP_OK;
+}
+
+// lvl: device, kKeyLevels + 3 entries; blo/bhi: device scratch of t.cap entries;
+// tot: one device int.  Uses c->flag and c->scan as per-level scratch.
+int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uint4* blo, uint4* bhi, int32_t* tot,
+                 cudaStream_t s) {
+    Tree& t = c->tree;
+    const int64_t n = c->n;
+    k_forest_roots<<<blocks_for(std::max(nbox, kKeyLevels + 3), 256), 256, 0, s>>>(nbox, box_off_dev, t.nlink,
+                                                                                 t.next, t.nlevel, lvl);
+    note_launch();
+    int rc = SPHGRP_OK;
+    for (int level = 0; level < kKeyLevels; ++level) {
+        k_split_count_dev<<<kForestGrid, 256, 0, s>>>(c->keys, t.nlink, lvl, level, c->p.leaf_size, c->flag);
+        note_launch();
+        if ((rc = exclusive_scan_i32_dev(c, c->flag, c->scan, lvl + level + 1, lvl + level, n, tot, s))) return rc;
+        k_split_write_dev<<<kForestGrid, 256, 0, s>>>(c->keys, t.nlink, t.next, t.nlevel, lvl, level, c->flag,
+                                                      c->scan, tot, t.cap, c->err);
+        note_launch();
+    }
+    // lvl[kKeyLevels + 1] = node count
+    for (int level = kKeyLevels; level >= 0; --level) {
+        k_box_level_dev<<<kForestGrid, 128, 0, s>>>(lvl, level, t.nlink, t.next, c->pfix, blo, bhi, t.ncen);
+        note_launch();
+    }
+    k_box_final_dev<<<kForestGrid, 256, 0, s>>>(lvl, blo, bhi, t.ncen, t.next);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "forest build");
+}
+
+int refresh_hmax_forest(Ctx* c, const int32_t* lvl, cudaStream_t s) {
+    Tree& t = c->tree;
+    for (int level = kKeyLevels; level >= 0; --level) {
+        k_hmax_level_dev<<<kForestGrid, 128, 0, s>>>(lvl, level, t.nlink, t.next, c->pfix, t.ncen);
+        note_launch();
+    }
+    return check_cuda(cudaGetLastError(), "forest hmax refresh");
+}
+
 int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s) {
     k_gather<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, pos, m, c->xd, c->yd, c->zd,
                                                   c->pfix, c->poff);

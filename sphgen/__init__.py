@@ -161,3 +161,41 @@ def lattice(n_side: int) -> np.ndarray:
     g = (np.arange(n_side) + 0.5) / n_side
     x, y, z = np.meshgrid(g, g, g, indexing="ij")
     return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+def batch(nbox: int, n_min: int, n_max: int, config: int = 5, seed_salt: int = 0,
+          frac_min: float = 0.01, frac_max: float = 1.0) -> dict:
+    """Many independent periodic boxes, concatenated (the batched workload).
+
+    Per box: N log-uniform in [n_min, n_max], uniform or clustered by a fair coin,
+    active fraction uniform in [frac_min, frac_max] (each particle active with that
+    probability, at least one per box).  Box k's particles are the rows
+    box_off[k] .. box_off[k+1] of every array; box_class is 0 for uniform, 1 for
+    clustered; h0 is each box's own initial guess, per particle."""
+    rng = rng_for(config, seed_salt)
+    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), nbox)).astype(np.int64)
+    kinds = np.where(rng.random(nbox) < 0.5, "uniform", "clustered")
+    fracs = rng.uniform(frac_min, frac_max, nbox)
+    parts = []
+    for k in range(nbox):
+        d = make(str(kinds[k]), int(sizes[k]), config=config, seed_salt=1000 * (seed_salt + 1) + k)
+        act = rng.random(int(sizes[k])) < fracs[k]
+        if not act.any():
+            act[rng.integers(0, int(sizes[k]))] = True
+        d["active"] = act
+        parts.append(d)
+    box_off = np.zeros(nbox + 1, dtype=np.int64)
+    box_off[1:] = np.cumsum(sizes)
+    cat = lambda key: np.concatenate([p[key] for p in parts])  # noqa: E731
+    return {
+        "pos": np.ascontiguousarray(cat("pos")),
+        "m": cat("m"),
+        "vel": cat("vel"),
+        "u": cat("u"),
+        "h0": np.concatenate([np.full(p["n"], p["h0"]) for p in parts]),
+        "active": cat("active"),
+        "box_off": box_off,
+        "box_class": (kinds == "clustered").astype(np.int32),
+        "kinds": kinds,
+        "fracs": fracs,
+    }
