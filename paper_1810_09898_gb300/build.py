@@ -63,5 +63,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+    extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
+    extra += [a for a in sys.argv[1:] if a.startswith("-D")]   # tuning macros, e.g. -DSPHGRP_GROUP_MIN_BLOCKS=6
+    print(build(force="--force" in sys.argv or any(a.startswith("-D") for a in sys.argv[1:]),
+                verbose="-v" in sys.argv, extra=extra or None))

@@ -24,9 +24,14 @@
 
 namespace sphgrp {
 
+#ifndef SPHGRP_STACK_CAP
+#define SPHGRP_STACK_CAP 256
+#endif
+
 constexpr int kWarpsPerBlock = 4;
-constexpr int kStackCap = 512;
-constexpr int kRangeCap = 96;
+constexpr int kStackCap = SPHGRP_STACK_CAP;   // walk stack entries in shared memory
+constexpr int kRangeCap = 64;                  // pending leaf ranges
+constexpr int kSpillCap = kStackSpillPerWarp;  // overflow entries per warp (global memory)
 constexpr int kTileD = 128;   // density tile (candidates)
 constexpr int kTileH = 128;   // hydro tile
 constexpr int kTileA = 128;   // adjoint tiles
@@ -377,6 +382,7 @@ struct DAdjTile {
 
 // kind policies
 struct KDens {
+    static constexpr int min_blocks = 7;   // resident blocks per SM (register budget; 0: compiler's choice)
     static constexpr int id = 0;
     static constexpr bool sym = false;
     static constexpr int cap = kTileD;
@@ -385,6 +391,7 @@ struct KDens {
     using Tile = DensTile;
 };
 struct KHydro {
+    static constexpr int min_blocks = 5;   // resident blocks per SM (register budget; 0: compiler's choice)
     static constexpr int id = 1;
     static constexpr bool sym = true;
     static constexpr int cap = kTileH;
@@ -393,6 +400,7 @@ struct KHydro {
     using Tile = HydroTile;
 };
 struct KHAdj {
+    static constexpr int min_blocks = 0;   // resident blocks per SM (register budget; 0: compiler's choice)
     static constexpr int id = 2;
     static constexpr bool sym = true;
     static constexpr int cap = kTileA;
@@ -401,6 +409,7 @@ struct KHAdj {
     using Tile = HAdjTile;
 };
 struct KDAdj {
+    static constexpr int min_blocks = 6;   // resident blocks per SM (register budget; 0: compiler's choice)
     static constexpr int id = 3;
     static constexpr bool sym = true;
     static constexpr int cap = kTileA;
@@ -917,6 +926,10 @@ __device__ __forceinline__ GroupDesc group_desc(const SearchArgs& a, int gid) {
         d.base = gid * a.g;
         d.cnt = min(a.g, a.nu - d.base);
     }
+    // member slots: the group's count rounded up to a power of two, so that a group cut
+    // smaller by the split keeps every lane busy with more slices
+    const int p2 = d.cnt <= 1 ? 1 : 1 << (32 - __clz(d.cnt - 1));
+    d.g = min(d.g, p2);
     return d;
 }
 
@@ -998,12 +1011,23 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
     const float reach = K::sym ? Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[root].w)) : rlane;
     const bool wrap_safe = reach < 0.49f;
 
-    int sp = 1;
+    // The stack lives in shared memory; entries that do not fit go to this warp's
+    // overflow area in global memory (a second stack, drained when the first is empty:
+    // the order of the walk changes, the superset does not).
+    uint32_t* spill = a.stack_spill + (size_t)(blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kSpillCap;
+    int sp = 1, gsp = 0;
     if (lane == 0) W.stack[0] = (uint32_t)root << 3;   // one node
     int nr = 0, pending = 0;
     __syncwarp();
     for (;;) {
-        while (sp > 0 && pending < TCAP && nr <= kRangeCap - 32) {
+        while ((sp > 0 || gsp > 0) && pending < TCAP && nr <= kRangeCap - 32) {
+            if (sp == 0) {
+                const int m = min(gsp, 32);
+                if (lane < m) W.stack[lane] = spill[gsp - m + lane];
+                gsp -= m;
+                sp = m;
+                __syncwarp();
+            }
             // take range entries from the top of the stack, up to 32 nodes
             uint32_t ent = 0;
             int ecnt = 0;
@@ -1053,13 +1077,26 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             pending += add;
             bool push = open && !leaf;
             unsigned pm = __ballot_sync(0xffffffffu, push);
+            const int npush = __popc(pm);
+            const int room = kStackCap - sp;
             if (push) {
-                int pos = sp + __popc(pm & lt);
-                if (pos < kStackCap) W.stack[pos] = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
-                else atomicOr(a.err, kErrStack);
+                const int k = __popc(pm & lt);
+                const uint32_t v = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
+                if (k < room) {
+                    W.stack[sp + k] = v;
+                } else {
+                    const int q = gsp + (k - room);
+                    if (q < kSpillCap) spill[q] = v;
+                    else atomicOr(a.err, kErrStack);
+                }
             }
-            sp = min(sp + __popc(pm), kStackCap);
-            lc.max_stack = max(lc.max_stack, sp);
+            if (npush > room) {
+                gsp = min(gsp + npush - room, kSpillCap);
+                sp = kStackCap;
+            } else {
+                sp += npush;
+            }
+            lc.max_stack = max(lc.max_stack, sp + gsp);
             __syncwarp();
         }
         if (nr > 0) {
@@ -1176,7 +1213,7 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             nr = 0;
             pending = 0;
         }
-        if (sp == 0) break;
+        if (sp == 0 && gsp == 0) break;
     }
 }
 
@@ -1233,7 +1270,7 @@ __device__ __forceinline__ int next_item(const SearchArgs& a, int lane) {
 }
 
 template <class K, int MODE, int M>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, M == 1 ? K::min_blocks : 0)
 k_group(SearchArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1256,7 +1293,8 @@ k_group(SearchArgs a) {
 // Two kinds of work item in one persistent queue: the groups of a0 (kind K0) first,
 // then those of a1 (kind K1).  Both share the work counter of a0.
 template <class K0, class K1, int M>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32,
+                                  M > 1 ? 0 : (K0::min_blocks < K1::min_blocks ? K0::min_blocks : K1::min_blocks))
 k_group_pair(SearchArgs a0, SearchArgs a1) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr size_t kTileBytes = sizeof(typename K0::Tile) > sizeof(typename K1::Tile) ? sizeof(typename K0::Tile)
@@ -1331,7 +1369,7 @@ __device__ __forceinline__ bool hsml_step(const SearchArgs& a, const IterArgs& i
 }
 
 template <int M>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, M == 1 ? 6 : 0)
 k_group_dens_iter(SearchArgs a, IterArgs it) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -1557,7 +1595,7 @@ static int launch_persistent(Kern kern, bool& configured, size_t sh, int64_t ngr
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpsPerBlock * 32, sh);
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * sm_count;
+    int64_t grid = (int64_t)std::min(per_sm, kSpillWarpsPerSM / kWarpsPerBlock) * sm_count;
     if (ngroups_host >= 0) grid = std::min<int64_t>(grid, (ngroups_host + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, kWarpsPerBlock * 32, sh, s>>>(args...);

@@ -60,6 +60,7 @@ struct SearchArgs {
     DevCounters* ctr;
     unsigned* err;
     int* work;
+    uint32_t* stack_spill;   // walk stack overflow, kStackSpillPerWarp entries per warp
 };
 
 struct UpdateArgs {

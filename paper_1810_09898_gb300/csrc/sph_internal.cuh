@@ -35,6 +35,11 @@ constexpr float kUnitToBox = 2.3283064365386962890625e-10f;  // 2^-32
 constexpr double kBoxToUnit = 4294967296.0;                   // 2^32
 constexpr int kKeyLevels = 21;
 
+// Walk stack overflow area of the grouped kernels: entries per warp, and warps per SM
+// it is sized for (the persistent grids never exceed it).
+constexpr int kStackSpillPerWarp = 1024;
+constexpr int kSpillWarpsPerSM = 64;
+
 // Octree: nodes are stored level by level; the children of a node are contiguous.
 //   ncen  uint4  {cx, cy, cz, hmax bits}   centre of the tight box in fixed point
 //   next  float4 {ex, ey, ez, nchild bits} half extents in fixed-point units, padded
@@ -89,6 +94,7 @@ struct Ctx {
     double* h64 = nullptr;
     float4* hyd0 = nullptr;
     float4* hyd1 = nullptr;
+    uint32_t* stack_spill = nullptr;   // walk stack overflow (kStackSpillPerWarp per warp)
     // active / iteration state (rank space)
     int32_t* act = nullptr;        // active ranks (key order)
     int32_t* act2 = nullptr;       // compaction target
