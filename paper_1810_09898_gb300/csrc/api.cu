@@ -268,6 +268,7 @@ SearchArgs base_args(Ctx* c) {
     a.err = c->err;
     a.work = c->work;
     a.stack_spill = c->stack_spill;
+    a.start_tab = c->start_valid ? c->start_tab : nullptr;
     a.centre_box = c->p.group_centre == SPHGRP_CENTRE_BOX;
     return a;
 }
@@ -359,6 +360,7 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     rc |= dalloc(&c->grp_cnt, n + 1);
     rc |= dalloc(&c->grp_off, n + 1);
     rc |= dalloc(&c->stack_spill, (int64_t)c->sm_count * kSpillWarpsPerSM * kStackSpillPerWarp);
+    rc |= dalloc(&c->start_tab, kStartTableSize);
     rc |= dalloc(&c->ctr, 1);
     rc |= dalloc(&c->err, 1);
     rc |= dalloc(&c->work, 64);
@@ -384,7 +386,7 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
                     c->scan, c->scan_aux, c->lo, c->hi, c->acc_rho, c->acc_drho, c->acc_n,
                     c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
                     c->acc_s2, c->wadj, c->dadj, c->adj0, c->adj1, c->adj2, c->adj3,
-                    c->stack_spill, c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
+                    c->stack_spill, c->start_tab, c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
                     c->tree.nlevel};
     for (void* p : ptrs)
         if (p) cudaFree(p);

@@ -984,6 +984,39 @@ __device__ __forceinline__ bool group_centre(const SearchArgs& a, const int (&rk
     return true;
 }
 
+// Morton index of a cell of level l (l bits per axis, axis 0 most significant).
+__device__ __forceinline__ uint32_t cell_morton(uint32_t x, uint32_t y, uint32_t z, int l) {
+    uint32_t m = 0;
+    for (int b = l - 1; b >= 0; --b) m = (m << 3) | (((x >> b) & 1u) << 2) | (((y >> b) & 1u) << 1) | ((z >> b) & 1u);
+    return m;
+}
+
+// First node of the walk: the node of the deepest cell (level <= kStartLevels) that
+// holds the whole search sphere (centre C, radius Rb in box units).  Every particle
+// within the sphere lies in that cell and hence in that node's subtree (a node is the
+// set of particles whose keys share its cell's prefix).  Cells the tree did not reach
+// fall back to the nearest ancestor cell with a node.
+__device__ __forceinline__ int walk_start(const SearchArgs& a, uint32_t cx, uint32_t cy, uint32_t cz, float Rb) {
+    // radius in fixed-point units, rounded up, plus the sub-unit offsets of the positions
+    const double Ru = ceil((double)Rb * 4294967296.0 * (1.0 + 1e-6)) + 2.0;
+    if (!(Ru < 2147483648.0)) return 0;
+    const int64_t r = (int64_t)Ru;
+    int lvl = kStartLevels;
+    const uint32_t c3[3] = {cx, cy, cz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int64_t lo = (int64_t)c3[ax] - r, hi = (int64_t)c3[ax] + r;
+        if (lo < 0 || hi > 0xffffffffll) lvl = 0;   // the sphere wraps around the box
+        else lvl = min(lvl, __clz((uint32_t)lo ^ (uint32_t)hi));
+    }
+    for (; lvl >= 1; --lvl) {
+        const int nd = a.start_tab[start_table_offset(lvl) +
+                                   cell_morton(cx >> (32 - lvl), cy >> (32 - lvl), cz >> (32 - lvl), lvl)];
+        if (nd >= 0) return nd;
+    }
+    return 0;
+}
+
 // One group's walk from node `root` and the member x candidate filter of every staged
 // tile (the members are initialised relative to the centre C).  kSupFill writes the
 // superset at sup_pos + sup_n; sup_n accumulates the candidates.
@@ -1010,13 +1043,14 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
     // reach stays below half the box (symmetric: with the largest h of the tree)
     const float reach = K::sym ? Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[root].w)) : rlane;
     const bool wrap_safe = reach < 0.49f;
+    const int start = (a.start_tab && root == 0) ? walk_start(a, cx, cy, cz, reach) : root;
 
     // The stack lives in shared memory; entries that do not fit go to this warp's
     // overflow area in global memory (a second stack, drained when the first is empty:
     // the order of the walk changes, the superset does not).
     uint32_t* spill = a.stack_spill + (size_t)(blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kSpillCap;
     int sp = 1, gsp = 0;
-    if (lane == 0) W.stack[0] = (uint32_t)root << 3;   // one node
+    if (lane == 0) W.stack[0] = (uint32_t)start << 3;   // one node
     int nr = 0, pending = 0;
     __syncwarp();
     for (;;) {

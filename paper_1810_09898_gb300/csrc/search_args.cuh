@@ -61,6 +61,7 @@ struct SearchArgs {
     unsigned* err;
     int* work;
     uint32_t* stack_spill;   // walk stack overflow, kStackSpillPerWarp entries per warp
+    const int32_t* start_tab; // walk start table (null: walks start at their root)
 };
 
 struct UpdateArgs {

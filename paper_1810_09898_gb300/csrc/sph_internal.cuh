@@ -40,6 +40,15 @@ constexpr int kKeyLevels = 21;
 constexpr int kStackSpillPerWarp = 1024;
 constexpr int kSpillWarpsPerSM = 64;
 
+// Walk start table: for every level l = 1 .. kStartLevels, the node of every octree
+// cell of that level (indexed by the cell's Morton number; -1 where the tree has no
+// node of that level), so that a walk can start at the deepest cell holding its
+// search sphere instead of the root.  Level l occupies entries
+// [start_table_offset(l), start_table_offset(l) + 8^l).
+constexpr int kStartLevels = 6;
+__host__ __device__ constexpr int start_table_offset(int l) { return ((1 << (3 * l)) - 8) / 7; }
+constexpr int kStartTableSize = start_table_offset(kStartLevels + 1);
+
 // Octree: nodes are stored level by level; the children of a node are contiguous.
 //   ncen  uint4  {cx, cy, cz, hmax bits}   centre of the tight box in fixed point
 //   next  float4 {ex, ey, ez, nchild bits} half extents in fixed-point units, padded
@@ -95,6 +104,8 @@ struct Ctx {
     float4* hyd0 = nullptr;
     float4* hyd1 = nullptr;
     uint32_t* stack_spill = nullptr;   // walk stack overflow (kStackSpillPerWarp per warp)
+    int32_t* start_tab = nullptr;      // walk start table of the current octree
+    bool start_valid = false;          // start_tab matches the tree (single-box tree only)
     // active / iteration state (rank space)
     int32_t* act = nullptr;        // active ranks (key order)
     int32_t* act2 = nullptr;       // compaction target

@@ -163,6 +163,25 @@ __global__ void k_hmax_level(int a, int nf, const int4* __restrict__ nlink, cons
     ncen[id].w = __float_as_uint(hm);
 }
 
+// Walk start table (see kStartLevels): every node of levels 1 .. kStartLevels enters
+// under its cell, found from any of its particles (the cell of level l is the top l
+// bits of the fixed-point coordinates).
+__global__ void k_start_table(int first, int count, const int4* __restrict__ nlink,
+                              const int32_t* __restrict__ nlevel, const uint4* __restrict__ pfix,
+                              int32_t* __restrict__ tab) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int id = first + k;
+    const int l = nlevel[id];
+    const int4 L = nlink[id];
+    if (l < 1 || l > kStartLevels || L.y <= 0) return;
+    const uint4 P = pfix[L.x];
+    const uint32_t x = P.x >> (32 - l), y = P.y >> (32 - l), z = P.z >> (32 - l);
+    uint32_t m = 0;
+    for (int b = l - 1; b >= 0; --b) m = (m << 3) | (((x >> b) & 1u) << 2) | (((y >> b) & 1u) << 1) | ((z >> b) & 1u);
+    tab[start_table_offset(l) + m] = id;
+}
+
 static int grow_tree(Ctx* c, int64_t need, cudaStream_t s) {
     Tree& t = c->tree;
     if (need <= t.cap) return SPHGRP_OK;
@@ -248,6 +267,17 @@ int build_tree(Ctx* c, cudaStream_t s) {
     }
     k_box_final<<<blocks_for(t.count, 256), 256, 0, s>>>(t.count, blo, bhi, t.ncen, t.next);
     note_launch();
+    {
+        const int first = t.level_begin[1];
+        const int last = t.level_begin[std::min(t.nlevels, kStartLevels) + 1];
+        cudaMemsetAsync(c->start_tab, 0xff, kStartTableSize * sizeof(int32_t), s);
+        if (last > first) {
+            k_start_table<<<blocks_for(last - first, 256), 256, 0, s>>>(first, last - first, t.nlink, t.nlevel,
+                                                                        c->pfix, c->start_tab);
+            note_launch();
+        }
+        c->start_valid = true;
+    }
     cudaFreeAsync(blo, s);
     cudaFreeAsync(bhi, s);
     return check_cuda(cudaGetLastError(), "octree build");
@@ -442,6 +472,7 @@ int alloc_forest(Ctx* c, int64_t cap) {
 int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uint4* blo, uint4* bhi, int32_t* tot,
                  cudaStream_t s) {
     Tree& t = c->tree;
+    c->start_valid = false;   // forest walks start at their box's root
     const int64_t n = c->n;
     k_forest_roots<<<blocks_for(std::max(nbox, kKeyLevels + 3), 256), 256, 0, s>>>(nbox, box_off_dev, t.nlink,
                                                                                  t.next, t.nlevel, lvl);
