@@ -81,7 +81,14 @@ typedef struct sphgrp_params {
                            group_split * members * (smallest h)^3, i.e. while every member
                            would filter more than group_split times its own sphere; <= 0
                            keeps plain chunks of group_size.  e.g. 2 */
+    int iteration;      /* smoothing-length iteration of the grouped density:
+                           SPHGRP_ITER_PASSES (one search launch per pass over the still
+                           unconverged particles, regrouped) or SPHGRP_ITER_IN_GROUP (one
+                           launch; every group repeats walk, filter and update until its
+                           members converge).  The individual form always iterates in passes. */
 } sphgrp_params;
+
+enum { SPHGRP_ITER_PASSES = 0, SPHGRP_ITER_IN_GROUP = 1 };
 
 enum { SPHGRP_CENTRE_FIRST = 0, SPHGRP_CENTRE_BOX = 1 };
 

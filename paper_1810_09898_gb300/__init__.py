@@ -16,6 +16,8 @@ from .binding import (  # noqa: F401
     GROUPED,
     HYDRO,
     INDIVIDUAL,
+    ITER_IN_GROUP,
+    ITER_PASSES,
     SphgrpError,
     Context,
     kernel_launches,

@@ -15,6 +15,7 @@ _LIB_PATH = os.path.join(HERE, "_build", "libsphgrp.so")
 
 INDIVIDUAL, GROUPED = 0, 1
 CENTRE_FIRST, CENTRE_BOX = 0, 1
+ITER_PASSES, ITER_IN_GROUP = 0, 1
 DENSITY, HYDRO = 0, 1
 
 EXPORTED = [
@@ -76,6 +77,7 @@ class Params(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("group_centre", ctypes.c_int),
         ("group_split", ctypes.c_double),
+        ("iteration", ctypes.c_int),
     ]
 
 

@@ -300,6 +300,7 @@ void sphgrp_default_params(sphgrp_params* p) {
     p->eps = 0.01;
     p->group_centre = SPHGRP_CENTRE_BOX;
     p->group_split = 2.0;
+    p->iteration = SPHGRP_ITER_PASSES;
 }
 
 const char* sphgrp_last_error(void) { return g_last_error.c_str(); }
@@ -318,7 +319,8 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     if (p) c->p = *p;
     else sphgrp_default_params(&c->p);
     if (c->p.leaf_size < 1 || c->p.leaf_size > 1024 || !(c->p.nngb > 0) || !(c->p.nngb_tol >= 0) ||
-        c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX)) {
+        c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX) ||
+        (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP)) {
         delete c;
         return set_error(SPHGRP_EINVAL, "bad parameters");
     }
@@ -572,6 +574,48 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     int32_t* U2 = c->act2;
     int* nfail = c->work + 8;
     cudaMemsetAsync(nfail, 0, sizeof(int), s);
+    if (grouped && iterate && c->p.iteration == SPHGRP_ITER_IN_GROUP) {
+        // one launch: every group iterates its members to convergence
+        SearchArgs a = base_args(c);
+        a.U = U;
+        a.nu = nu;
+        a.g = group_size;
+        a.ngroups = (nu + group_size - 1) / group_size;
+        if (nu > 0 && (rc = make_groups(c, &a, U, nu, group_size, s))) return rc;
+        int* max_pass = c->work + 10;
+        cudaMemsetAsync(max_pass, 0, sizeof(int), s);
+        IterArgs it;
+        std::memset(&it, 0, sizeof(it));
+        it.nngb = c->p.nngb;
+        it.tol = c->p.nngb_tol;
+        it.max_iter = c->p.max_iter;
+        it.h64 = c->h64;
+        it.pfix = c->pfix;
+        it.h_out = h;
+        it.rho = rho;
+        it.drhodh = drhodh;
+        it.fgrad = fgrad;
+        it.nngb_out = nngb;
+        it.iters = iters;
+        it.nfail = nfail;
+        it.max_pass = max_pass;
+        if (nu > 0) {
+            timer_begin(c, s);
+            rc = launch_density_iter(a, it, group_size, c->sm_count, s);
+            timer_end(c, s, nu);
+            if (rc) return rc;
+        }
+        cudaMemcpyAsync(c->host_small + 2, nfail, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(c->host_small + 3, max_pass, sizeof(int), cudaMemcpyDeviceToHost, s);
+        rc = finish(c, s, 0);
+        c->last.walks = a.ngroups;
+        c->last.members = nu;
+        c->last.iterations = c->host_small[3];
+        if (rc) return rc;
+        if (c->host_small[2] > 0)
+            return set_error(SPHGRP_ENOCONV, std::to_string(c->host_small[2]) + " particles did not converge");
+        return SPHGRP_OK;
+    }
     int64_t walks = 0, members = 0;
     int it = 1;
     const int max_iter = iterate ? c->p.max_iter : 1;

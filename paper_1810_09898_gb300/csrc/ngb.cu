@@ -1380,6 +1380,7 @@ __device__ __forceinline__ bool hsml_step(const SearchArgs& a, const IterArgs& i
             if (it.iters) it.iters[orig] = pass;
             it.h_out[orig] = h;
             if (!done) atomicAdd(it.nfail, 1);
+            if (it.max_pass) atomicMax(it.max_pass, pass);
         }
         return true;
     }

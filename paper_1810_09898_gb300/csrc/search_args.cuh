@@ -105,6 +105,7 @@ struct IterArgs {
     int32_t* nngb_out;
     int32_t* iters;
     int* nfail;
+    int* max_pass;        // optional: largest pass count of any particle
 };
 
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s);

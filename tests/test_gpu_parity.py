@@ -168,10 +168,10 @@ def test_density_fixed_h(clu, mode, g):
 
 
 @pytest.mark.parametrize("dist,n,cfg", [("uniform", 32768, 1), ("clustered", 24001, 2)])
-@pytest.mark.parametrize("mode,g", [(0, 1), (1, 32)])
-def test_density_iteration(cuda_device, dist, n, cfg, mode, g):
+@pytest.mark.parametrize("mode,g,iteration", [(0, 1, 0), (1, 32, 0), (1, 16, 1), (1, 64, 1)])
+def test_density_iteration(cuda_device, dist, n, cfg, mode, g, iteration):
     d = dataset(dist, n, cfg)
-    G = Gpu(d["pos"], d["m32"])
+    G = Gpu(d["pos"], d["m32"], iteration=iteration)
     h0 = np.full(n, d["h0"])
     act = np.arange(n, dtype=np.int32)
     out = G.density(act, h0, 1, mode, g)
