@@ -544,7 +544,9 @@ __device__ __forceinline__ bool sym_decide(const Mem& M, const SearchArgs& a, fl
 template <int MODE, bool WRAP = false>
 __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 q,
                                            float4 v, float4 hh, int crank, LocalCounters& lc) {
-    if (crank == M.rank) return;
+    // The member itself is a candidate: the exports skip it by rank; the sums skip it
+    // as a pair at r = 0 (counted, then taken off the neighbour count at the end).
+    if (MODE != kAcc && crank == M.rank) return;
     float dx, dy, dz, r2;
     if (!sym_decide<WRAP>(M, a, p, q.x, crank, lc, dx, dy, dz, r2)) return;
     M.n++;
@@ -570,10 +572,10 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
     float visc = 0.0f;
     if (vr < 0.0f) {
         float hb = 0.5f * fmaf(q.x, hh.z, M.h);
-        float mu = hb * vr / fmaf(a.eps * hb, hb, r2);
+        float mu = hb * vr * __frcp_rn(fmaf(a.eps * hb, hb, r2));
         float cb = 0.5f * (M.cs + v.w);
-        float rb = 0.5f * (M.rho + hh.y);
-        visc = fmaf(-a.alpha * cb, mu, a.beta * mu * mu) / rb;
+        // Pi = (-alpha cbar mu + beta mu^2) / rhobar, rhobar = (rho_i + rho_j) / 2
+        visc = 2.0f * fmaf(-a.alpha * cb, mu, a.beta * mu * mu) * __frcp_rn(M.rho + hh.y);
     }
     float gbar = 0.5f * (dWi + dWj);
     float coef = q.y * fmaf(M.A, dWi, fmaf(hh.x, dWj, visc * gbar)) * rinv;
@@ -591,7 +593,7 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
 template <int MODE, bool WRAP = false>
 __device__ __forceinline__ void hydro_adj_pair(HAMember& M, const SearchArgs& a, float4 p, float4 q, float4 v,
                                                float4 hh, float4 wj, int crank, LocalCounters& lc) {
-    if (crank == M.rank) return;
+    // the member itself enters as a pair at r = 0, which contributes nothing
     float dx, dy, dz, r2;
     if (!sym_decide<WRAP>(M, a, p, q.x, crank, lc, dx, dy, dz, r2)) return;
     M.n++;
@@ -613,13 +615,14 @@ __device__ __forceinline__ void hydro_adj_pair(HAMember& M, const SearchArgs& a,
     const float vr = fmaf(v0, D0, fmaf(v1, D1, v2 * D2));
     const float hbar = 0.5f * fmaf(q.x, hh.z, M.h);
     const float Dn = fmaf(a.eps * hbar, hbar, r2);
-    const float rbar = 0.5f * (M.rho + hh.y);
+    const float iDn = __frcp_rn(Dn);
+    const float irbar = 2.0f * __frcp_rn(M.rho + hh.y);   // 1 / rhobar
     float Pi = 0.0f, Pmu = 0.0f;
     if (vr < 0.0f) {
         const float cbar = 0.5f * (M.cs + v.w);
-        const float mu = hbar * vr / Dn;
-        Pi = fmaf(-a.alpha * cbar, mu, a.beta * mu * mu) / rbar;
-        Pmu = fmaf(2.0f * a.beta, mu, -a.alpha * cbar) / rbar;
+        const float mu = hbar * vr * iDn;
+        Pi = fmaf(-a.alpha * cbar, mu, a.beta * mu * mu) * irbar;
+        Pmu = fmaf(2.0f * a.beta, mu, -a.alpha * cbar) * irbar;
     }
     const float sdw = Wr_k + Wr_j;
     const float B = fmaf(M.A, Wr_k, fmaf(hh.x, Wr_j, 0.5f * Pi * sdw));
@@ -629,19 +632,19 @@ __device__ __forceinline__ void hydro_adj_pair(HAMember& M, const SearchArgs& a,
     M.mb = fmaf(B, fmaf(e0, wj.x, fmaf(e1, wj.y, e2 * wj.z)), M.mb);
     M.Ab = fmaf(-Q, Wr_k, M.Ab);
     float dmu_dh = 0.0f;
-    if (vr < 0.0f) dmu_dh = 0.5f * vr * fmaf(-a.eps * hbar, hbar, r2) / (Dn * Dn);
+    if (vr < 0.0f) dmu_dh = 0.5f * vr * fmaf(-a.eps * hbar, hbar, r2) * iDn * iDn;
     M.hb = fmaf(-Q, fmaf(M.A, Wrh_k, fmaf(0.5f * Pi, Wrh_k, 0.5f * sdw * Pmu * dmu_dh)), M.hb);
-    M.rb = fmaf(Q * Pi, sdw / (4.0f * rbar), M.rb);
+    M.rb = fmaf(Q * Pi, 0.25f * sdw * irbar, M.rb);
     const float cm = 0.5f * sdw * Pmu;
     if (vr < 0.0f) {
-        const float cv = -Q * cm * hbar / Dn;
+        const float cv = -Q * cm * hbar * iDn;
         M.vb[0] = fmaf(cv, D0, M.vb[0]);
         M.vb[1] = fmaf(cv, D1, M.vb[1]);
         M.vb[2] = fmaf(cv, D2, M.vb[2]);
     }
     const float dBr = fmaf(M.A, Wrr_k, fmaf(hh.x, Wrr_j, 0.5f * Pi * (Wrr_k + Wrr_j)));
-    const float ca = (vr < 0.0f) ? hbar / Dn : 0.0f;
-    const float cb2 = (vr < 0.0f) ? -2.0f * hbar * vr / (Dn * Dn) : 0.0f;
+    const float ca = (vr < 0.0f) ? hbar * iDn : 0.0f;
+    const float cb2 = (vr < 0.0f) ? -2.0f * hbar * vr * iDn * iDn : 0.0f;
     {
         const float dB = fmaf(dBr, e0, cm * fmaf(ca, v0, cb2 * D0));
         const float dQ = (U0 - Q * e0) * rinv;
@@ -665,12 +668,8 @@ __device__ __forceinline__ void hydro_adj_pair(HAMember& M, const SearchArgs& a,
 template <int MODE, bool WRAP = false>
 __device__ __forceinline__ void dens_adj_pair(DAMember& M, const SearchArgs& a, float4 p, float4 q, float4 d,
                                               int crank, LocalCounters& lc) {
-    if (crank == M.rank) {
-        // self: W(0, h) = sigma = s h, dW/dh(0, h) = -3 sigma / h = -3 s
-        M.n++;
-        if (MODE == kAcc) M.mb = fmaf(M.alpha * M.sk, M.h, fmaf(-3.0f * M.beta, M.sk, M.mb));
-        return;
-    }
+    // The member itself enters as a pair at r = 0 like any coincident neighbour:
+    // alpha W(0, h) + beta W_h(0, h) = alpha s h - 3 beta s, and no position term.
     float dx, dy, dz, r2;
     if (!sym_decide<WRAP>(M, a, p, q.x, crank, lc, dx, dy, dz, r2)) return;
     M.n++;
@@ -772,7 +771,7 @@ __device__ __forceinline__ void write_result(const HMember& H, const SearchArgs&
         a.o_acc[3 * (int64_t)orig + 1] = H.sy - H.cy_;
         a.o_acc[3 * (int64_t)orig + 2] = H.sz - H.cz_;
         a.o_dudt[orig] = H.su - H.cu;
-        if (a.o_nh) a.o_nh[orig] = H.n;
+        if (a.o_nh) a.o_nh[orig] = H.n - 1;   // the member itself was counted as a pair
     } else if (MODE == kCount) {
         a.x_cnt[orig] = H.n;
     }
@@ -1279,8 +1278,11 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
     int64_t sup_pos = 0, sup_n = 0;
     if (MODE == kSupFill) sup_pos = a.x_off[gid];
     group_search<K, MODE, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, sup_pos, sup_n);
+    // the symmetric sums count the member itself as a pair at r = 0 (once, in slice 0)
+    constexpr bool kSelfPair = MODE == kAcc && (K::id == kKindHydro || K::id == kKindHydroAdj);
 #pragma unroll
-    for (int mm = 0; mm < M; ++mm) lc.pairs += mem[mm].n;
+    for (int mm = 0; mm < M; ++mm)
+        lc.pairs += mem[mm].n - ((kSelfPair && L.slice == 0 && mem[mm].rank >= 0) ? 1 : 0);
     if (kSup) {
         if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
         return;
@@ -1528,7 +1530,7 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
                 node = lk.w;
             }
         }
-        lc.pairs += (KIND == 0) ? dm.n : hm.n;
+        lc.pairs += (KIND == 0) ? dm.n : hm.n - (MODE == kAcc ? 1 : 0);
         if (KIND == 0) write_result<MODE>(dm, a);
         else write_result<MODE>(hm, a);
     }
