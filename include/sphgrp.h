@@ -86,9 +86,17 @@ typedef struct sphgrp_params {
                            unconverged particles, regrouped) or SPHGRP_ITER_IN_GROUP (one
                            launch; every group repeats walk, filter and update until its
                            members converge).  The individual form always iterates in passes. */
+    int group_mode;     /* how the grouped form cuts the active list (in key order) into groups:
+                           SPHGRP_GROUP_COUNT: chunks of group_size, split as group_split says;
+                           SPHGRP_GROUP_RADIUS (Sec. 3.1, the paper's rule): a group starts at an
+                           active particle and takes the following ones while they lie within
+                           R = group_f * h of its first particle, at most group_size of them
+                           (the scan restarts at the start of every run of 1024 actives) */
+    double group_f;     /* R / h of the radius mode, e.g. 0.5 */
 } sphgrp_params;
 
 enum { SPHGRP_ITER_PASSES = 0, SPHGRP_ITER_IN_GROUP = 1 };
+enum { SPHGRP_GROUP_COUNT = 0, SPHGRP_GROUP_RADIUS = 1 };
 
 enum { SPHGRP_CENTRE_FIRST = 0, SPHGRP_CENTRE_BOX = 1 };
 

@@ -13,6 +13,8 @@ from .binding import (  # noqa: F401
     Batch,
     CENTRE_FIRST,
     DENSITY,
+    GROUP_COUNT,
+    GROUP_RADIUS,
     GROUPED,
     HYDRO,
     INDIVIDUAL,

@@ -16,6 +16,7 @@ _LIB_PATH = os.path.join(HERE, "_build", "libsphgrp.so")
 INDIVIDUAL, GROUPED = 0, 1
 CENTRE_FIRST, CENTRE_BOX = 0, 1
 ITER_PASSES, ITER_IN_GROUP = 0, 1
+GROUP_COUNT, GROUP_RADIUS = 0, 1
 DENSITY, HYDRO = 0, 1
 
 EXPORTED = [
@@ -78,6 +79,8 @@ class Params(ctypes.Structure):
         ("group_centre", ctypes.c_int),
         ("group_split", ctypes.c_double),
         ("iteration", ctypes.c_int),
+        ("group_mode", ctypes.c_int),
+        ("group_f", ctypes.c_double),
     ]
 
 

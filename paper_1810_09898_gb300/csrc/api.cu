@@ -229,14 +229,19 @@ int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s,
 int make_groups(Ctx* c, SearchArgs* a, const int32_t* U, int nu, int g, cudaStream_t s) {
     a->groups = nullptr;
     a->ngroups = (nu + g - 1) / g;
-    if (nu <= 0 || g <= 1 || !(c->p.group_split > 0.0)) return SPHGRP_OK;
-    int nch = (nu + g - 1) / g;
-    int rc = launch_split_groups(U, nu, g, (float)c->p.group_split, c->pfix, c->h64, c->groups_tmp,
-                                 c->grp_cnt, s);
+    const bool radius = c->p.group_mode == SPHGRP_GROUP_RADIUS;
+    if (nu <= 0 || g <= 1 || (!radius && !(c->p.group_split > 0.0))) return SPHGRP_OK;
+    int nch = radius ? (nu + kRadiusRun - 1) / kRadiusRun : (nu + g - 1) / g;
+    int rc = radius ? launch_radius_groups(U, nu, g, c->p.group_f, c->pfix, c->poff, c->h64, c->groups_tmp,
+                                           c->grp_cnt, s)
+                    : launch_split_groups(U, nu, g, (float)c->p.group_split, c->pfix, c->h64, c->groups_tmp,
+                                          c->grp_cnt, s);
     if (rc) return rc;
     int32_t* total = reinterpret_cast<int32_t*>(c->work) + 16;
     if ((rc = exclusive_scan_i32(c, c->grp_cnt, c->grp_off, nch, total, s))) return rc;
-    if ((rc = launch_gather_groups(nch, g, c->groups_tmp, c->grp_cnt, c->grp_off, c->groups, s))) return rc;
+    if ((rc = launch_gather_groups(nch, radius ? kRadiusRun : g, c->groups_tmp, c->grp_cnt, c->grp_off, c->groups,
+                                   s)))
+        return rc;
     cudaMemcpyAsync(c->host_small + 40, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if ((rc = check_cuda(cudaStreamSynchronize(s), "group count"))) return rc;
     a->groups = c->groups;
@@ -301,6 +306,8 @@ void sphgrp_default_params(sphgrp_params* p) {
     p->group_centre = SPHGRP_CENTRE_BOX;
     p->group_split = 2.0;
     p->iteration = SPHGRP_ITER_PASSES;
+    p->group_mode = SPHGRP_GROUP_COUNT;
+    p->group_f = 0.5;
 }
 
 const char* sphgrp_last_error(void) { return g_last_error.c_str(); }
@@ -320,7 +327,9 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     else sphgrp_default_params(&c->p);
     if (c->p.leaf_size < 1 || c->p.leaf_size > 1024 || !(c->p.nngb > 0) || !(c->p.nngb_tol >= 0) ||
         c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX) ||
-        (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP)) {
+        (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP) ||
+        (c->p.group_mode != SPHGRP_GROUP_COUNT && c->p.group_mode != SPHGRP_GROUP_RADIUS) ||
+        (c->p.group_mode == SPHGRP_GROUP_RADIUS && !(c->p.group_f > 0.0 && c->p.group_f < 1e3))) {
         delete c;
         return set_error(SPHGRP_EINVAL, "bad parameters");
     }

@@ -798,7 +798,6 @@ struct alignas(16) WalkSmem {
     uint32_t stack[kStackCap];   // node ranges: (first child << 3) | (count - 1)
     int2 ranges[kRangeCap];      // pending leaf ranges (first rank, count)
     int rpre[kRangeCap + 1];     // prefix of the pending counts
-    int nodes[32];
 };
 
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
@@ -1073,14 +1072,14 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             unsigned tm = __ballot_sync(0xffffffffu, take);
             int nent = __popc(tm);
             int nnodes = __shfl_sync(0xffffffffu, incl, nent - 1);
-            if (take) {
-                int first = (int)(ent >> 3), ex = incl - ecnt;
-                for (int q = 0; q < ecnt; ++q) W.nodes[ex + q] = first + q;
-            }
+            // node slot l belongs to the taken entry whose first slot is the highest entry
+            // start <= l (the starts as a bit mask; entries sit on lanes 0 .. nent-1)
+            const unsigned starts = __reduce_or_sync(0xffffffffu, take ? 1u << (incl - ecnt) : 0u);
+            const unsigned below = (lane == 31) ? starts : (starts & ((2u << lane) - 1u));
+            const int e_of = max(__popc(below) - 1, 0);
+            const uint32_t my_ent = __shfl_sync(0xffffffffu, ent, e_of);
             sp -= nent;
-            __syncwarp();
-            int node = lane < nnodes ? W.nodes[lane] : -1;
-            __syncwarp();
+            int node = lane < nnodes ? (int)(my_ent >> 3) + (lane - (31 - __clz(below))) : -1;
             bool open = false, leaf = false;
             int4 lk = make_int4(0, 0, -1, 0);
             int nch = 0;
@@ -1586,6 +1585,51 @@ __global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, flo
         }
     }
     cnt[ch] = ng;
+}
+
+// Radius grouping (Sec. 3.1): a group starts at a work-list entry and takes the entries
+// that follow while they lie closer than R = f h to its first particle (periodic
+// minimum image), at most cap of them; the first entry farther away starts the next
+// group.  One thread scans each run of kRadiusRun entries; groups go to tmp at the
+// run's first entry.
+__global__ void k_radius_groups(const int32_t* __restrict__ U, int nu, int cap, float f,
+                                const uint4* __restrict__ pfix, const float4* __restrict__ poff,
+                                const double* __restrict__ h64, int2* __restrict__ tmp, int32_t* __restrict__ cnt) {
+    const int run = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s0 = run * kRadiusRun;
+    if (s0 >= nu) return;
+    const int e0 = min(s0 + kRadiusRun, nu);
+    int ng = 0;
+    int i = s0;
+    while (i < e0) {
+        const int r0 = U[i];
+        const uint4 P0 = pfix[r0];
+        const float4 O0 = poff[r0];
+        const float R = f * (float)h64[r0];
+        const float R2 = R * R;
+        int j = i + 1;
+        while (j < e0 && j - i < cap) {
+            const int rj = U[j];
+            const uint4 P = pfix[rj];
+            const float4 O = poff[rj];
+            const float dx = fix_diff(P.x, O.x, P0.x, O0.x);
+            const float dy = fix_diff(P.y, O.y, P0.y, O0.y);
+            const float dz = fix_diff(P.z, O.z, P0.z, O0.z);
+            if (!(fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < R2)) break;
+            ++j;
+        }
+        tmp[s0 + ng++] = make_int2(i, j - i);
+        i = j;
+    }
+    cnt[run] = ng;
+}
+
+int launch_radius_groups(const int32_t* U, int nu, int cap, double f, const uint4* pfix, const float4* poff,
+                         const double* h64, int2* tmp, int32_t* cnt, cudaStream_t s) {
+    const int runs = (nu + kRadiusRun - 1) / kRadiusRun;
+    k_radius_groups<<<blocks_for(runs, 64), 64, 0, s>>>(U, nu, cap, (float)f, pfix, poff, h64, tmp, cnt);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "radius grouping");
 }
 
 __global__ void k_gather_groups(int nch, int g, const int2* __restrict__ tmp, const int32_t* __restrict__ cnt,

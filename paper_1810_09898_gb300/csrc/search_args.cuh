@@ -117,6 +117,11 @@ int launch_search_pair(const SearchArgs& a0, int kind0, const SearchArgs& a1, in
 int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
 int launch_split_groups(const int32_t* U, int nu, int g, float split, const uint4* pfix, const double* h64,
                         int2* tmp, int32_t* cnt, cudaStream_t s);
+// radius grouping: the greedy scan restarts at the start of every run of this many
+// work-list entries (one thread per run)
+constexpr int kRadiusRun = 1024;
+int launch_radius_groups(const int32_t* U, int nu, int cap, double f, const uint4* pfix, const float4* poff,
+                         const double* h64, int2* tmp, int32_t* cnt, cudaStream_t s);
 int launch_gather_groups(int nch, int g, const int2* tmp, const int32_t* cnt, const int32_t* off, int2* groups,
                          cudaStream_t s);
 int gather_particles(Ctx* c, const double* pos, const float* m, cudaStream_t s);

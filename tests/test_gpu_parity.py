@@ -277,3 +277,67 @@ def test_rejects_bad_input(cuda_device):
         ctx.density(act, torch.tensor([0.6], dtype=torch.float64, device="cuda"), 0, 1, 8, z, z, z, zi)
     with pytest.raises(sg.SphgrpError, match="EINVAL"):
         ctx.density(act, torch.tensor([0.1], dtype=torch.float64, device="cuda"), 0, 1, 999, z, z, z, zi)
+
+
+# ---------------------------------------------------------------- radius grouping (Sec. 3.1)
+
+@pytest.fixture(scope="module", params=[(0.5, 1), (1.0, 0)], ids=["f0.5-box", "f1.0-first"])
+def clu_radius(cuda_device, request):
+    """The paper's grouping rule: consecutive actives within f h of the group's first."""
+    f, centre = request.param
+    d = dataset("clustered", 24001, config=2)
+    return d, Gpu(d["pos"], d["m32"], group_mode=1, group_f=f, group_centre=centre), f
+
+
+def _min_image(a):
+    return a - np.rint(a)
+
+
+def test_radius_groups_follow_the_rule(clu_radius):
+    d, G, f = clu_radius
+    h, _ = converged("clustered", 24001, 2)
+    act = active_runs(G.n, 0.3, 7, G.perm.cpu().numpy())
+    cap = 32
+    gfirst, members, goff, cand = G.supersets(act, h, 0, cap)
+    pos = d["pos"]
+    sizes = np.diff(gfirst)
+    assert np.all(sizes >= 1) and np.all(sizes <= cap)
+    # members in key order, as the active list
+    keys = oracle.hilbert_keys(pos)
+    assert np.all(np.diff(keys[members]) >= 0)
+    run = 1024
+    for k in range(len(sizes)):
+        a, b = gfirst[k], gfirst[k + 1]
+        first = members[a]
+        R = f * h[first]
+        dist = np.linalg.norm(_min_image(pos[members[a:b]] - pos[first]), axis=1)
+        assert np.all(dist[1:] < R * (1 + 1e-5)), k          # every member within R of the first
+        # the group ends at the cap, at a run boundary, or at an entry outside R
+        if b < len(members) and b - a < cap and b % run != 0:
+            nxt = np.linalg.norm(_min_image(pos[members[b]] - pos[first]))
+            assert nxt >= R * (1 - 1e-5), k
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_radius_groups_sets_and_supersets(clu_radius, kind):
+    d, G, f = clu_radius
+    h, _ = converged("clustered", 24001, 2)
+    act = active_runs(G.n, 0.2, 8, G.perm.cpu().numpy())
+    _check_supersets(d, G, act, h, kind, 32, exact_chunks=False)
+    _compare_sets(G.ngb_sets(act, h, kind, 1, 32), oracle.ngb_sets(d["pos"], h, act, kind))
+
+
+def test_radius_groups_density_and_hydro(clu_radius):
+    d, G, f = clu_radius
+    h, dens = converged("clustered", 24001, 2)
+    act = np.arange(G.n, dtype=np.int32)
+    out = G.density(act, h, 0, 1, 32)
+    ref = oracle.density(d["pos"], d["m32"].astype(np.float64), h)
+    assert np.array_equal(out["nngb"], ref["nngb"])
+    assert np.max(np.abs(out["rho"] / ref["rho"] - 1.0)) <= RHO_TOL
+    rho32, f32 = dens["rho"].astype(np.float32), dens["f"].astype(np.float32)
+    hy = G.hydro(act, h, rho32, f32, d["vel32"], d["u32"], 1, 32)
+    href = oracle.hydro(d["pos"], d["vel32"].astype(np.float64), d["m32"].astype(np.float64), h,
+                        rho32.astype(np.float64), f32.astype(np.float64), d["u32"].astype(np.float64))
+    assert np.array_equal(hy["nngb"], href["nngb"])
+    assert _rel_l2(hy["acc"], href["acc"]) <= ACC_TOL
