@@ -635,15 +635,8 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         a.g = grouped ? group_size : 1;
         a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
         if (grouped && (rc = make_groups(c, &a, U, nu, group_size, s))) return rc;
-        a.o_s0 = c->acc_rho;
-        a.o_s1 = c->acc_drho;
-        a.o_n = c->acc_n;
         walks += a.ngroups;
         members += nu;
-        timer_begin(c, s);
-        rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
-        timer_end(c, s, a.nu);
-        if (rc) return rc;
         UpdateArgs ua;
         std::memset(&ua, 0, sizeof(ua));
         ua.U = U;
@@ -652,9 +645,6 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         ua.max_iter = max_iter;
         ua.nngb = c->p.nngb;
         ua.tol = c->p.nngb_tol;
-        ua.s0 = c->acc_rho;
-        ua.s1 = c->acc_drho;
-        ua.n = c->acc_n;
         ua.poff = c->poff;
         ua.h64 = c->h64;
         ua.pfix = c->pfix;
@@ -670,7 +660,13 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         ua.iters = iters;
         ua.iterate = iterate;
         ua.nfail = nfail;
-        if ((rc = launch_hsml_update(ua, s))) return rc;
+        // the update of every member runs in the search kernel's epilogue
+        a.fuse_update = 1;
+        a.upd = ua;
+        timer_begin(c, s);
+        rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
+        timer_end(c, s, a.nu);
+        if (rc) return rc;
         if (!iterate) break;
         int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
         if ((rc = exclusive_scan_i32(c, c->flag, c->scan, nu, total, s))) return rc;

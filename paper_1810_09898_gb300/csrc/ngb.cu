@@ -36,6 +36,8 @@ constexpr int kTileD = 128;   // density tile (candidates)
 constexpr int kTileH = 128;   // hydro tile
 constexpr int kTileA = 128;   // adjoint tiles
 
+__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0, float s1, int n);
+
 struct LocalCounters {
     unsigned long long nodes = 0, cands = 0, tests = 0, pairs = 0, retests = 0;
     int max_stack = 0;
@@ -1293,8 +1295,17 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
     }
     if (L.slice == 0) {
 #pragma unroll
-        for (int mm = 0; mm < M; ++mm)
-            if (mem[mm].rank >= 0) write_result<MODE>(mem[mm], a);
+        for (int mm = 0; mm < M; ++mm) {
+            if (mem[mm].rank < 0) continue;
+            if constexpr (K::id == kKindDensity && MODE == kAcc) {
+                if (a.fuse_update) {
+                    const DMember& D = reinterpret_cast<const DMember&>(mem[mm]);
+                    hsml_update(a.upd, d.base + member_of(L, lane, mm, d.g), D.rank, D.s0 - D.c0, D.s1 - D.c1, D.n);
+                    continue;
+                }
+            }
+            write_result<MODE>(mem[mm], a);
+        }
     }
 }
 
@@ -1530,8 +1541,12 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
             }
         }
         lc.pairs += (KIND == 0) ? dm.n : hm.n - (MODE == kAcc ? 1 : 0);
-        if (KIND == 0) write_result<MODE>(dm, a);
-        else write_result<MODE>(hm, a);
+        if (KIND == 0) {
+            if (MODE == kAcc && a.fuse_update) hsml_update(a.upd, u, dm.rank, dm.s0 - dm.c0, dm.s1 - dm.c1, dm.n);
+            else write_result<MODE>(dm, a);
+        } else {
+            write_result<MODE>(hm, a);
+        }
     }
     flush_counters(a, lc, lane);
 }
@@ -1810,16 +1825,15 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
 // Smoothing-length iteration: per unconverged particle, FP64
 // ---------------------------------------------------------------------------------
 
-__global__ void k_hsml_update(UpdateArgs a) {
-    int u = blockIdx.x * blockDim.x + threadIdx.x;
-    if (u >= a.nu) return;
-    const int r = a.U[u];
+// One particle's pass of the smoothing-length iteration: u = its work-list entry, r =
+// its rank, s0 / s1 / n its density sums at the current h.
+__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0, float s1, int n) {
     const double h = a.h64[r];
     const double m = (double)a.poff[r].w;
     const double kPi = 3.14159265358979323846;
     const double sigma = 8.0 / (kPi * h * h * h);
-    const double rho = sigma * (double)a.s0[r];
-    const double drho = -sigma / h * (double)a.s1[r];
+    const double rho = sigma * (double)s0;
+    const double drho = -sigma / h * (double)s1;
     const double neff = 4.0 * kPi / 3.0 * h * h * h * rho / m;
     bool done = !a.iterate || fabs(neff - a.nngb) <= a.tol;
     bool last = a.it >= a.max_iter;
@@ -1828,7 +1842,7 @@ __global__ void k_hsml_update(UpdateArgs a) {
         a.rho[orig] = (float)rho;
         a.drhodh[orig] = (float)drho;
         a.fgrad[orig] = (float)(1.0 / (1.0 + h / (3.0 * rho) * drho));
-        a.nngb_out[orig] = a.n[r];
+        a.nngb_out[orig] = n;
         if (a.iters) a.iters[orig] = a.it;
         a.h_out[orig] = h;
         a.keep[u] = 0;
@@ -1852,13 +1866,6 @@ __global__ void k_hsml_update(UpdateArgs a) {
     a.h64[r] = hn;
     a.pfix[r].w = __float_as_uint((float)hn);
     a.keep[u] = 1;
-}
-
-int launch_hsml_update(const UpdateArgs& a, cudaStream_t s) {
-    if (a.nu <= 0) return SPHGRP_OK;
-    k_hsml_update<<<blocks_for(a.nu, 256), 256, 0, s>>>(a);
-    note_launch();
-    return check_cuda(cudaGetLastError(), "hsml update");
 }
 
 }  // namespace sphgrp

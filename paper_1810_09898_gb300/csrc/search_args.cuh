@@ -11,6 +11,31 @@ enum Mode { kAcc = 0, kCount = 1, kFill = 2, kSupCount = 3, kSupFill = 4 };
 // pair loops of the search kernels: SPHGRP_DENSITY (0), SPHGRP_HYDRO (1) and the adjoints
 enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3 };
 
+// smoothing-length update of the density passes (per unconverged particle, FP64)
+struct UpdateArgs {
+    const int32_t* U;
+    int nu;
+    int it;
+    int max_iter;
+    double nngb, tol;
+    const float4* poff;
+    double* h64;
+    uint4* pfix;
+    double* lo;
+    double* hi;
+    int32_t* keep;        // 1 = still unconverged
+    const int32_t* perm;
+    // caller outputs (original order)
+    double* h_out;
+    float* rho;
+    float* drhodh;
+    float* fgrad;
+    int32_t* nngb_out;
+    int32_t* iters;
+    int iterate;
+    int* nfail;
+};
+
 struct SearchArgs {
     // octree
     const uint4* ncen;
@@ -62,34 +87,12 @@ struct SearchArgs {
     int* work;
     uint32_t* stack_spill;   // walk stack overflow, kStackSpillPerWarp entries per warp
     const int32_t* start_tab; // walk start table (null: walks start at their root)
+    // density passes: the FP64 smoothing-length update of every member runs in the
+    // search kernel's epilogue from the member's own sums (no separate update kernel)
+    int fuse_update;
+    UpdateArgs upd;
 };
 
-struct UpdateArgs {
-    const int32_t* U;
-    int nu;
-    int it;
-    int max_iter;
-    double nngb, tol;
-    const float* s0;
-    const float* s1;
-    const int32_t* n;
-    const float4* poff;
-    double* h64;
-    uint4* pfix;
-    double* lo;
-    double* hi;
-    int32_t* keep;        // 1 = still unconverged
-    const int32_t* perm;
-    // caller outputs (original order)
-    double* h_out;
-    float* rho;
-    float* drhodh;
-    float* fgrad;
-    int32_t* nngb_out;
-    int32_t* iters;
-    int iterate;
-    int* nfail;
-};
 
 // smoothing-length iteration inside the grouped density kernel (batch path)
 struct IterArgs {
@@ -114,7 +117,6 @@ int launch_search_dev(const SearchArgs& a, int kind, int max_g, int sm_count, cu
 int launch_density_iter(const SearchArgs& a, const IterArgs& it, int max_g, int sm_count, cudaStream_t s);
 int launch_search_pair(const SearchArgs& a0, int kind0, const SearchArgs& a1, int kind1, int max_g, int sm_count,
                        cudaStream_t s);
-int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
 int launch_split_groups(const int32_t* U, int nu, int g, float split, const uint4* pfix, const double* h64,
                         int2* tmp, int32_t* cnt, cudaStream_t s);
 // radius grouping: the greedy scan restarts at the start of every run of this many

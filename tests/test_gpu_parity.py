@@ -341,3 +341,22 @@ def test_radius_groups_density_and_hydro(clu_radius):
                         rho32.astype(np.float64), f32.astype(np.float64), d["u32"].astype(np.float64))
     assert np.array_equal(hy["nngb"], href["nngb"])
     assert _rel_l2(hy["acc"], href["acc"]) <= ACC_TOL
+
+
+# ---------------------------------------------------------------- deep walks
+
+def test_walk_stack_overflow_area(cuda_device):
+    """A group whose sphere covers most of the box opens most of the tree: the walk
+    stack outgrows its shared part and continues in the global overflow area; the
+    neighbour sets stay exact."""
+    n = 1 << 17
+    d = dataset("uniform", n, 9)
+    G = Gpu(d["pos"], d["m32"])
+    h = np.full(n, 0.45)
+    perm = G.perm.cpu().numpy()
+    act = np.sort(perm[:128]).astype(np.int32)   # one group of 128 consecutive particles
+    got = G.ngb_sets(act, h, 0, 1, 128)
+    st = G.ctx.stats()
+    print("max_stack", st["max_stack"], "nodes", st["nodes_tested"])
+    _compare_sets(got, oracle.ngb_sets(d["pos"], h, act, oracle.DENSITY))
+    assert st["max_stack"] > 256, st["max_stack"]
