@@ -93,6 +93,8 @@ typedef struct sphgrp_params {
                            R = group_f * h of its first particle, at most group_size of them
                            (the scan restarts at the start of every run of 1024 actives) */
     double group_f;     /* R / h of the radius mode, e.g. 0.5 */
+    int stack_shared;   /* walk-stack entries per warp kept in shared memory (32 .. 256); deeper
+                           walks continue in a global overflow area.  e.g. 256 */
 } sphgrp_params;
 
 enum { SPHGRP_ITER_PASSES = 0, SPHGRP_ITER_IN_GROUP = 1 };

@@ -81,6 +81,7 @@ class Params(ctypes.Structure):
         ("iteration", ctypes.c_int),
         ("group_mode", ctypes.c_int),
         ("group_f", ctypes.c_double),
+        ("stack_shared", ctypes.c_int),
     ]
 
 

@@ -274,6 +274,7 @@ SearchArgs base_args(Ctx* c) {
     a.work = c->work;
     a.stack_spill = c->stack_spill;
     a.start_tab = c->start_valid ? c->start_tab : nullptr;
+    a.stack_cap = c->p.stack_shared;
     a.centre_box = c->p.group_centre == SPHGRP_CENTRE_BOX;
     return a;
 }
@@ -308,6 +309,7 @@ void sphgrp_default_params(sphgrp_params* p) {
     p->iteration = SPHGRP_ITER_PASSES;
     p->group_mode = SPHGRP_GROUP_COUNT;
     p->group_f = 0.5;
+    p->stack_shared = 256;
 }
 
 const char* sphgrp_last_error(void) { return g_last_error.c_str(); }
@@ -329,7 +331,8 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
         c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX) ||
         (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP) ||
         (c->p.group_mode != SPHGRP_GROUP_COUNT && c->p.group_mode != SPHGRP_GROUP_RADIUS) ||
-        (c->p.group_mode == SPHGRP_GROUP_RADIUS && !(c->p.group_f > 0.0 && c->p.group_f < 1e3))) {
+        (c->p.group_mode == SPHGRP_GROUP_RADIUS && !(c->p.group_f > 0.0 && c->p.group_f < 1e3)) ||
+        c->p.stack_shared < 32 || c->p.stack_shared > kStackSharedMax) {
         delete c;
         return set_error(SPHGRP_EINVAL, "bad parameters");
     }
@@ -660,13 +663,17 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         ua.iters = iters;
         ua.iterate = iterate;
         ua.nfail = nfail;
-        // the update of every member runs in the search kernel's epilogue
-        a.fuse_update = 1;
-        a.upd = ua;
+        a.o_s0 = c->acc_rho;
+        a.o_s1 = c->acc_drho;
+        a.o_n = c->acc_n;
+        ua.s0 = c->acc_rho;
+        ua.s1 = c->acc_drho;
+        ua.n = c->acc_n;
         timer_begin(c, s);
         rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
         timer_end(c, s, a.nu);
         if (rc) return rc;
+        if ((rc = launch_hsml_update(ua, s))) return rc;
         if (!iterate) break;
         int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
         if ((rc = exclusive_scan_i32(c, c->flag, c->scan, nu, total, s))) return rc;

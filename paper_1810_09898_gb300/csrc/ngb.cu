@@ -24,19 +24,13 @@
 
 namespace sphgrp {
 
-#ifndef SPHGRP_STACK_CAP
-#define SPHGRP_STACK_CAP 256
-#endif
-
 constexpr int kWarpsPerBlock = 4;
-constexpr int kStackCap = SPHGRP_STACK_CAP;   // walk stack entries in shared memory
+constexpr int kStackCap = kStackSharedMax;     // walk stack entries in shared memory
 constexpr int kRangeCap = 64;                  // pending leaf ranges
 constexpr int kSpillCap = kStackSpillPerWarp;  // overflow entries per warp (global memory)
 constexpr int kTileD = 128;   // density tile (candidates)
 constexpr int kTileH = 128;   // hydro tile
 constexpr int kTileA = 128;   // adjoint tiles
-
-__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0, float s1, int n);
 
 struct LocalCounters {
     unsigned long long nodes = 0, cands = 0, tests = 0, pairs = 0, retests = 0;
@@ -1112,24 +1106,26 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             bool push = open && !leaf;
             unsigned pm = __ballot_sync(0xffffffffu, push);
             const int npush = __popc(pm);
-            const int room = kStackCap - sp;
-            if (push) {
-                const int k = __popc(pm & lt);
-                const uint32_t v = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
-                if (k < room) {
-                    W.stack[sp + k] = v;
-                } else {
-                    const int q = gsp + (k - room);
-                    if (q < kSpillCap) spill[q] = v;
-                    else atomicOr(a.err, kErrStack);
+            if (npush > a.stack_cap - sp) {
+                // make room: the oldest entries (the bottom of the shared part, a multiple
+                // of 32 of them) move to the top of the overflow area, which stays below
+                // the shared part, so the whole stack remains last in, first out
+                const int ev = min(((npush - (a.stack_cap - sp) + 31) >> 5) << 5, sp);
+                if (gsp + ev > kSpillCap) atomicOr(a.err, kErrStack);
+                for (int b = lane; b < ev; b += 32)
+                    if (gsp + b < kSpillCap) spill[gsp + b] = W.stack[b];
+                __syncwarp();
+                for (int b = 0; b < sp - ev; b += 32) {
+                    const uint32_t v = (b + lane < sp - ev) ? W.stack[ev + b + lane] : 0u;
+                    __syncwarp();
+                    if (b + lane < sp - ev) W.stack[b + lane] = v;
+                    __syncwarp();
                 }
+                gsp = min(gsp + ev, kSpillCap);
+                sp -= ev;
             }
-            if (npush > room) {
-                gsp = min(gsp + npush - room, kSpillCap);
-                sp = kStackCap;
-            } else {
-                sp += npush;
-            }
+            if (push) W.stack[sp + __popc(pm & lt)] = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
+            sp += npush;
             lc.max_stack = max(lc.max_stack, sp + gsp);
             __syncwarp();
         }
@@ -1296,15 +1292,7 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
     if (L.slice == 0) {
 #pragma unroll
         for (int mm = 0; mm < M; ++mm) {
-            if (mem[mm].rank < 0) continue;
-            if constexpr (K::id == kKindDensity && MODE == kAcc) {
-                if (a.fuse_update) {
-                    const DMember& D = reinterpret_cast<const DMember&>(mem[mm]);
-                    hsml_update(a.upd, d.base + member_of(L, lane, mm, d.g), D.rank, D.s0 - D.c0, D.s1 - D.c1, D.n);
-                    continue;
-                }
-            }
-            write_result<MODE>(mem[mm], a);
+            if (mem[mm].rank >= 0) write_result<MODE>(mem[mm], a);
         }
     }
 }
@@ -1541,12 +1529,8 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
             }
         }
         lc.pairs += (KIND == 0) ? dm.n : hm.n - (MODE == kAcc ? 1 : 0);
-        if (KIND == 0) {
-            if (MODE == kAcc && a.fuse_update) hsml_update(a.upd, u, dm.rank, dm.s0 - dm.c0, dm.s1 - dm.c1, dm.n);
-            else write_result<MODE>(dm, a);
-        } else {
-            write_result<MODE>(hm, a);
-        }
+        if (KIND == 0) write_result<MODE>(dm, a);
+        else write_result<MODE>(hm, a);
     }
     flush_counters(a, lc, lane);
 }
@@ -1825,23 +1809,29 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
 // Smoothing-length iteration: per unconverged particle, FP64
 // ---------------------------------------------------------------------------------
 
-// One particle's pass of the smoothing-length iteration: u = its work-list entry, r =
-// its rank, s0 / s1 / n its density sums at the current h.
-__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0, float s1, int n) {
+// One particle's pass of the smoothing-length iteration (FP64): u = its work-list
+// entry, r = its rank, s0 / s1 / n its density sums at the current h.  Runs as its own
+// kernel with one particle per thread: in the search kernel's epilogue only one slice
+// of each warp would hold the members, which doubles the FP64 issue.
+__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0f, float s1f, int n) {
+    // With rho = sigma S0, dRho/dh = -(sigma / h) S1 and sigma = 8 / (pi h^3), the
+    // quantities of the iteration reduce to the sums themselves:
+    //   N_eff = (4 pi / 3) h^3 rho / m = (32 / 3) S0 / m,
+    //   f = 1 / (1 + h / (3 rho) dRho/dh) = 3 S0 / (3 S0 - S1),
+    //   g / g' = h (32 S0 - 3 N_ngb m) / (32 (3 S0 - S1))  (the Newton step).
     const double h = a.h64[r];
     const double m = (double)a.poff[r].w;
-    const double kPi = 3.14159265358979323846;
-    const double sigma = 8.0 / (kPi * h * h * h);
-    const double rho = sigma * (double)s0;
-    const double drho = -sigma / h * (double)s1;
-    const double neff = 4.0 * kPi / 3.0 * h * h * h * rho / m;
+    const double s0 = (double)s0f, s1 = (double)s1f;
+    const double neff = (32.0 / 3.0) * s0 / m;
     bool done = !a.iterate || fabs(neff - a.nngb) <= a.tol;
     bool last = a.it >= a.max_iter;
     if (done || last) {
+        const double kPi = 3.14159265358979323846;
+        const double sigma = 8.0 / (kPi * h * h * h);
         const int orig = a.perm[r];
-        a.rho[orig] = (float)rho;
-        a.drhodh[orig] = (float)drho;
-        a.fgrad[orig] = (float)(1.0 / (1.0 + h / (3.0 * rho) * drho));
+        a.rho[orig] = (float)(sigma * s0);
+        a.drhodh[orig] = (float)(-sigma / h * s1);
+        a.fgrad[orig] = (float)(3.0 * s0 / (3.0 * s0 - s1));
         a.nngb_out[orig] = n;
         if (a.iters) a.iters[orig] = a.it;
         a.h_out[orig] = h;
@@ -1852,9 +1842,7 @@ __device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, f
     double lo = a.it == 1 ? 0.0 : a.lo[r];
     double hi = a.it == 1 ? __longlong_as_double(0x7ff0000000000000ll) : a.hi[r];
     if (neff < a.nngb) lo = h; else hi = h;
-    const double g = 4.0 * kPi / 3.0 * h * h * h * rho - a.nngb * m;
-    const double gp = 4.0 * kPi * h * h * rho + 4.0 * kPi / 3.0 * h * h * h * drho;
-    double hn = h - g / gp;
+    double hn = h - h * (32.0 * s0 - 3.0 * a.nngb * m) / (32.0 * (3.0 * s0 - s1));
     const double cbrt2 = 1.2599210498948731647672106;
     if (!(hn > lo && hn < hi) || !isfinite(hn)) {
         if (isinf(hi)) hn = h * cbrt2;
@@ -1866,6 +1854,20 @@ __device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, f
     a.h64[r] = hn;
     a.pfix[r].w = __float_as_uint((float)hn);
     a.keep[u] = 1;
+}
+
+__global__ void k_hsml_update(UpdateArgs a) {
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= a.nu) return;
+    const int r = a.U[u];
+    hsml_update(a, u, r, a.s0[r], a.s1[r], a.n[r]);
+}
+
+int launch_hsml_update(const UpdateArgs& a, cudaStream_t s) {
+    if (a.nu <= 0) return SPHGRP_OK;
+    k_hsml_update<<<blocks_for(a.nu, 256), 256, 0, s>>>(a);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "hsml update");
 }
 
 }  // namespace sphgrp

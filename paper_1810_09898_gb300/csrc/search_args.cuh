@@ -18,6 +18,9 @@ struct UpdateArgs {
     int it;
     int max_iter;
     double nngb, tol;
+    const float* s0;
+    const float* s1;
+    const int32_t* n;
     const float4* poff;
     double* h64;
     uint4* pfix;
@@ -87,10 +90,7 @@ struct SearchArgs {
     int* work;
     uint32_t* stack_spill;   // walk stack overflow, kStackSpillPerWarp entries per warp
     const int32_t* start_tab; // walk start table (null: walks start at their root)
-    // density passes: the FP64 smoothing-length update of every member runs in the
-    // search kernel's epilogue from the member's own sums (no separate update kernel)
-    int fuse_update;
-    UpdateArgs upd;
+    int stack_cap;            // walk-stack entries kept in shared memory (<= kStackSharedMax)
 };
 
 
@@ -112,6 +112,7 @@ struct IterArgs {
 };
 
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s);
+int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
 // persistent launches over a device-side group count (a.ngroups_dev), graph-capturable
 int launch_search_dev(const SearchArgs& a, int kind, int max_g, int sm_count, cudaStream_t s);
 int launch_density_iter(const SearchArgs& a, const IterArgs& it, int max_g, int sm_count, cudaStream_t s);

@@ -38,6 +38,7 @@ constexpr int kKeyLevels = 21;
 // Walk stack overflow area of the grouped kernels: entries per warp, and warps per SM
 // it is sized for (the persistent grids never exceed it).
 constexpr int kStackSpillPerWarp = 1024;
+constexpr int kStackSharedMax = 256;   // walk-stack entries per warp in shared memory
 constexpr int kSpillWarpsPerSM = 64;
 
 // Walk start table: for every level l = 1 .. kStartLevels, the node of every octree
