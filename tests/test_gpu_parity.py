@@ -360,3 +360,13 @@ def test_walk_stack_overflow_area(cuda_device):
     print("max_stack", st["max_stack"], "nodes", st["nodes_tested"])
     _compare_sets(got, oracle.ngb_sets(d["pos"], h, act, oracle.DENSITY))
     assert st["max_stack"] > 32, st["max_stack"]
+
+
+def test_rejects_bad_parameters(cuda_device):
+    import paper_1810_09898_gb300 as sg
+
+    for bad in ({"stack_shared": 16}, {"stack_shared": 512}, {"group_mode": 5}, {"group_mode": 1, "group_f": 0.0},
+                {"iteration": 3}, {"leaf_size": 0}, {"group_centre": 4}, {"max_iter": 0}):
+        with pytest.raises(sg.SphgrpError, match="EINVAL"):
+            sg.Context(100, **bad)
+    sg.Context(100, stack_shared=32, group_mode=1, group_f=0.7, iteration=1).close()
