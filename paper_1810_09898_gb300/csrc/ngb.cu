@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
     int nr = 0, pending = 0;
     __syncwarp();
     for (;;) {
-        while ((sp > 0 || gsp > 0) && pending < TCAP && nr <= kRangeCap - 32) {
+        while ((sp > 0 || gsp > 0) && sp <= a.stack_cap - 32 && pending < TCAP && nr <= kRangeCap - 32) {
             if (sp == 0) {
                 const int m = min(gsp, 32);
                 if (lane < m) W.stack[lane] = spill[gsp - m + lane];
@@ -1106,24 +1106,6 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             bool push = open && !leaf;
             unsigned pm = __ballot_sync(0xffffffffu, push);
             const int npush = __popc(pm);
-            if (npush > a.stack_cap - sp) {
-                // make room: the oldest entries (the bottom of the shared part, a multiple
-                // of 32 of them) move to the top of the overflow area, which stays below
-                // the shared part, so the whole stack remains last in, first out
-                const int ev = min(((npush - (a.stack_cap - sp) + 31) >> 5) << 5, sp);
-                if (gsp + ev > kSpillCap) atomicOr(a.err, kErrStack);
-                for (int b = lane; b < ev; b += 32)
-                    if (gsp + b < kSpillCap) spill[gsp + b] = W.stack[b];
-                __syncwarp();
-                for (int b = 0; b < sp - ev; b += 32) {
-                    const uint32_t v = (b + lane < sp - ev) ? W.stack[ev + b + lane] : 0u;
-                    __syncwarp();
-                    if (b + lane < sp - ev) W.stack[b + lane] = v;
-                    __syncwarp();
-                }
-                gsp = min(gsp + ev, kSpillCap);
-                sp -= ev;
-            }
             if (push) W.stack[sp + __popc(pm & lt)] = ((uint32_t)lk.z << 3) | (uint32_t)(nch - 1);
             sp += npush;
             lc.max_stack = max(lc.max_stack, sp + gsp);
@@ -1242,6 +1224,23 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             if (kSup) sup_n += total;
             nr = 0;
             pending = 0;
+        }
+        if (sp > a.stack_cap - 32) {
+            // the next step could push 32 entries: the oldest (up to 32, the bottom of the
+            // shared part) move to the top of the overflow area, which stays below the
+            // shared part, so the whole stack remains last in, first out
+            const int ev = min(32, sp);
+            if (gsp + ev > kSpillCap) atomicOr(a.err, kErrStack);
+            else if (lane < ev) spill[gsp + lane] = W.stack[lane];
+            __syncwarp();
+            for (int b = 0; b < sp - ev; b += 32) {
+                const uint32_t v = (b + lane < sp - ev) ? W.stack[ev + b + lane] : 0u;
+                __syncwarp();
+                if (b + lane < sp - ev) W.stack[b + lane] = v;
+                __syncwarp();
+            }
+            gsp = min(gsp + ev, kSpillCap);
+            sp -= ev;
         }
         if (sp == 0 && gsp == 0) break;
     }
