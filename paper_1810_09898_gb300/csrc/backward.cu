@@ -154,19 +154,6 @@ int launch_bwd_combine(Ctx* c, float* g_pos, float* g_vel, float* g_m, cudaStrea
     return check_cuda(cudaGetLastError(), "backward combine");
 }
 
-namespace {
-
-__global__ void k_gather_h_all(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
-                               double* __restrict__ h64, uint4* __restrict__ pfix, unsigned* err) {
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    double v = h[perm[r]];
-    if (!(v > 0.0 && v < 0.5)) atomicOr(err, kErrH);
-    h64[r] = v;
-    pfix[r].w = __float_as_uint((float)v);
-}
-
-}  // namespace
 }  // namespace sphgrp
 
 using namespace sphgrp;
@@ -184,8 +171,7 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     if (!g_pos && !g_vel && !g_m) return set_error(SPHGRP_EINVAL, "no gradient requested");
     if ((rc = backward_buffers(c))) return rc;
     reset_flags(c, s);
-    k_gather_h_all<<<blocks_for(n, 256), 256, 0, s>>>(n, c->perm, h, c->h64, c->pfix, c->err);
-    note_launch();
+    if ((rc = launch_gather_h(c, h, s))) return rc;
     // the smoothing lengths are checked before any walk uses them
     cudaMemcpyAsync(c->host_small + 1, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
     if ((rc = check_cuda(cudaStreamSynchronize(s), "smoothing-length check"))) return rc;
