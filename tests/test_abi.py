@@ -64,3 +64,49 @@ def test_default_params_and_error_text(lib_path):
     assert lib.sphgrp_ctx_create(None, None, 10) == -1
     assert lib.sphgrp_ctx_create(ctypes.byref(h), None, 0) == -1
     assert b"n_max" in lib.sphgrp_last_error()
+
+
+_CTYPES = {"double": ctypes.c_double, "int": ctypes.c_int, "int64_t": ctypes.c_int64}
+
+
+def _struct_fields(name):
+    """(type, field) of a typedef struct in include/sphgrp.h, in declaration order."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sphgrp.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct " + name + r"\s*\{(.*?)\}\s*" + name + ";", text, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"(const )?([\w]+)\s*(\*?)\s*(\w+)$", decl.replace("* ", " *"))
+        assert m, decl
+        out.append(("ptr" if m.group(3) else m.group(2), m.group(4)))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("sphgrp_params", "Params"), ("sphgrp_stats", "Stats"),
+                                          ("sphgrp_batch_io", "BatchIO")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes mirrors of the ABI structs have the header's fields, in order and of
+    the same C type (a layout mismatch would corrupt every call without a GPU error)."""
+    from paper_1810_09898_gb300 import binding
+
+    fields = _struct_fields(cname)
+    py = getattr(binding, pyname)._fields_
+    assert [f for _, f in fields] == [f for f, _ in py]
+    for (ctype, f), (_, pytype) in zip(fields, py):
+        if ctype == "ptr":
+            assert pytype is ctypes.c_void_p, f
+        else:
+            assert pytype is _CTYPES[ctype], f
+
+
+def test_batch_io_rejects_unknown_arrays():
+    import torch
+
+    from paper_1810_09898_gb300 import binding
+
+    io = binding.Batch._io({"pos": torch.zeros(3), "acc": torch.zeros(3)})
+    assert io.pos and io.acc and not io.vel
+    with pytest.raises(KeyError):
+        binding.Batch._io({"position": torch.zeros(3)})
