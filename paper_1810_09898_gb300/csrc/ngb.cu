@@ -162,11 +162,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint3
 // Per-member state of the four pair loops
 // ---------------------------------------------------------------------------------
 
-// position part shared by all members: centre-relative coordinates, fixed point
+// position part shared by all members: coordinates relative to the group centre (the
+// exact fixed-point position is reloaded by the rare paths that need it)
 struct MemberPos {
     float mx, my, mz;
-    uint32_t X, Y, Z;   // fixed-point position (exact pair differences)
-    float ox, oy, oz;
     bool precise;       // far from the group centre: physics from exact differences
     int rank;           // -1: slot empty
     int n;              // neighbours found
@@ -181,8 +180,6 @@ __device__ __forceinline__ bool pos_init(MemberPos& M, const SearchArgs& a, int 
     M.precise = false;
     if (rank < 0) {
         M.mx = M.my = M.mz = 0.0f;
-        M.X = M.Y = M.Z = 0u;
-        M.ox = M.oy = M.oz = 0.0f;
         return false;
     }
     uint4 P = a.pfix[rank];
@@ -190,8 +187,6 @@ __device__ __forceinline__ bool pos_init(MemberPos& M, const SearchArgs& a, int 
     M.mx = rel_coord(P.x, O.x, cx);
     M.my = rel_coord(P.y, O.y, cy);
     M.mz = rel_coord(P.z, O.z, cz);
-    M.X = P.x; M.Y = P.y; M.Z = P.z;
-    M.ox = O.x; M.oy = O.y; M.oz = O.z;
     M.precise = fmaxf(fabsf(M.mx), fmaxf(fabsf(M.my), fabsf(M.mz))) > kPreciseReach * hf;
     return true;
 }
@@ -378,7 +373,7 @@ struct DAdjTile {
 
 // kind policies
 struct KDens {
-    static constexpr int min_blocks = 7;   // resident blocks per SM (register budget; 0: compiler's choice)
+    static constexpr int min_blocks = 8;   // resident blocks per SM (register budget; 0: compiler's choice)
     static constexpr int id = 0;
     static constexpr bool sym = false;
     static constexpr int cap = kTileD;
@@ -471,9 +466,12 @@ __device__ __forceinline__ void precise_diff(const Mem& M, const SearchArgs& a, 
                                              float& dz, float& r2) {
     uint4 Q = a.pfix[crank];
     float4 O = a.poff[crank];
-    dx = fix_diff(Q.x, O.x, M.X, M.ox);
-    dy = fix_diff(Q.y, O.y, M.Y, M.oy);
-    dz = fix_diff(Q.z, O.z, M.Z, M.oz);
+    // the member's own fixed-point position, reloaded (rare path: no registers held)
+    const uint4 P = a.pfix[M.rank];
+    const float4 Om = a.poff[M.rank];
+    dx = fix_diff(Q.x, O.x, P.x, Om.x);
+    dy = fix_diff(Q.y, O.y, P.y, Om.y);
+    dz = fix_diff(Q.z, O.z, P.z, Om.z);
     r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
