@@ -77,6 +77,7 @@ struct Batch {
     int4* groups_all = nullptr;     // all-particle groups (backward)
     float4* hyd0b = nullptr;        // hydro inputs of the backward (all particles at h)
     float4* hyd1b = nullptr;
+    int32_t* start_tabs = nullptr;  // walk start tables, one per box
     // graph
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -301,6 +302,7 @@ SearchArgs batch_args(Batch* b, bool all) {
     a.nu = (int)b->n;   // bound only; groups4 carries the ranges
     a.g = b->max_g;
     a.groups4 = all ? b->groups_all : b->groups;
+    a.start_tab = b->start_tabs;   // one start table per box, indexed by the box's root
     a.ngroups_dev = b->dsc + (all ? kNGroupsAll : kNGroups);
     return a;
 }
@@ -320,7 +322,9 @@ int issue_step(Batch* b, const sphgrp_batch_io* io, int flags, cudaStream_t s) {
         return rc;
     if ((rc = gather_particles(c, io->pos, io->m, s))) return rc;
     if ((rc = launch_gather_h(c, io->h, s))) return rc;
-    if ((rc = build_forest(c, b->nbox, b->box_off, b->lvl, b->blo, b->bhi, b->dsc + kTot, s))) return rc;
+    if ((rc = build_forest(c, b->nbox, b->box_off, b->lvl, b->blo, b->bhi, b->dsc + kTot, b->box_of_rank,
+                           b->start_tabs, s)))
+        return rc;
     // density with the smoothing-length iteration over the active groups
     if ((rc = make_batch_groups(b, false, -1, io->active, s))) return rc;
     {
@@ -498,6 +502,7 @@ int sphgrp_batch_create(sphgrp_batch** out, const sphgrp_params* params, int nbo
     rc = rc ? rc : dalloc(&b->groups_all, n);
     rc = rc ? rc : dalloc(&b->hyd0b, n);
     rc = rc ? rc : dalloc(&b->hyd1b, n);
+    rc = rc ? rc : dalloc(&b->start_tabs, (int64_t)nbox * kStartTableSize);
     rc = rc ? rc : alloc_forest(b->c, node_cap);
     rc = rc ? rc : backward_buffers(b->c);
     if (!rc && cudaMallocHost(&b->host, (2 + kNScalars) * sizeof(int32_t)) != cudaSuccess) rc = SPHGRP_ENOMEM;
@@ -530,7 +535,8 @@ int sphgrp_batch_destroy(sphgrp_batch* w) {
     drop_graph(b);
     void* ptrs[] = {b->box_off, b->box_g, b->box_split, b->box_cls, b->box_of_rank, b->tmp64a, b->tmp64b,
                     b->tmp32a, b->tmp32b, b->lvl, b->blo, b->bhi, b->U_all, b->dsc, b->box_act, b->box_chunk,
-                    b->chunks, b->ccnt, b->coff, b->gtmp, b->groups, b->groups_all, b->hyd0b, b->hyd1b};
+                    b->chunks, b->ccnt, b->coff, b->gtmp, b->groups, b->groups_all, b->hyd0b, b->hyd1b,
+                    b->start_tabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->host) cudaFreeHost(b->host);

@@ -983,15 +983,17 @@ __device__ __forceinline__ uint32_t cell_morton(uint32_t x, uint32_t y, uint32_t
     return m;
 }
 
-// First node of the walk: the node of the deepest cell (level <= kStartLevels) that
+// First node of the walk: the node of the deepest cell (level <= kStartLevels) of the
+// tree rooted at `root` (tab: that tree's start table) that
 // holds the whole search sphere (centre C, radius Rb in box units).  Every particle
 // within the sphere lies in that cell and hence in that node's subtree (a node is the
 // set of particles whose keys share its cell's prefix).  Cells the tree did not reach
 // fall back to the nearest ancestor cell with a node.
-__device__ __forceinline__ int walk_start(const SearchArgs& a, uint32_t cx, uint32_t cy, uint32_t cz, float Rb) {
+__device__ __forceinline__ int walk_start(const int32_t* __restrict__ tab, int root, uint32_t cx, uint32_t cy,
+                                          uint32_t cz, float Rb) {
     // radius in fixed-point units, rounded up, plus the sub-unit offsets of the positions
     const double Ru = ceil((double)Rb * 4294967296.0 * (1.0 + 1e-6)) + 2.0;
-    if (!(Ru < 2147483648.0)) return 0;
+    if (!(Ru < 2147483648.0)) return root;
     const int64_t r = (int64_t)Ru;
     int lvl = kStartLevels;
     const uint32_t c3[3] = {cx, cy, cz};
@@ -1002,11 +1004,11 @@ __device__ __forceinline__ int walk_start(const SearchArgs& a, uint32_t cx, uint
         else lvl = min(lvl, __clz((uint32_t)lo ^ (uint32_t)hi));
     }
     for (; lvl >= 1; --lvl) {
-        const int nd = a.start_tab[start_table_offset(lvl) +
-                                   cell_morton(cx >> (32 - lvl), cy >> (32 - lvl), cz >> (32 - lvl), lvl)];
+        const int nd = tab[start_table_offset(lvl) +
+                           cell_morton(cx >> (32 - lvl), cy >> (32 - lvl), cz >> (32 - lvl), lvl)];
         if (nd >= 0) return nd;
     }
-    return 0;
+    return root;
 }
 
 // One group's walk from node `root` and the member x candidate filter of every staged
@@ -1035,7 +1037,10 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
     // reach stays below half the box (symmetric: with the largest h of the tree)
     const float reach = K::sym ? Rg + fmaxf(hmax_g, __uint_as_float(a.ncen[root].w)) : rlane;
     const bool wrap_safe = reach < 0.49f;
-    const int start = (a.start_tab && root == 0) ? walk_start(a, cx, cy, cz, reach) : root;
+    // the start table of the walk's tree (one per box of a forest, whose roots are the
+    // first nodes)
+    const int start = a.start_tab ? walk_start(a.start_tab + (size_t)root * kStartTableSize, root, cx, cy, cz, reach)
+                                  : root;
 
     // The stack lives in shared memory; entries that do not fit go to this warp's
     // overflow area in global memory (a second stack, drained when the first is empty:

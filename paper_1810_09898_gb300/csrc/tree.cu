@@ -444,6 +444,25 @@ __global__ void k_hmax_level_dev(const int32_t* __restrict__ lvl, int level, con
     }
 }
 
+// Start tables of a forest (one per box, see k_start_table): every node of levels
+// 1 .. kStartLevels enters its box's table under its cell.
+__global__ void k_start_table_forest(const int32_t* __restrict__ lvl, const int4* __restrict__ nlink,
+                                     const int32_t* __restrict__ nlevel, const uint4* __restrict__ pfix,
+                                     const int32_t* __restrict__ box_of_rank, int32_t* __restrict__ tab) {
+    const int first = lvl[1], count = lvl[kStartLevels + 1] - first;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const int id = first + k;
+        const int l = nlevel[id];
+        const int4 L = nlink[id];
+        if (l < 1 || l > kStartLevels || L.y <= 0) continue;
+        const uint4 P = pfix[L.x];
+        const uint32_t x = P.x >> (32 - l), y = P.y >> (32 - l), z = P.z >> (32 - l);
+        uint32_t m = 0;
+        for (int b = l - 1; b >= 0; --b) m = (m << 3) | (((x >> b) & 1u) << 2) | (((y >> b) & 1u) << 1) | ((z >> b) & 1u);
+        tab[(size_t)box_of_rank[L.x] * kStartTableSize + start_table_offset(l) + m] = id;
+    }
+}
+
 int alloc_forest(Ctx* c, int64_t cap) {
     Tree& t = c->tree;
     if (t.cap >= cap) return SPHGRP_OK;
@@ -470,9 +489,9 @@ int alloc_forest(Ctx* c, int64_t cap) {
 // lvl: device, kKeyLevels + 3 entries; blo/bhi: device scratch of t.cap entries;
 // tot: one device int.  Uses c->flag and c->scan as per-level scratch.
 int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uint4* blo, uint4* bhi, int32_t* tot,
-                 cudaStream_t s) {
+                 const int32_t* box_of_rank, int32_t* start_tabs, cudaStream_t s) {
     Tree& t = c->tree;
-    c->start_valid = false;   // forest walks start at their box's root
+    c->start_valid = false;   // the single-box table does not describe a forest
     const int64_t n = c->n;
     k_forest_roots<<<blocks_for(std::max(nbox, kKeyLevels + 3), 256), 256, 0, s>>>(nbox, box_off_dev, t.nlink,
                                                                                  t.next, t.nlevel, lvl);
@@ -493,6 +512,11 @@ int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uin
     }
     k_box_final_dev<<<kForestGrid, 256, 0, s>>>(lvl, blo, bhi, t.ncen, t.next);
     note_launch();
+    if (start_tabs) {
+        cudaMemsetAsync(start_tabs, 0xff, (size_t)nbox * kStartTableSize * sizeof(int32_t), s);
+        k_start_table_forest<<<kForestGrid, 256, 0, s>>>(lvl, t.nlink, t.nlevel, c->pfix, box_of_rank, start_tabs);
+        note_launch();
+    }
     return check_cuda(cudaGetLastError(), "forest build");
 }
 
