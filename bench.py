@@ -378,6 +378,53 @@ def measured_traffic(kind: str, members_per_launch: float):
     return None if per is None else per * members_per_launch
 
 
+def per_pass(P, mode: int, g: int, reps: int = 5) -> dict:
+    """Per-pass metric at converged h: one density pass (no iteration) and one hydro pass
+    over the active particles, N_act / (t_density + t_hydro), CUDA events per pass."""
+    torch = P.torch
+    c = P.ctx
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    td, th = [], []
+    for rep in range(reps + 1):
+        ev[0].record(stream)
+        c.density(P.act, P.h, 0, mode, g, P.rho, P.drho, P.f, P.nn)
+        ev[1].record(stream)
+        c.hydro_force(P.act, P.h, P.rho, P.f, P.vel, P.u, mode, g, P.acc, P.dudt, P.nnh)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            td.append(ev[0].elapsed_time(ev[1]))
+            th.append(ev[1].elapsed_time(ev[2]))
+    d, h = float(np.median(td)), float(np.median(th))
+    return {"density_ms": d, "hydro_ms": h, "value": P.n_act / ((d + h) / 1e3), "unit": UNIT}
+
+
+def active_leg(P, frac: float, g: int, steps: int, warmup: int, dist, rank: int) -> dict:
+    """The same step with a fraction of the particles active in key-order runs (mean
+    length 32); inactive particles keep their converged h, rho and f."""
+    import sphgen
+
+    torch, sg = P.torch, P.sg
+    keep = (P.act, P.h_init, P.n_act)
+    mask = sphgen.active_rank_mask(P.n, frac, 32.0, np.random.default_rng(2000 + rank))
+    act = np.sort(P.perm.cpu().numpy()[np.flatnonzero(mask)]).astype(np.int32)
+    P.act = torch.from_numpy(act).to(P.dev)
+    P.n_act = len(act)
+    h = P.h.clone()
+    rng = np.random.default_rng(3000 + rank)
+    scat = torch.from_numpy(np.exp(P.a.h_scatter * rng.standard_normal(len(act)))).to(P.dev)
+    h[P.act.long()] *= scat
+    P.h_init = h
+    out = {"fraction": frac, "n_active": P.n_act}
+    for name, mode, gs in (("grouped", sg.GROUPED, g), ("individual", sg.INDIVIDUAL, 1)):
+        ms, _, _ = timed(P, lambda cl: P.step(mode, gs, cl), steps, warmup, dist)
+        out[name] = {"ms_per_step": ms / steps, "value": P.n_act / (ms / steps / 1e3)}
+    out["speedup_grouped"] = out["individual"]["ms_per_step"] / out["grouped"]["ms_per_step"]
+    P.act, P.h_init, P.n_act = keep
+    return out
+
+
 def backward_leg(a, rank: int, steps: int, warmup: int):
     """Forward + backward step on the clustered 2^21-particle workload: keys, sort,
     tree, density at converged h, hydro forces, then the adjoint of
@@ -610,6 +657,13 @@ def run_ours(a):
     col_i = []
     if not a.no_individual:
         ms_i, col_i, _ = timed(P, lambda c: P.step(sg.INDIVIDUAL, 1, c), steps, warmup, dist)
+    passes = {"grouped": per_pass(P, sg.GROUPED, g)}
+    if not a.no_individual:
+        passes["individual"] = per_pass(P, sg.INDIVIDUAL, 1)
+        passes["speedup_grouped"] = passes["grouped"]["value"] / passes["individual"]["value"]
+    low_active = None
+    if a.active >= 1.0 and not a.no_individual:
+        low_active = active_leg(P, 0.1, g, steps, warmup, dist, rank)
     e2e = None
     if not a.no_e2e:
         for _ in range(2):
@@ -664,6 +718,8 @@ def run_ours(a):
         "clocks": clocks,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "per_pass_converged_h": passes,
+        "active_10pct": low_active,
         "backward": back,
         "batch": batch,
     }
