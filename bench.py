@@ -298,6 +298,22 @@ class Problem:
         return h2d, d2h
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over all ranks (every rank gets it); the value itself at N = 1."""
+    if not dist:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(world: int, units_per_rank: int, ms_per_step: float) -> float:
+    """Whole-job throughput of N replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 def timed(P, fn, steps, warmup, dist):
     torch = P.torch
     for _ in range(warmup):
@@ -318,11 +334,7 @@ def timed(P, fn, steps, warmup, dist):
     launches = P.sg.kernel_launches() - l0
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=P.dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, P.dev)
     return ms, collect, launches
 
 
@@ -674,13 +686,9 @@ def run_ours(a):
         t0 = time.perf_counter()
         for _ in range(steps):
             P.step_e2e(g)
-        t_e2e = (time.perf_counter() - t0) / steps
-        if dist:
-            tt = torch.tensor([t_e2e], device=P.dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / steps, dist, P.dev)
         h2d, d2h = P.io_bytes()
-        e2e = {"value": world * P.n_act / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": replicas_value(world, P.n_act, 1e3 * t_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e}
     back = None
     if not a.no_backward:
@@ -699,7 +707,7 @@ def run_ours(a):
             dist.destroy_process_group()
         return
     ms_step = ms_g / steps
-    value = world * P.n_act / (ms_step / 1e3)
+    value = replicas_value(world, P.n_act, ms_step)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -709,7 +717,7 @@ def run_ours(a):
                    "h_init": f"converged h x exp({a.h_scatter} N(0,1)) per step",
                    "l2": "inputs larger than L2 (no flush needed)", "parallelism": f"replicas x{world}"},
         "individual": None if ms_i is None else {
-            "value": world * P.n_act / (ms_i / steps / 1e3), "ms_per_step": ms_i / steps,
+            "value": replicas_value(world, P.n_act, ms_i / steps), "ms_per_step": ms_i / steps,
             "speedup_grouped": (ms_i / steps) / ms_step},
         "roofline": roof,
         "search_detail": detail,
