@@ -91,14 +91,19 @@ typedef struct sphgrp_params {
                            SPHGRP_GROUP_RADIUS (Sec. 3.1, the paper's rule): a group starts at an
                            active particle and takes the following ones while they lie within
                            R = group_f * h of its first particle, at most group_size of them
-                           (the scan restarts at the start of every run of 1024 actives) */
+                           (the scan restarts at the start of every run of 1024 actives);
+                           SPHGRP_GROUP_TREE: see group_level */
     double group_f;     /* R / h of the radius mode, e.g. 0.5 */
+    int group_level;    /* depth of the tree mode (SPHGRP_GROUP_TREE, the octree grouping of
+                           Sec. 3): a group is the active particles under one node of this
+                           depth (the actives sharing the key's first 3 * group_level bits),
+                           cut into pieces of at most group_size; 1 .. 21, e.g. 7 */
     int stack_shared;   /* walk-stack entries per warp kept in shared memory (32 .. 256); deeper
                            walks continue in a global overflow area.  e.g. 256 */
 } sphgrp_params;
 
 enum { SPHGRP_ITER_PASSES = 0, SPHGRP_ITER_IN_GROUP = 1 };
-enum { SPHGRP_GROUP_COUNT = 0, SPHGRP_GROUP_RADIUS = 1 };
+enum { SPHGRP_GROUP_COUNT = 0, SPHGRP_GROUP_RADIUS = 1, SPHGRP_GROUP_TREE = 2 };
 
 enum { SPHGRP_CENTRE_FIRST = 0, SPHGRP_CENTRE_BOX = 1 };
 

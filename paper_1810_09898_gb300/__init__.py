@@ -15,6 +15,7 @@ from .binding import (  # noqa: F401
     DENSITY,
     GROUP_COUNT,
     GROUP_RADIUS,
+    GROUP_TREE,
     GROUPED,
     HYDRO,
     INDIVIDUAL,

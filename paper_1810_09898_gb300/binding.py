@@ -16,7 +16,7 @@ _LIB_PATH = os.path.join(HERE, "_build", "libsphgrp.so")
 INDIVIDUAL, GROUPED = 0, 1
 CENTRE_FIRST, CENTRE_BOX = 0, 1
 ITER_PASSES, ITER_IN_GROUP = 0, 1
-GROUP_COUNT, GROUP_RADIUS = 0, 1
+GROUP_COUNT, GROUP_RADIUS, GROUP_TREE = 0, 1, 2
 DENSITY, HYDRO = 0, 1
 
 EXPORTED = [
@@ -81,6 +81,7 @@ class Params(ctypes.Structure):
         ("iteration", ctypes.c_int),
         ("group_mode", ctypes.c_int),
         ("group_f", ctypes.c_double),
+        ("group_level", ctypes.c_int),
         ("stack_shared", ctypes.c_int),
     ]
 

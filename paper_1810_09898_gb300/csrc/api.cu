@@ -226,10 +226,74 @@ int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s,
 
 // Groups of the grouped form over the work list U (see k_split_groups); fills
 // a->groups and a->ngroups.  Reads the group count back (stream sync).
+// Tree grouping (Sec. 3): the actives under one node of depth L share the key's first
+// 3 L bits, and every node is a contiguous range of the key order, so a group is a run
+// of consecutive actives with one prefix, cut into pieces of at most g.
+__global__ void k_prefix_runs(int nu, const int32_t* __restrict__ U, const uint64_t* __restrict__ keys, int shift,
+                              int32_t* __restrict__ flag) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nu) return;
+    flag[u] = (u == 0 || (keys[U[u]] >> shift) != (keys[U[u - 1]] >> shift)) ? 1 : 0;
+}
+
+// run k starts at the entry u whose flag begins it: run_start[pos[u]] = u
+__global__ void k_run_starts(int nu, const int32_t* __restrict__ flag, const int32_t* __restrict__ pos,
+                             int32_t* __restrict__ run_start) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < nu && flag[u]) run_start[pos[u]] = u;
+}
+
+__global__ void k_run_pieces(int nruns, int nu, int g, const int32_t* __restrict__ run_start,
+                             int32_t* __restrict__ pieces) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nruns) return;
+    const int len = (k + 1 < nruns ? run_start[k + 1] : nu) - run_start[k];
+    pieces[k] = (len + g - 1) / g;
+}
+
+__global__ void k_run_groups(int nruns, int nu, int g, const int32_t* __restrict__ run_start,
+                             const int32_t* __restrict__ piece_off, int2* __restrict__ groups) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nruns) return;
+    const int s0 = run_start[k], e0 = k + 1 < nruns ? run_start[k + 1] : nu;
+    int o = piece_off[k];
+    for (int s1 = s0; s1 < e0; s1 += g) groups[o++] = make_int2(s1, min(g, e0 - s1));
+}
+
+int make_tree_groups(Ctx* c, SearchArgs* a, const int32_t* U, int nu, int g, cudaStream_t s) {
+    a->groups = nullptr;
+    a->ngroups = 0;
+    if (nu <= 0) return SPHGRP_OK;
+    const int shift = 3 * (kKeyLevels - c->p.group_level);
+    int32_t* nruns_dev = reinterpret_cast<int32_t*>(c->work) + 20;
+    int32_t* ngroups_dev = reinterpret_cast<int32_t*>(c->work) + 21;
+    k_prefix_runs<<<blocks_for(nu, 256), 256, 0, s>>>(nu, U, c->keys, shift, c->grp_cnt);
+    note_launch();
+    int rc = exclusive_scan_i32(c, c->grp_cnt, c->grp_off, nu, nruns_dev, s);
+    if (rc) return rc;
+    // run starts go to scan (free here), piece counts to grp_cnt, their offsets to grp_off
+    k_run_starts<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->grp_cnt, c->grp_off, c->scan);
+    note_launch();
+    cudaMemcpyAsync(c->host_small + 41, nruns_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "tree groups"))) return rc;
+    const int nruns = c->host_small[41];
+    k_run_pieces<<<blocks_for(nruns, 256), 256, 0, s>>>(nruns, nu, g, c->scan, c->grp_cnt);
+    note_launch();
+    if ((rc = exclusive_scan_i32(c, c->grp_cnt, c->grp_off, nruns, ngroups_dev, s))) return rc;
+    k_run_groups<<<blocks_for(nruns, 256), 256, 0, s>>>(nruns, nu, g, c->scan, c->grp_off, c->groups);
+    note_launch();
+    cudaMemcpyAsync(c->host_small + 40, ngroups_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "tree group count"))) return rc;
+    a->groups = c->groups;
+    a->ngroups = c->host_small[40];
+    return SPHGRP_OK;
+}
+
 int make_groups(Ctx* c, SearchArgs* a, const int32_t* U, int nu, int g, cudaStream_t s) {
     a->groups = nullptr;
     a->ngroups = (nu + g - 1) / g;
     const bool radius = c->p.group_mode == SPHGRP_GROUP_RADIUS;
+    if (c->p.group_mode == SPHGRP_GROUP_TREE) return make_tree_groups(c, a, U, nu, g, s);
     if (nu <= 0 || g <= 1 || (!radius && !(c->p.group_split > 0.0))) return SPHGRP_OK;
     int nch = radius ? (nu + kRadiusRun - 1) / kRadiusRun : (nu + g - 1) / g;
     int rc = radius ? launch_radius_groups(U, nu, g, c->p.group_f, c->pfix, c->poff, c->h64, c->groups_tmp,
@@ -309,6 +373,7 @@ void sphgrp_default_params(sphgrp_params* p) {
     p->iteration = SPHGRP_ITER_PASSES;
     p->group_mode = SPHGRP_GROUP_COUNT;
     p->group_f = 0.5;
+    p->group_level = 7;
     p->stack_shared = 256;
 }
 
@@ -330,7 +395,9 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     if (c->p.leaf_size < 1 || c->p.leaf_size > 1024 || !(c->p.nngb > 0) || !(c->p.nngb_tol >= 0) ||
         c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX) ||
         (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP) ||
-        (c->p.group_mode != SPHGRP_GROUP_COUNT && c->p.group_mode != SPHGRP_GROUP_RADIUS) ||
+        (c->p.group_mode != SPHGRP_GROUP_COUNT && c->p.group_mode != SPHGRP_GROUP_RADIUS &&
+         c->p.group_mode != SPHGRP_GROUP_TREE) ||
+        (c->p.group_mode == SPHGRP_GROUP_TREE && (c->p.group_level < 1 || c->p.group_level > kKeyLevels)) ||
         (c->p.group_mode == SPHGRP_GROUP_RADIUS && !(c->p.group_f > 0.0 && c->p.group_f < 1e3)) ||
         c->p.stack_shared < 32 || c->p.stack_shared > kStackSharedMax) {
         delete c;

@@ -366,7 +366,51 @@ def test_rejects_bad_parameters(cuda_device):
     import paper_1810_09898_gb300 as sg
 
     for bad in ({"stack_shared": 16}, {"stack_shared": 512}, {"group_mode": 5}, {"group_mode": 1, "group_f": 0.0},
-                {"iteration": 3}, {"leaf_size": 0}, {"group_centre": 4}, {"max_iter": 0}):
+                {"iteration": 3}, {"leaf_size": 0}, {"group_centre": 4}, {"max_iter": 0},
+                {"group_mode": 2, "group_level": 0}, {"group_mode": 2, "group_level": 22}):
         with pytest.raises(sg.SphgrpError, match="EINVAL"):
             sg.Context(100, **bad)
     sg.Context(100, stack_shared=32, group_mode=1, group_f=0.7, iteration=1).close()
+
+
+# ---------------------------------------------------------------- tree-depth grouping (Sec. 3)
+
+@pytest.fixture(scope="module", params=[5, 8], ids=["level5", "level8"])
+def clu_tree(cuda_device, request):
+    """Groups are the actives under one octree node of a given depth."""
+    d = dataset("clustered", 24001, config=2)
+    return d, Gpu(d["pos"], d["m32"], group_mode=2, group_level=request.param), request.param
+
+
+def test_tree_groups_follow_the_rule(clu_tree):
+    d, G, level = clu_tree
+    h, _ = converged("clustered", 24001, 2)
+    act = active_runs(G.n, 0.3, 7, G.perm.cpu().numpy())
+    cap = 32
+    gfirst, members, goff, cand = G.supersets(act, h, 0, cap)
+    prefix = oracle.hilbert_keys(d["pos"])[members] >> np.uint64(3 * (21 - level))
+    sizes = np.diff(gfirst)
+    assert gfirst[-1] == len(members) and np.all(sizes >= 1) and np.all(sizes <= cap)
+    for k in range(len(sizes)):
+        a, b = gfirst[k], gfirst[k + 1]
+        assert np.all(prefix[a:b] == prefix[a]), k                      # one node per group
+        if b < len(members) and prefix[b] == prefix[a]:
+            assert b - a == cap, k                                        # cut only at the cap
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_tree_groups_sets_and_supersets(clu_tree, kind):
+    d, G, level = clu_tree
+    h, _ = converged("clustered", 24001, 2)
+    act = active_runs(G.n, 0.2, 8, G.perm.cpu().numpy())
+    _check_supersets(d, G, act, h, kind, 32, exact_chunks=False)
+    _compare_sets(G.ngb_sets(act, h, kind, 1, 32), oracle.ngb_sets(d["pos"], h, act, kind))
+
+
+def test_tree_groups_density(clu_tree):
+    d, G, level = clu_tree
+    h, _ = converged("clustered", 24001, 2)
+    out = G.density(np.arange(G.n, dtype=np.int32), h, 0, 1, 32)
+    ref = oracle.density(d["pos"], d["m32"].astype(np.float64), h)
+    assert np.array_equal(out["nngb"], ref["nngb"])
+    assert np.max(np.abs(out["rho"] / ref["rho"] - 1.0)) <= RHO_TOL
