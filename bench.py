@@ -338,7 +338,7 @@ def timed(P, fn, steps, warmup, dist):
     return ms, collect, launches
 
 
-def roofline(collect, peak_gbs):
+def roofline(collect, peak_gbs, clocks=None):
     """Dominant search kernel: algorithmic bytes per launch / event time per launch."""
     agg = {}
     for rec in collect:
@@ -367,9 +367,18 @@ def roofline(collect, peak_gbs):
                   "members_per_walk": v["members"] / max(1, v["walks"]),
                   "nodes_per_walk": v["nodes"] / max(1, v["walks"])} for k, v in agg.items()}
     traffic = measured_traffic(dom, A["members"] / max(1, A["launches"]))
+    # the FP32 side of the same launches: ~10 flop per member x candidate test (the
+    # difference, r^2, the threshold) and ~25 per true pair (kernel and sums), against
+    # 152 SMs x 128 lanes x 2 flop x the sampled SM clock
+    flops = (10.0 * A["tests"] + 25.0 * A["pairs"]) / max(1, A["launches"])
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu = {"achieved_tflops": flops / per_launch_s / 1e12, "peak_tflops": alu_peak,
+           "frac": flops / per_launch_s / 1e12 / alu_peak,
+           "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock (derived)"}
     return {"bound": "hbm", "kernel": f"k_group ({dom})", "achieved": achieved, "peak": peak_gbs,
             "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
-            "bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3,
+            "bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3, "alu": alu,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}, detail
 
 
@@ -697,7 +706,7 @@ def run_ours(a):
     if not a.no_batch:
         batch = batch_leg(a, rank, steps, warmup)
     peak = measured_peak_hbm()
-    roof, detail = roofline(col_g, peak)
+    roof, detail = roofline(col_g, peak, clocks)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_sample(a.cpu_n, a.h_scatter)
