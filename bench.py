@@ -562,6 +562,8 @@ def batch_leg(a, rank: int, steps: int, warmup: int):
     B.tune(io)
     tune_s = time.perf_counter() - t0
     tuned = {("uniform" if c == 0 else "clustered"): B.get_config(c) for c in (0, 1)}
+    for cfg in tuned.values():   # the class's own throughput: one density + hydro pass
+        cfg["pass_active_per_s"] = cfg["tuned_members"] / (cfg["tuned_pass_ms"] / 1e3) if cfg["tuned_pass_ms"] else None
     rng2 = np.random.default_rng(277 + rank)
     io["g_acc"] = t(rng2.standard_normal((n, 3)), torch.float32)
     io["g_rho"] = t(rng2.standard_normal(n), torch.float32)

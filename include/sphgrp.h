@@ -319,9 +319,12 @@ int sphgrp_batch_run(sphgrp_batch* b, const sphgrp_batch_io* io, int flags, cuda
 int sphgrp_batch_tune(sphgrp_batch* b, const sphgrp_batch_io* io, cudaStream_t stream);
 
 /* Read / set the configuration of one class (group_size in [1, 128], max_slices in
- * {1, 2, 4}, group_split >= 0; 0 = no splitting).  Setting drops the captured graph. */
+ * {1, 2, 4}, group_split >= 0; 0 = no splitting).  Setting drops the captured graph.
+ * pass_ms / pass_members (host, may be NULL) receive the autotuner's best time of one
+ * density + hydro pass over the class's active particles and their count (0 when the
+ * class was not tuned): the class's own throughput. */
 int sphgrp_batch_get_config(sphgrp_batch* b, int cls, int* group_size, int* max_slices,
-                            double* group_split);
+                            double* group_split, double* pass_ms, int64_t* pass_members);
 int sphgrp_batch_set_config(sphgrp_batch* b, int cls, int group_size, int max_slices,
                             double group_split);
 

@@ -42,6 +42,8 @@ struct ClassCfg {
     int g = 16;
     int smax = 4;
     float split = 2.0f;
+    float tuned_ms = 0.0f;        // the tuner's best density + hydro pass over the class
+    int64_t tuned_members = 0;    // active particles of that pass
 };
 
 struct Batch {
@@ -593,9 +595,12 @@ int sphgrp_batch_run(sphgrp_batch* w, const sphgrp_batch_io* io, int flags, cuda
     return read_status(b, flags);
 }
 
-int sphgrp_batch_get_config(sphgrp_batch* w, int cls, int* group_size, int* max_slices, double* group_split) {
+int sphgrp_batch_get_config(sphgrp_batch* w, int cls, int* group_size, int* max_slices, double* group_split,
+                            double* pass_ms, int64_t* pass_members) {
     if (!w || cls < 0 || cls >= SPHGRP_BATCH_CLASSES) return set_error(SPHGRP_EINVAL, "bad batch or class");
     const ClassCfg& cc = w->b.cfg[cls];
+    if (pass_ms) *pass_ms = cc.tuned_ms;
+    if (pass_members) *pass_members = cc.tuned_members;
     if (group_size) *group_size = cc.g;
     if (max_slices) *max_slices = cc.smax;
     if (group_split) *group_split = cc.split;
@@ -608,7 +613,7 @@ int sphgrp_batch_set_config(sphgrp_batch* w, int cls, int group_size, int max_sl
     if (max_slices != 1 && max_slices != 2 && max_slices != 4) return set_error(SPHGRP_EINVAL, "max_slices not 1, 2, 4");
     if (!(group_split >= 0.0)) return set_error(SPHGRP_EINVAL, "group_split < 0");
     Batch* b = &w->b;
-    b->cfg[cls] = ClassCfg{group_size, max_slices, (float)group_split};
+    b->cfg[cls] = ClassCfg{group_size, max_slices, (float)group_split, 0.0f, 0};
     drop_graph(b);
     return upload_box_cfg(b, b->cap_stream);
 }
@@ -645,7 +650,7 @@ int sphgrp_batch_tune(sphgrp_batch* w, const sphgrp_batch_io* io, cudaStream_t s
         float best = 3.0e38f;
         ClassCfg best_cfg = keep;
         for (const Cand& cd : cands) {
-            b->cfg[cls] = ClassCfg{cd.g, cd.smax, cd.split};
+            b->cfg[cls] = ClassCfg{cd.g, cd.smax, cd.split, 0.0f, 0};
             if ((rc = upload_box_cfg(b, s))) break;
             float t_best = 3.0e38f;
             for (int rep = 0; rep < 2 && !rc; ++rep) {
@@ -673,6 +678,15 @@ int sphgrp_batch_tune(sphgrp_batch* w, const sphgrp_batch_io* io, cudaStream_t s
             }
         }
         b->cfg[cls] = rc ? keep : best_cfg;
+        if (!rc) {
+            int32_t members = 0;
+            rc = check_cuda(cudaMemcpyAsync(b->host + 2 + kNu, b->dsc + kNu, sizeof(int32_t), cudaMemcpyDeviceToHost, s),
+                            "tuned class size");
+            if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "tuned class size");
+            members = b->host[2 + kNu];
+            b->cfg[cls].tuned_ms = best;
+            b->cfg[cls].tuned_members = members;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -239,8 +239,13 @@ def test_batch_tune_and_config(cuda_device):
         act = np.flatnonzero(b["active"][s])
         assert np.array_equal(out["nngb"][s][act], ref["nngb"][s][act]) or \
             np.mean(np.abs(out["h"][s][act] / ref["h"][s][act] - 1.0) <= 1e-5) > 0.999
+    for cls in (0, 1):
+        cfg = B.get_config(cls)
+        assert cfg["tuned_pass_ms"] > 0.0 and cfg["tuned_members"] == int(
+            sum(b["active"][b["box_off"][k]:b["box_off"][k + 1]].sum() for k in range(5) if b["box_class"][k] == cls))
     B.set_config(1, 8, 2, 2.0)
-    assert B.get_config(1) == {"group_size": 8, "max_slices": 2, "group_split": 2.0}
+    assert B.get_config(1) == {"group_size": 8, "max_slices": 2, "group_split": 2.0, "tuned_pass_ms": 0.0,
+                               "tuned_members": 0}
     with pytest.raises(sg.SphgrpError, match="EINVAL"):
         B.set_config(1, 0, 2, 2.0)
     with pytest.raises(sg.SphgrpError, match="EINVAL"):
