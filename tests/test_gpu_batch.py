@@ -274,3 +274,65 @@ def test_batch_rejects_bad_input(cuda_device):
         B.run(io.a, backward=True)   # no g_acc
     B.close()
     torch.cuda.synchronize()
+
+
+def test_batch_single_box_equals_context(cuda_device):
+    """One box through the batch call gives the single-box entry points' results."""
+    import torch
+
+    import paper_1810_09898_gb300 as sg
+
+    d = sphgen.make("clustered", 12000, config=33)
+    n = 12000
+    dev = torch.device("cuda:0")
+    m32 = d["m"].astype(np.float32)
+    b = {"pos": d["pos"], "m32": m32, "vel32": d["vel"].astype(np.float32), "u32": d["u"].astype(np.float32),
+         "h0": np.full(n, d["h0"]), "active": np.ones(n, bool), "rho0": np.zeros(n, np.float32),
+         "f0": np.ones(n, np.float32), "box_off": np.array([0, n])}
+    B = sg.Batch(b["box_off"], [1])
+    io = Io(b)
+    B.run(io.a)
+    out = io.host()
+    B.close()
+    ctx = sg.Context(n)
+    pos = torch.as_tensor(d["pos"], device=dev)
+    ctx.sfc_keys_sort(pos)
+    ctx.tree_build(pos, torch.as_tensor(m32, device=dev))
+    h = torch.as_tensor(out["h"], device=dev)
+    act = torch.arange(n, dtype=torch.int32, device=dev)
+    rho, drho, f = (torch.zeros(n, device=dev) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=dev)
+    ctx.density(act, h, 0, sg.GROUPED, 16, rho, drho, f, nn)
+    assert np.array_equal(nn.cpu().numpy(), out["nngb"])
+    assert np.max(np.abs(rho.cpu().numpy() / out["rho"] - 1.0)) <= 1e-6
+    ref = oracle.density(d["pos"], m32.astype(np.float64), out["h"])
+    neff = 4.0 * np.pi / 3.0 * out["h"] ** 3 * ref["rho"] / m32
+    assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3)
+    ctx.close()
+
+
+def test_batch_inactive_boxes_and_no_actives(cuda_device):
+    """A box without active particles is left untouched; a call with none at all does
+    nothing and succeeds."""
+    import paper_1810_09898_gb300 as sg
+
+    b = dict(_case())
+    act = b["active"].copy()
+    s1 = slice(int(b["box_off"][1]), int(b["box_off"][2]))
+    act[s1] = False
+    b["active"] = act
+    B = sg.Batch(b["box_off"], b["box_class"])
+    io = Io(b)
+    B.run(io.a)
+    out = io.host()
+    assert np.array_equal(out["h"][s1], b["h0"][s1])
+    assert np.all(out["acc"][s1] == 0.0) and np.all(out["nngb"][s1] == 0)
+    s0 = slice(int(b["box_off"][0]), int(b["box_off"][1]))
+    assert np.all(out["nngb"][s0][b["active"][s0]] > 0)
+    b["active"] = np.zeros_like(act)
+    io2 = Io(b)
+    B.run(io2.a)
+    out2 = io2.host()
+    assert np.array_equal(out2["h"], b["h0"]) and np.all(out2["acc"] == 0.0)
+    assert B.stats()["pairs"] == 0
+    B.close()
