@@ -1042,9 +1042,9 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
     const int start = a.start_tab ? walk_start(a.start_tab + (size_t)root * kStartTableSize, root, cx, cy, cz, reach)
                                   : root;
 
-    // The stack lives in shared memory; entries that do not fit go to this warp's
-    // overflow area in global memory (a second stack, drained when the first is empty:
-    // the order of the walk changes, the superset does not).
+    // The stack lives in shared memory (at most a.stack_cap entries); when it fills up,
+    // its oldest entries move to this warp's overflow area in global memory, which holds
+    // the bottom of the stack and refills the shared part when that runs empty.
     uint32_t* spill = a.stack_spill + (size_t)(blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5)) * kSpillCap;
     int sp = 1, gsp = 0;
     if (lane == 0) W.stack[0] = (uint32_t)start << 3;   // one node
