@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kGrid = 1024;   // blocks of the grid-stride kernels
 constexpr int kLevels = kKeyLevels + 3;
+constexpr int kMaxTableBoxes = 256;   // boxes that get a walk start table
 
 // device scalars of a batch call
 enum Scalar {
@@ -504,7 +505,9 @@ int sphgrp_batch_create(sphgrp_batch** out, const sphgrp_params* params, int nbo
     rc = rc ? rc : dalloc(&b->groups_all, n);
     rc = rc ? rc : dalloc(&b->hyd0b, n);
     rc = rc ? rc : dalloc(&b->hyd1b, n);
-    rc = rc ? rc : dalloc(&b->start_tabs, (int64_t)nbox * kStartTableSize);
+    // walk start tables: 1.2 MB per box, so only for batches of up to kMaxTableBoxes
+    // boxes (larger batches walk from their boxes' roots)
+    if (nbox <= kMaxTableBoxes) rc = rc ? rc : dalloc(&b->start_tabs, (int64_t)nbox * kStartTableSize);
     rc = rc ? rc : alloc_forest(b->c, node_cap);
     rc = rc ? rc : backward_buffers(b->c);
     if (!rc && cudaMallocHost(&b->host, (2 + kNScalars) * sizeof(int32_t)) != cudaSuccess) rc = SPHGRP_ENOMEM;

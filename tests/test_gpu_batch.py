@@ -336,3 +336,32 @@ def test_batch_inactive_boxes_and_no_actives(cuda_device):
     assert np.array_equal(out2["h"], b["h0"]) and np.all(out2["acc"] == 0.0)
     assert B.stats()["pairs"] == 0
     B.close()
+
+
+def test_batch_many_small_boxes(cuda_device):
+    """300 boxes: the box sort takes two radix passes (more than 256 boxes) and the walks
+    start at the boxes' roots (no start tables for more than 256 boxes); sampled boxes
+    match the oracle."""
+    import paper_1810_09898_gb300 as sg
+
+    b = sphgen.batch(300, 1500, 3000, config=35, frac_min=0.5, frac_max=1.0)
+    n = int(b["box_off"][-1])
+    b["m32"] = b["m"].astype(np.float32)
+    b["vel32"] = b["vel"].astype(np.float32)
+    b["u32"] = b["u"].astype(np.float32)
+    b["rho0"] = np.ones(n, np.float32)
+    b["f0"] = np.ones(n, np.float32)
+    B = sg.Batch(b["box_off"], b["box_class"])
+    io = Io(b)
+    B.run(io.a)
+    out = io.host()
+    B.close()
+    for k in (0, 137, 299):
+        s = slice(int(b["box_off"][k]), int(b["box_off"][k + 1]))
+        act = np.flatnonzero(b["active"][s]).astype(np.int32)
+        m = b["m32"][s].astype(np.float64)
+        chk = oracle.density(b["pos"][s], m, out["h"][s], targets=act)
+        neff = 4.0 * np.pi / 3.0 * out["h"][s][act] ** 3 * chk["rho"] / m[act]
+        assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3), k
+        assert np.array_equal(out["nngb"][s][act], chk["nngb"]), k
+        assert np.max(np.abs(out["rho"][s][act] / chk["rho"] - 1.0)) <= RHO_TOL, k
