@@ -399,6 +399,15 @@ def measured_traffic(kind: str, members_per_launch: float):
     return None if per is None else per * members_per_launch
 
 
+def guarded(fn, *args):
+    """Runs an optional leg of the bench; a failure is reported in its place instead of
+    losing the main line."""
+    try:
+        return fn(*args)
+    except Exception as e:  # noqa: BLE001 - any failure of an optional leg is reported
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def per_pass(P, mode: int, g: int, reps: int = 5) -> dict:
     """Per-pass metric at converged h: one density pass (no iteration) and one hydro pass
     over the active particles, N_act / (t_density + t_hydro), CUDA events per pass."""
@@ -680,13 +689,14 @@ def run_ours(a):
     col_i = []
     if not a.no_individual:
         ms_i, col_i, _ = timed(P, lambda c: P.step(sg.INDIVIDUAL, 1, c), steps, warmup, dist)
-    passes = {"grouped": per_pass(P, sg.GROUPED, g)}
+    passes = {"grouped": guarded(per_pass, P, sg.GROUPED, g)}
     if not a.no_individual:
-        passes["individual"] = per_pass(P, sg.INDIVIDUAL, 1)
-        passes["speedup_grouped"] = passes["grouped"]["value"] / passes["individual"]["value"]
+        passes["individual"] = guarded(per_pass, P, sg.INDIVIDUAL, 1)
+        if "value" in passes["grouped"] and "value" in passes["individual"]:
+            passes["speedup_grouped"] = passes["grouped"]["value"] / passes["individual"]["value"]
     low_active = None
     if a.active >= 1.0 and not a.no_individual:
-        low_active = active_leg(P, 0.1, g, steps, warmup, dist, rank)
+        low_active = guarded(active_leg, P, 0.1, g, steps, warmup, dist, rank)
     e2e = None
     if not a.no_e2e:
         for _ in range(2):
@@ -703,10 +713,10 @@ def run_ours(a):
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * t_e2e}
     back = None
     if not a.no_backward:
-        back = backward_leg(a, rank, steps, warmup)
+        back = guarded(backward_leg, a, rank, steps, warmup)
     batch = None
     if not a.no_batch:
-        batch = batch_leg(a, rank, steps, warmup)
+        batch = guarded(batch_leg, a, rank, steps, warmup)
     peak = measured_peak_hbm()
     roof, detail = roofline(col_g, peak, clocks)
     cpu = None
