@@ -447,11 +447,13 @@ def active_leg(P, frac: float, g: int, steps: int, warmup: int, dist, rank: int)
     h[P.act.long()] *= scat
     P.h_init = h
     out = {"fraction": frac, "n_active": P.n_act}
-    for name, mode, gs in (("grouped", sg.GROUPED, g), ("individual", sg.INDIVIDUAL, 1)):
-        ms, _, _ = timed(P, lambda cl: P.step(mode, gs, cl), steps, warmup, dist)
-        out[name] = {"ms_per_step": ms / steps, "value": P.n_act / (ms / steps / 1e3)}
-    out["speedup_grouped"] = out["individual"]["ms_per_step"] / out["grouped"]["ms_per_step"]
-    P.act, P.h_init, P.n_act = keep
+    try:
+        for name, mode, gs in (("grouped", sg.GROUPED, g), ("individual", sg.INDIVIDUAL, 1)):
+            ms, _, _ = timed(P, lambda cl: P.step(mode, gs, cl), steps, warmup, dist)
+            out[name] = {"ms_per_step": ms / steps, "value": P.n_act / (ms / steps / 1e3)}
+        out["speedup_grouped"] = out["individual"]["ms_per_step"] / out["grouped"]["ms_per_step"]
+    finally:
+        P.act, P.h_init, P.n_act = keep
     return out
 
 
