@@ -58,6 +58,7 @@ def lib():
             L.orc_hydro.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, dbl, dbl, dbl,
                                     dbl, i32, P, P, P, P, P]
             L.orc_threads.argtypes = []
+            L.orc_velocity_derivs.argtypes = [i64, P, P, P, P, P, P, P, i64, P, i32, P, P]
             L.orc_h_exact.argtypes = [i64, P, P, P, P, P, dbl, i32]
             L.orc_loss_grad.argtypes = [i64, P, P, P, P, P, P, P, P, P, dbl, dbl, dbl, dbl, dbl, i32,
                                         P, P, P, P]
@@ -187,6 +188,19 @@ def hydro(pos, vel, m, h, rho, f, u, targets=None, gamma=5.0 / 3.0, alpha=1.0, b
                     _p(u), nt, _p(t), gamma, alpha, beta, eps, int(use_tree), _p(ax), _p(ay),
                     _p(az), _p(dudt), _p(nn))
     return {"acc": np.stack([ax, ay, az], axis=1), "dudt": dudt, "nngb": nn}
+
+
+def velocity_derivs(pos, vel, m, h, rho, targets=None, use_tree=True):
+    """Divergence (nt,) and curl (nt, 3) of the velocity at the targets (density sets)."""
+    x, y, z = _xyz(pos)
+    n = len(x)
+    v = _f64(np.asarray(vel).reshape(n, 3))
+    t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    divv = np.empty(len(t))
+    curl = np.empty((len(t), 3))
+    lib().orc_velocity_derivs(n, _p(x), _p(y), _p(z), _p(v), _p(_f64(m)), _p(_f64(h)), _p(_f64(rho)), len(t),
+                              _p(t), int(use_tree), _p(divv), _p(curl))
+    return divv, curl
 
 
 # ----------------------------------------------------------------------------- backward

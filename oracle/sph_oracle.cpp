@@ -511,6 +511,47 @@ int64_t orc_density_iterate(int64_t n, const double* x, const double* y, const d
 // Monaghan viscosity Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar for v_ij . r_ij < 0
 // (else 0), mu = hbar v_ij.r_ij / (r^2 + eps hbar^2), bars = pair means.
 // Coincident pairs (r = 0) contribute nothing (the kernel gradient vanishes there).
+// Velocity divergence and curl of the targets over their density sets (the other
+// quantities a Gadget density pass hands to the hydro loop; not in the paper).  With
+// the SPH velocity gradient at h_i,
+//   G_ab(i) = -(1 / rho_i) sum_{j in N_i} m_j (v_i - v_j)_a (grad_i W(r_ij, h_i))_b,
+//   grad_i W = W'(r) (x_i - x_j) / r,
+// the divergence is tr G and the curl is (G_zy - G_yz, G_xz - G_zx, G_yx - G_xy).
+// A linear field v = A x gives G = c A with a scalar c near 1 on a uniform set.
+int orc_velocity_derivs(int64_t n, const double* x, const double* y, const double* z, const double* vel,
+                        const double* m, const double* h, const double* rho, int64_t nt,
+                        const int32_t* targets, int use_tree, double* divv, double* curl) {
+    Particles P{n, x, y, z};
+    Tree tree;
+    if (use_tree) build_tree(tree, n, x, y, z, nullptr);
+    parallel_for(nt, [&](int64_t t) {
+        std::vector<int32_t> cand, nb;
+        const int64_t i = targets[t];
+        density_at(P, m, h[i], use_tree ? &tree : nullptr, i, cand, nb);
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int32_t j : nb) {
+            double dx, dy, dz;
+            const double r2 = dist2(x, y, z, i, j, dx, dy, dz);
+            if (r2 == 0.0) continue;
+            const double r = std::sqrt(r2);
+            double w, dwdr;
+            m4_kernel(r, h[i], w, dwdr);
+            const double g[3] = {-dx / r * dwdr, -dy / r * dwdr, -dz / r * dwdr};   // x_i - x_j = -d
+            const double v[3] = {vel[3 * i] - vel[3 * j], vel[3 * i + 1] - vel[3 * j + 1],
+                                 vel[3 * i + 2] - vel[3 * j + 2]};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) G[a][b] -= m[j] * v[a] * g[b];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) G[a][b] /= rho[i];
+        divv[t] = G[0][0] + G[1][1] + G[2][2];
+        curl[3 * t] = G[2][1] - G[1][2];
+        curl[3 * t + 1] = G[0][2] - G[2][0];
+        curl[3 * t + 2] = G[1][0] - G[0][1];
+    });
+    return 0;
+}
+
 int orc_hydro(int64_t n, const double* x, const double* y, const double* z,
               const double* vx, const double* vy, const double* vz, const double* m,
               const double* h, const double* rho, const double* fgrad, const double* u,
