@@ -219,6 +219,21 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
                        const float* vel, const float* u, int mode, int group_size,
                        float* acc, float* dudt, int32_t* nngb, cudaStream_t stream);
 
+/* Velocity divergence and curl of the active particles over their density sets (the
+ * a6 neighbour definition, support h_i), the inputs of the viscosity limiters used with
+ * the Sec. 2.1 hydro loop.  The paper prints no formula for them; the standard SPH
+ * estimates are taken:
+ *   div v_i  = -(1/rho_i) sum_j m_j (v_i - v_j) . grad_i W(r_ij, h_i),
+ *   curl v_i =  (1/rho_i) sum_j m_j (v_i - v_j) x grad_i W(r_ij, h_i),
+ * grad_i W = dW/dr (x_i - x_j) / r, W the M4 spline of a6; pairs at r = 0 add nothing.
+ * h: device n FP64 (0 < h < 0.5); rho: device n FP32 (> 0 for active particles);
+ * vel: device n x 3 FP32 -- all particles.  divv: device n FP32, curlv: device n x 3
+ * FP32; only active entries are written.  Grouped form only (mode is implied), group_size
+ * in [1, 128].  Errors as sphgrp_hydro_force. */
+int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
+                           const double* h, const float* rho, const float* vel,
+                           int group_size, float* divv, float* curlv, cudaStream_t stream);
+
 /* a9: backward (adjoint) of the density and the hydro accelerations.  The paper has
  * no backward pass; this differentiates the a6 and a8 loops above.  For the positions
  * x and masses m of the last sphgrp_tree_build, and the given h, vel and u, it returns

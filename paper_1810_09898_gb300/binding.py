@@ -30,6 +30,7 @@ EXPORTED = [
     "sphgrp_group_supersets",
     "sphgrp_density",
     "sphgrp_hydro_force",
+    "sphgrp_velocity_derivs",
     "sphgrp_backward",
     "sphgrp_get_stats",
     "sphgrp_kernel_launches",
@@ -128,6 +129,7 @@ def load_library():
                                          ctypes.POINTER(I64), ctypes.POINTER(I64), P]
     L.sphgrp_density.argtypes = [P, I64, P, P, I32, I32, I32, P, P, P, P, P, P]
     L.sphgrp_hydro_force.argtypes = [P, I64, P, P, P, P, P, P, I32, I32, P, P, P, P]
+    L.sphgrp_velocity_derivs.argtypes = [P, I64, P, P, P, P, I32, P, P, P]
     L.sphgrp_backward.argtypes = [P, P, P, P, P, P, I32, P, P, P, P]
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     L.sphgrp_kernel_launches.argtypes = [ctypes.POINTER(I64)]
@@ -245,6 +247,11 @@ class Context:
         _check(self._L.sphgrp_hydro_force(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
                                           _ptr(fgrad), _ptr(vel), _ptr(u), mode, group_size, _ptr(acc),
                                           _ptr(dudt), _ptr(nngb), _stream()))
+
+    def velocity_derivs(self, active, h, rho, vel, group_size, divv, curlv):
+        """Velocity divergence (n,) and curl (n, 3) over the density sets (grouped walk)."""
+        _check(self._L.sphgrp_velocity_derivs(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
+                                              _ptr(vel), int(group_size), _ptr(divv), _ptr(curlv), _stream()))
 
     # -- a9
     def backward(self, h, vel, u, g_acc, g_rho, group_size, g_pos=None, g_vel=None, g_m=None):

@@ -114,6 +114,25 @@ __global__ void k_hydro_prep(int64_t n, const int32_t* __restrict__ perm, const 
     hyd1[r] = make_float4(A, rh, 1.0f / hf, s);
 }
 
+// velocity-derivative inputs in key order: hyd0 = {v, 0}, hyd1 = {0, rho, 1/h, 8/(pi h^4)}
+__global__ void k_velocity_prep(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
+                                const float* __restrict__ rho, const float* __restrict__ vel,
+                                double* __restrict__ h64, uint4* __restrict__ pfix, float4* __restrict__ hyd0,
+                                float4* __restrict__ hyd1, unsigned* err) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int i = perm[r];
+    double hv = h[i];
+    if (!(hv > 0.0 && hv < 0.5)) atomicOr(err, kErrH);
+    h64[r] = hv;
+    float hf = (float)hv;
+    pfix[r].w = __float_as_uint(hf);
+    hyd0[r] = make_float4(vel[3 * (int64_t)i], vel[3 * (int64_t)i + 1], vel[3 * (int64_t)i + 2], 0.0f);
+    const double kPi = 3.14159265358979323846;
+    float s = (float)(8.0 / (kPi * hv * hv * hv * hv));
+    hyd1[r] = make_float4(0.0f, rho[i], 1.0f / hf, s);
+}
+
 __global__ void k_counts_by_caller(int64_t n_act, const int32_t* __restrict__ active,
                                    const int64_t* __restrict__ cnt, int64_t* __restrict__ out) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -790,6 +809,37 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, co
     a.o_nh = nngb;
     timer_begin(c, s);
     rc = launch_search(a, SPHGRP_HYDRO, kAcc, grouped, c->sm_count, s);
+    timer_end(c, s, a.nu);
+    if (rc) return rc;
+    c->last.walks = a.ngroups;
+    c->last.members = nu;
+    return finish(c, s, 0);
+}
+
+int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                           const float* rho, const float* vel, int group_size, float* divv, float* curlv,
+                           cudaStream_t s) {
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    int rc = check_common(c, n_act, active, SPHGRP_GROUPED, group_size);
+    if (rc) return rc;
+    if (!h || !rho || !vel || !divv || !curlv) return set_error(SPHGRP_EINVAL, "null array");
+    reset_flags(c, s);
+    k_velocity_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, rho, vel, c->h64, c->pfix, c->hyd0,
+                                                         c->hyd1, c->err);
+    note_launch();
+    if ((rc = refresh_hmax(c, s))) return rc;
+    int nu = 0;
+    if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
+    SearchArgs a = base_args(c);
+    a.U = c->act;
+    a.nu = nu;
+    a.g = group_size;
+    a.ngroups = (nu + group_size - 1) / group_size;
+    if ((rc = make_groups(c, &a, c->act, nu, group_size, s))) return rc;
+    a.o_divv = divv;
+    a.o_curl = curlv;
+    timer_begin(c, s);
+    rc = launch_search(a, kKindVelocity, kAcc, true, c->sm_count, s);
     timer_end(c, s, a.nu);
     if (rc) return rc;
     c->last.walks = a.ngroups;

@@ -31,6 +31,7 @@ constexpr int kSpillCap = kStackSpillPerWarp;  // overflow entries per warp (glo
 constexpr int kTileD = 128;   // density tile (candidates)
 constexpr int kTileH = 128;   // hydro tile
 constexpr int kTileA = 128;   // adjoint tiles
+constexpr int kTileV = 128;   // velocity-derivative tile
 
 struct LocalCounters {
     unsigned long long nodes = 0, cands = 0, tests = 0, pairs = 0, retests = 0;
@@ -228,6 +229,19 @@ struct DAMember : SymMember {
     float xb[3], mb;
 };
 
+// velocity-derivative member (density criterion): sums of -m v_ij . grad W (divergence)
+// and m v_ij x grad W (curl), v_ij = v_i - v_j, grad W at h_i
+struct VMember : MemberPos {
+    float hinv;
+    float h2lo, h2hi;
+    float thr_dot;
+    float sk;               // 8 / (pi h^4): dW/dr = sk * dw/dq
+    float vx, vy, vz;
+    float rrho;             // 1 / rho_i
+    float sd, cd, sx, cx_, sy, cy_, sz, cz_;   // compensated totals
+    float pd, px_, py_, pz_;                   // plain partial sums of the current tile
+};
+
 __device__ __forceinline__ void member_init(DMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
                                             uint32_t cz) {
     M.s0 = M.c0 = M.s1 = M.c1 = M.s2 = M.c2 = 0.0f;
@@ -314,7 +328,42 @@ __device__ __forceinline__ void member_init(DAMember& M, const SearchArgs& a, in
     M.m = a.poff[rank].w;
 }
 
+__device__ __forceinline__ void member_init(VMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    M.sd = M.cd = M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = 0.0f;
+    M.pd = M.px_ = M.py_ = M.pz_ = 0.0f;
+    M.vx = M.vy = M.vz = 0.0f;
+    M.sk = 0.0f;
+    M.rrho = 0.0f;
+    double h = rank >= 0 ? a.h64[rank] : 1.0;
+    float hf = (float)h;
+    if (!pos_init(M, a, rank, cx, cy, cz, hf)) {
+        M.hinv = 0.0f;
+        M.h2lo = M.h2hi = -1.0f;
+        M.thr_dot = -3.0e38f;
+        return;
+    }
+    M.hinv = 1.0f / hf;
+    float h2 = (float)(h * h);
+    float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
+    float bk = 8.0f * kBandRel * m2;
+    M.h2hi = fmaf(h2, 1.0f + 3.0f * kBandRel, bk);
+    M.h2lo = fmaf(h2, 1.0f - 3.0f * kBandRel, -bk);
+    M.thr_dot = M.h2hi - m2;
+    const float4 H0 = a.hyd0[rank];
+    const float4 H1 = a.hyd1[rank];
+    M.vx = H0.x; M.vy = H0.y; M.vz = H0.z;
+    M.rrho = 1.0f / H1.y;
+    M.sk = H1.w;
+}
+
 // walk radius ingredients: density R_s = max(|m| + h); symmetric R_g = max |m|, hmax_g
+__device__ __forceinline__ void radius_terms(const VMember& M, float& rl, float& hl) {
+    if (M.rank < 0) return;
+    float mr = sqrt(M.mx * M.mx + M.my * M.my + M.mz * M.mz);
+    rl = fmaxf(rl, mr + 1.0f / M.hinv);
+}
+
 __device__ __forceinline__ void radius_terms(const DMember& M, float& rl, float& hl) {
     if (M.rank < 0) return;
     float mr = sqrtf(M.mx * M.mx + M.my * M.my + M.mz * M.mz);
@@ -371,6 +420,14 @@ struct DAdjTile {
     uint32_t masks[kTileA];
 };
 
+struct VelTile {
+    float4 p[kTileV];   // raw pfix -> {px, py, pz, |p|^2}
+    float4 o[kTileV];   // raw poff {ox, oy, oz, m}
+    float4 v[kTileV];   // raw hyd0 {vx, vy, vz, -}
+    int r[kTileV];
+    uint32_t masks[kTileV];
+};
+
 // kind policies
 struct KDens {
     static constexpr int min_blocks = 8;   // resident blocks per SM (register budget; 0: compiler's choice)
@@ -409,6 +466,16 @@ struct KDAdj {
     using Tile = DAdjTile;
 };
 
+struct KVel {
+    static constexpr int min_blocks = 0;   // resident blocks per SM (register budget; 0: compiler's choice)
+    static constexpr int id = 4;
+    static constexpr bool sym = false;
+    static constexpr int cap = kTileV;
+    static constexpr uint32_t bytes = 48u;
+    using Member = VMember;
+    using Tile = VelTile;
+};
+
 // bulk copies of one run of candidates into the tile
 __device__ __forceinline__ void stage_run(DensTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
                                           unsigned long long* bar) {
@@ -429,6 +496,12 @@ __device__ __forceinline__ void stage_run(HAdjTile& T, const SearchArgs& a, int 
     bulk_to_smem(&T.v[dst], a.hyd0 + src, b, bar);
     bulk_to_smem(&T.h[dst], a.hyd1 + src, b, bar);
     bulk_to_smem(&T.w[dst], a.wadj + src, b, bar);
+}
+__device__ __forceinline__ void stage_run(VelTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
+                                          unsigned long long* bar) {
+    bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
+    bulk_to_smem(&T.o[dst], a.poff + src, b, bar);
+    bulk_to_smem(&T.v[dst], a.hyd0 + src, b, bar);
 }
 __device__ __forceinline__ void stage_run(DAdjTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
                                           unsigned long long* bar) {
@@ -456,6 +529,14 @@ __device__ __forceinline__ void flush(HMember& M) {
     kahan_add(M.sz, M.cz_, M.pz_);
     kahan_add(M.su, M.cu, M.pu);
     M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
+}
+
+__device__ __forceinline__ void flush(VMember& M) {
+    kahan_add(M.sd, M.cd, M.pd);
+    kahan_add(M.sx, M.cx_, M.px_);
+    kahan_add(M.sy, M.cy_, M.py_);
+    kahan_add(M.sz, M.cz_, M.pz_);
+    M.pd = M.px_ = M.py_ = M.pz_ = 0.0f;
 }
 
 __device__ __forceinline__ void flush(HAMember&) {}
@@ -511,6 +592,38 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
         if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
         else atomicOr(a.err, kErrCap);
     }
+}
+
+// velocity-derivative pair (density criterion): p = relative coordinates, mj the mass,
+// vj = {vx, vy, vz, -}
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void vel_pair(VMember& M, const SearchArgs& a, float4 p, float mj, float4 vj, int crank,
+                                         LocalCounters& lc) {
+    float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
+    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    bool in = r2 < M.h2lo;
+    if (!in) {
+        if (!(r2 < M.h2hi)) return;
+        double e = exact_r2(a.xd, a.yd, a.zd, M.rank, crank);
+        double h = a.h64[M.rank];
+        in = e < __dmul_rn(h, h);
+        lc.retests++;
+    }
+    if (!in) return;
+    M.n++;
+    if (MODE != kAcc) return;
+    if (M.precise) precise_diff(M, a, crank, dx, dy, dz, r2);
+    if (r2 == 0.0f) return;   // the particle itself (and coincident ones): grad W = 0
+    const float rinv = rsqrtf(r2);
+    float w, dw;
+    m4_shape(r2 * rinv * M.hinv, w, dw);
+    const float c = -M.sk * dw * rinv;   // grad_i W = W' (x_i - x_j) / r, x_i - x_j = -d
+    const float gx = c * dx, gy = c * dy, gz = c * dz;
+    const float vx = M.vx - vj.x, vy = M.vy - vj.y, vz = M.vz - vj.z;
+    M.pd = fmaf(-mj, fmaf(vx, gx, fmaf(vy, gy, vz * gz)), M.pd);
+    M.px_ = fmaf(mj, fmaf(vy, gz, -vz * gy), M.px_);
+    M.py_ = fmaf(mj, fmaf(vz, gx, -vx * gz), M.py_);
+    M.pz_ = fmaf(mj, fmaf(vx, gy, -vy * gx), M.pz_);
 }
 
 // decision of the symmetric criterion |r| < max(h_i, h_j) with the FP64 band re-test
@@ -696,6 +809,11 @@ __device__ __forceinline__ void tile_pair(DMember& M, const SearchArgs& a, const
     density_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.r[j], lc);
 }
 template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(VMember& M, const SearchArgs& a, const VelTile& T, int j,
+                                          LocalCounters& lc) {
+    vel_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.v[j], T.r[j], lc);
+}
+template <int MODE, bool WRAP>
 __device__ __forceinline__ void tile_pair(HMember& M, const SearchArgs& a, const HydroTile& T, int j,
                                           LocalCounters& lc) {
     hydro_pair<MODE, WRAP>(M, a, T.p[j], T.o[j], T.v[j], T.h[j], T.r[j], lc);
@@ -718,6 +836,8 @@ __device__ __forceinline__ float thr_dot(const SymMember& M, float hj2) {
     return fmaf(fmaxf(M.h2, hj2), 1.0f + 3.0f * kBandRel, M.bk_dot);
 }
 __device__ __forceinline__ float thr_diff(const DMember& M, float) { return M.h2hi; }
+__device__ __forceinline__ float thr_dot(const VMember& M, float) { return M.thr_dot; }
+__device__ __forceinline__ float thr_diff(const VMember& M, float) { return M.h2hi; }
 __device__ __forceinline__ float thr_diff(const SymMember& M, float hj2) {
     return fmaf(fmaxf(M.h2, hj2), 1.0f + 3.0f * kBandRel, M.bk);
 }
@@ -732,6 +852,11 @@ __device__ __forceinline__ void slice_add(DMember& M, int o) {
 __device__ __forceinline__ void slice_add(HMember& M, int o) {
     M.sx = xsum(M.sx, o); M.cx_ = xsum(M.cx_, o); M.sy = xsum(M.sy, o); M.cy_ = xsum(M.cy_, o);
     M.sz = xsum(M.sz, o); M.cz_ = xsum(M.cz_, o); M.su = xsum(M.su, o); M.cu = xsum(M.cu, o);
+    M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
+}
+__device__ __forceinline__ void slice_add(VMember& M, int o) {
+    M.sd = xsum(M.sd, o); M.cd = xsum(M.cd, o); M.sx = xsum(M.sx, o); M.cx_ = xsum(M.cx_, o);
+    M.sy = xsum(M.sy, o); M.cy_ = xsum(M.cy_, o); M.sz = xsum(M.sz, o); M.cz_ = xsum(M.cz_, o);
     M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
 }
 __device__ __forceinline__ void slice_add(HAMember& M, int o) {
@@ -776,6 +901,15 @@ __device__ __forceinline__ void write_result(const HAMember& H, const SearchArgs
     a.o_adj0[H.rank] = make_float4(H.xb[0], H.xb[1], H.xb[2], H.mb);
     a.o_adj1[H.rank] = make_float4(H.vb[0], H.vb[1], H.vb[2], 0.0f);
     a.o_adj2[H.rank] = make_float4(H.hb, H.rb, H.Ab, (float)H.n);
+}
+template <int MODE>
+__device__ __forceinline__ void write_result(const VMember& V, const SearchArgs& a) {
+    if (MODE != kAcc) return;
+    const int orig = a.perm[V.rank];
+    a.o_divv[orig] = V.rrho * (V.sd - V.cd);
+    a.o_curl[3 * (int64_t)orig] = V.rrho * (V.sx - V.cx_);
+    a.o_curl[3 * (int64_t)orig + 1] = V.rrho * (V.sy - V.cy_);
+    a.o_curl[3 * (int64_t)orig + 2] = V.rrho * (V.sz - V.cz_);
 }
 template <int MODE>
 __device__ __forceinline__ void write_result(const DAMember& D, const SearchArgs& a) {
@@ -1786,6 +1920,9 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
             case 3:
                 if (mode != kAcc) return set_error(SPHGRP_EINVAL, "adjoint kernels accumulate only");
                 return launch_group_m<KDAdj, kAcc>(a, sm_count, s);
+            case kKindVelocity:
+                if (mode != kAcc) return set_error(SPHGRP_EINVAL, "the velocity derivatives accumulate only");
+                return launch_group_m<KVel, kAcc>(a, sm_count, s);
         }
         return set_error(SPHGRP_EINVAL, "bad kind");
     }

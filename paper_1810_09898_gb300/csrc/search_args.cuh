@@ -9,7 +9,7 @@ namespace sphgrp {
 enum Mode { kAcc = 0, kCount = 1, kFill = 2, kSupCount = 3, kSupFill = 4 };
 
 // pair loops of the search kernels: SPHGRP_DENSITY (0), SPHGRP_HYDRO (1) and the adjoints
-enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3 };
+enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3, kKindVelocity = 4 };
 
 // smoothing-length update of the density passes (per unconverged particle, FP64)
 struct UpdateArgs {
@@ -73,6 +73,9 @@ struct SearchArgs {
     float4* o_adj1;       // hydro adjoint {vb, -}
     float4* o_adj2;       // hydro adjoint {hb, rhob, Ab, n}
     float4* o_adj3;       // density adjoint {xb, mb}
+    // velocity derivatives (original order)
+    float* o_divv;
+    float* o_curl;        // n x 3
     // hydro results (original order)
     float* o_acc;
     float* o_dudt;
