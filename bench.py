@@ -430,6 +430,27 @@ def per_pass(P, mode: int, g: int, reps: int = 5) -> dict:
     return {"density_ms": d, "hydro_ms": h, "value": P.n_act / ((d + h) / 1e3), "unit": UNIT}
 
 
+def velocity_pass(P, g: int, reps: int = 5) -> dict:
+    """One grouped velocity divergence + curl pass over the active particles at converged
+    h (density sets), CUDA events per pass."""
+    torch = P.torch
+    n = P.n
+    divv = torch.zeros(n, dtype=torch.float32, device=P.dev)
+    curl = torch.zeros((n, 3), dtype=torch.float32, device=P.dev)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    t = []
+    for rep in range(reps + 1):
+        ev[0].record(stream)
+        P.ctx.velocity_derivs(P.act, P.h, P.rho, P.vel, g, divv, curl)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            t.append(ev[0].elapsed_time(ev[1]))
+    ms = float(np.median(t))
+    return {"ms": ms, "value": P.n_act / (ms / 1e3), "unit": UNIT, "group_size": g}
+
+
 def active_leg(P, frac: float, g: int, steps: int, warmup: int, dist, rank: int) -> dict:
     """The same step with a fraction of the particles active in key-order runs (mean
     length 32); inactive particles keep their converged h, rho and f."""
@@ -696,6 +717,7 @@ def run_ours(a):
         passes["individual"] = guarded(per_pass, P, sg.INDIVIDUAL, 1)
         if "value" in passes["grouped"] and "value" in passes["individual"]:
             passes["speedup_grouped"] = passes["grouped"]["value"] / passes["individual"]["value"]
+    vel_derivs = guarded(velocity_pass, P, g)
     low_active = None
     if a.active >= 1.0 and not a.no_individual:
         low_active = guarded(active_leg, P, 0.1, g, steps, warmup, dist, rank)
@@ -750,6 +772,7 @@ def run_ours(a):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "per_pass_converged_h": passes,
+        "velocity_derivs": vel_derivs,
         "active_10pct": low_active,
         "backward": back,
         "batch": batch,
