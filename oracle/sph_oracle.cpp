@@ -22,6 +22,11 @@
 //  * SPH hydro accelerations and du/dt (grad-h pressure term plus Monaghan
 //    artificial viscosity); the paper only cites its hydro scheme, the reading is the
 //    standard energy-conserving form.
+//  * velocity divergence and curl over the density sets (no formula in the paper; the
+//    standard SPH estimates from the velocity gradient at h_i).
+//  * the backward (adjoint) of the density and the accelerations with respect to
+//    positions, velocities and masses, h tied to them by the neighbour-number relation
+//    (the paper has no backward pass), and a forward-mode dual-number check of it.
 //
 // A pointer octree is used only to prune the candidate set; every candidate is still
 // tested with the exact definition above, and the pruned sets are pinned against the
