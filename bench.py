@@ -255,6 +255,7 @@ class Problem:
         hi[act] = hc[act] * np.exp(a.h_scatter * rng.standard_normal(len(act)))
         self.h_init = torch.from_numpy(hi).to(dev)
         self.host["h_init"] = torch.from_numpy(hi).pin_memory()
+        self.side = torch.cuda.Stream(device=dev)
         self.out_host = {
             "acc": torch.empty((n, 3), dtype=torch.float32).pin_memory(),
             "dudt": torch.empty(n, dtype=torch.float32).pin_memory(),
@@ -275,21 +276,42 @@ class Problem:
             collect.append({"density": sd, "hydro": c.stats()})
 
     def step_e2e(self, g: int):
-        """The same step from host buffers: inputs copied in, results copied out."""
-        H = self.host
+        """The same step from host buffers: inputs copied in, results copied out.  Only
+        the positions go up before the keys; the other inputs follow on a second stream in
+        the order they are needed (m for the tree, the active list and h for the density,
+        v and u for the hydro loop) while keys, sort, tree and density run, and rho and h
+        come back on it while hydro runs; the step ends when both streams are done."""
+        torch, c = self.torch, self.ctx
+        H, O = self.host, self.out_host
+        main = torch.cuda.current_stream()
+        side = self.side
         self.pos.copy_(H["pos"], non_blocking=True)
-        self.m.copy_(H["m"], non_blocking=True)
-        self.vel.copy_(H["vel"], non_blocking=True)
-        self.u.copy_(H["u"], non_blocking=True)
-        self.act.copy_(H["act"], non_blocking=True)
-        self.h_init.copy_(H["h_init"], non_blocking=True)
-        self.step(self.sg.GROUPED, g)
-        O = self.out_host
+        side.wait_stream(main)   # the other inputs start after the positions
+        with torch.cuda.stream(side):
+            self.m.copy_(H["m"], non_blocking=True)
+            tree_in = side.record_event()
+            self.act.copy_(H["act"], non_blocking=True)
+            self.h.copy_(H["h_init"], non_blocking=True)
+            density_in = side.record_event()
+            self.vel.copy_(H["vel"], non_blocking=True)
+            self.u.copy_(H["u"], non_blocking=True)
+            hydro_in = side.record_event()
+        c.sfc_keys_sort(self.pos, None, self.perm)
+        main.wait_event(tree_in)
+        c.tree_build(self.pos, self.m)
+        main.wait_event(density_in)
+        c.density(self.act, self.h, 1, self.sg.GROUPED, g, self.rho, self.drho, self.f, self.nn)
+        side.wait_event(main.record_event())
+        with torch.cuda.stream(side):
+            O["rho"].copy_(self.rho, non_blocking=True)
+            O["h"].copy_(self.h, non_blocking=True)
+        main.wait_event(hydro_in)
+        c.hydro_force(self.act, self.h, self.rho, self.f, self.vel, self.u, self.sg.GROUPED, g, self.acc,
+                      self.dudt, self.nnh)
         O["acc"].copy_(self.acc, non_blocking=True)
         O["dudt"].copy_(self.dudt, non_blocking=True)
-        O["rho"].copy_(self.rho, non_blocking=True)
-        O["h"].copy_(self.h, non_blocking=True)
-        self.torch.cuda.current_stream().synchronize()
+        main.synchronize()
+        side.synchronize()
 
     def io_bytes(self):
         n = self.n
