@@ -41,6 +41,15 @@ UNIT = "active particles/s"
 B_CAND = {"density": 32, "hydro": 64}
 B_MEMBER = {"density": 32 + 16, "hydro": 64 + 16}
 B_NODE = 48
+# the backward's three pair loops and the velocity-derivative loop: (bytes per staged
+# candidate, bytes per member)
+B_BWD = {"density_sums": (32, 48), "hydro_adjoint": (80, 136), "density_adjoint": (48, 72)}
+B_VEL = (48, 92)
+
+
+def launch_gbs(e: dict, b_cand: int, b_member: int) -> float:
+    """Algorithmic GB/s of one logged search launch (candidates, members, nodes tested)."""
+    return (e["candidates"] * b_cand + e["members"] * b_member + e["nodes"] * B_NODE) / (e["ms"] / 1e3) / 1e9
 
 
 def parse():
@@ -469,8 +478,12 @@ def velocity_pass(P, g: int, reps: int = 5) -> dict:
         torch.cuda.synchronize()
         if rep:
             t.append(ev[0].elapsed_time(ev[1]))
+        if rep == reps:
+            gbs = launch_gbs(P.ctx.launch_log()[0], *B_VEL)
     ms = float(np.median(t))
-    return {"ms": ms, "value": P.n_act / (ms / 1e3), "unit": UNIT, "group_size": g}
+    peak = measured_peak_hbm()
+    return {"ms": ms, "value": P.n_act / (ms / 1e3), "unit": UNIT, "group_size": g,
+            "roofline": {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak}}
 
 
 def active_leg(P, frac: float, g: int, steps: int, warmup: int, dist, rank: int) -> dict:
@@ -536,7 +549,8 @@ def backward_leg(a, rank: int, steps: int, warmup: int):
         if e.code != -3:
             raise
     g = a.group
-    bw = {"ms": 0.0, "search_ms": 0.0, "launches": [0.0, 0.0, 0.0]}
+    bw = {"ms": 0.0, "search_ms": 0.0, "launches": [0.0, 0.0, 0.0], "gbs": [0.0, 0.0, 0.0]}
+    names = ("density_sums", "hydro_adjoint", "density_adjoint")
 
     def step(collect):
         ctx.sfc_keys_sort(pos)
@@ -549,6 +563,7 @@ def backward_leg(a, rank: int, steps: int, warmup: int):
             bw["search_ms"] += sum(e["ms"] for e in log)
             for k, e in enumerate(log[:3]):
                 bw["launches"][k] += e["ms"]
+                bw["gbs"][k] += launch_gbs(e, *B_BWD[names[k]])
 
     for _ in range(warmup):
         step(None)
@@ -572,12 +587,14 @@ def backward_leg(a, rank: int, steps: int, warmup: int):
     torch.cuda.synchronize()
     ms_b = e0.elapsed_time(e1) / steps
     ctx.close()
-    names = ("density_sums", "hydro_adjoint", "density_adjoint")
+    peak = measured_peak_hbm()
     return {"workload": f"clustered N={n} (2^{n.bit_length() - 1}), all active, group {g}, "
                         "L = sum w.a + sum s rho, w and s standard normal",
             "value": n / (ms / 1e3), "unit": "particles/s (forward + backward step)", "ms_per_step": ms,
             "backward_value": n / (ms_b / 1e3), "backward_ms": ms_b,
-            "backward_search_ms": {k: v / steps for k, v in zip(names, bw["launches"])}}
+            "backward_search_ms": {k: v / steps for k, v in zip(names, bw["launches"])},
+            "backward_roofline": {k: {"achieved_gbs": v / steps, "peak_gbs": peak, "frac": v / steps / peak}
+                                  for k, v in zip(names, bw["gbs"])}}
 
 
 def batch_leg(a, rank: int, steps: int, warmup: int):
