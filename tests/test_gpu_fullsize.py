@@ -112,3 +112,79 @@ def test_fullsize_step_ten_percent_active(full):
     _check_density(d, out, sample)
     _check_hydro(d, out["h"], rho, f, hyd, sample)
     assert np.all(hyd["acc"][inactive] == 0.0)
+
+
+# ---------------------------------------------------------------- batched boxes at full size
+
+BATCH_FIELDS = ("h", "rho", "drhodh", "fgrad", "nngb", "acc", "dudt")
+
+
+@pytest.fixture(scope="module")
+def boxes(cuda_device):
+    """The batched workload as bench.py times it: 96 boxes (N per box log-uniform in
+    [1e4, 2e6], about 41.5 M particles), a cold all-active step, the active sets and the
+    scattered h, the per-class autotuner, then one eager step and the same step replayed
+    from the captured graph."""
+    import torch
+
+    import paper_1810_09898_gb300 as sg
+
+    b = sphgen.batch(96, 10_000, 2_000_000, config=5)
+    n = int(b["box_off"][-1])
+    dev = torch.device("cuda:0")
+    t = lambda x, dt=None: torch.from_numpy(np.ascontiguousarray(x)).to(dev, dtype=dt)  # noqa: E731
+    f32 = dict(dtype=torch.float32, device=dev)
+    io = {"pos": t(b["pos"]), "m": t(b["m"], torch.float32), "vel": t(b["vel"], torch.float32),
+          "u": t(b["u"], torch.float32), "h": t(b["h0"]), "active": None,
+          "rho": torch.zeros(n, **f32), "drhodh": torch.zeros(n, **f32), "fgrad": torch.ones(n, **f32),
+          "nngb": torch.zeros(n, dtype=torch.int32, device=dev), "acc": torch.zeros((n, 3), **f32),
+          "dudt": torch.zeros(n, **f32)}
+    B = sg.Batch(b["box_off"], b["box_class"])
+    B.run(io)
+    io["active"] = t(b["active"].astype(np.uint8))
+    rng = np.random.default_rng(sphgen.SEED_BASE + 243)
+    hc = io["h"].cpu().numpy()
+    h_init = t(np.where(b["active"], hc * np.exp(0.05 * rng.standard_normal(n)), hc))
+    io["h"].copy_(h_init)
+    B.tune(io)
+    io["h"].copy_(h_init)
+    B.run(io)
+    eager = {k: io[k].cpu().numpy() for k in BATCH_FIELDS}
+    for _ in range(2):   # capture, then replay
+        io["h"].copy_(h_init)
+        B.run(io, graph=True)
+    graph = {k: io[k].cpu().numpy() for k in BATCH_FIELDS}
+    B.close()
+    yield b, eager, graph
+
+
+def test_batch_fullsize_graph_replay_bit_identical(boxes):
+    _, eager, graph = boxes
+    for k in BATCH_FIELDS:
+        assert np.array_equal(eager[k], graph[k]), k
+
+
+def test_batch_fullsize_sampled_boxes(boxes):
+    b, _, out = boxes
+    sizes = np.diff(b["box_off"])
+    cls = b["box_class"]
+    picks = {int(np.argmax(sizes)),
+             int(np.flatnonzero(cls == 0)[np.argmin(sizes[cls == 0])]),
+             int(np.flatnonzero(cls == 1)[np.argmin(sizes[cls == 1])])}
+    rng = np.random.default_rng(sphgen.SEED_BASE + 244)
+    for k in sorted(picks):
+        s = slice(int(b["box_off"][k]), int(b["box_off"][k + 1]))
+        act = np.flatnonzero(b["active"][s])
+        sample = np.sort(rng.choice(act, min(512, len(act)), replace=False)).astype(np.int32)
+        pos, m = b["pos"][s], b["m"][s].astype(np.float32).astype(np.float64)
+        h = out["h"][s]
+        chk = oracle.density(pos, m, h, targets=sample)
+        assert np.array_equal(out["nngb"][s][sample], chk["nngb"]), k
+        assert np.max(np.abs(out["rho"][s][sample] / chk["rho"] - 1.0)) <= RHO_TOL, k
+        neff = 4.0 * np.pi / 3.0 * h[sample] ** 3 * chk["rho"] / m[sample]
+        assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3), k
+        ref = oracle.hydro(pos, b["vel"][s].astype(np.float32).astype(np.float64), m, h,
+                           out["rho"][s].astype(np.float64), out["fgrad"][s].astype(np.float64),
+                           b["u"][s].astype(np.float32).astype(np.float64), targets=sample)
+        assert _rel_l2(out["acc"][s][sample], ref["acc"]) <= ACC_TOL, k
+        assert _rel_l2(out["dudt"][s][sample], ref["dudt"]) <= ACC_TOL, k
