@@ -188,3 +188,35 @@ def test_batch_fullsize_sampled_boxes(boxes):
                            b["u"][s].astype(np.float32).astype(np.float64), targets=sample)
         assert _rel_l2(out["acc"][s][sample], ref["acc"]) <= ACC_TOL, k
         assert _rel_l2(out["dudt"][s][sample], ref["dudt"]) <= ACC_TOL, k
+
+
+# ---------------------------------------------------------------- group-size sweep at full size
+
+def test_group_size_sweep_fullsize(cuda_device):
+    """The group-size sweep's workload at its full size: clustered N = 2^21, 20% active
+    in key-order runs, h scattered by exp(0.05 N(0,1)) and iterated, for every group
+    size of the sweep; sampled actives against the oracle at each g's h, and hydro at
+    g = 16."""
+    n = 1 << 21
+    d = sphgen.make("clustered", n, config=2)
+    m32 = d["m"].astype(np.float32)
+    gpu = Gpu(d["pos"], m32)
+    cold = gpu.density(np.arange(n, dtype=np.int32), np.full(n, d["h0"]), 1, 1, 16)
+    act = active_runs(n, 0.2, 245, gpu.perm.cpu().numpy())
+    rng = np.random.default_rng(sphgen.SEED_BASE + 246)
+    h = cold["h"].copy()
+    h[act] *= np.exp(0.05 * rng.standard_normal(len(act)))
+    sample = np.sort(rng.choice(act, 512, replace=False)).astype(np.int32)
+    dd = {"pos": d["pos"], "m32": m32}
+    for g in (1, 4, 8, 16, 32, 64, 128):
+        out = gpu.density(act, h, 1, 1, g)
+        _check_density(dd, out, sample)
+        if g == 16:
+            is_act = np.zeros(n, dtype=bool)
+            is_act[act] = True
+            rho = np.where(is_act, out["rho"], cold["rho"]).astype(np.float32)
+            f = np.where(is_act, out["f"], cold["f"]).astype(np.float32)
+            dd.update(vel32=d["vel"].astype(np.float32), u32=d["u"].astype(np.float32))
+            hyd = gpu.hydro(act, out["h"], rho, f, dd["vel32"], dd["u32"], 1, g)
+            _check_hydro(dd, out["h"], rho, f, hyd, sample)
+    gpu.ctx.close()
