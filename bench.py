@@ -115,6 +115,28 @@ class CpuSample:
         o.hydro(self.pos, self.vel, self.m, h, dens["rho"], dens["f"], self.u)
         return time.perf_counter() - t0
 
+    def per_pass(self, g: int) -> dict:
+        """One density pass and one hydro pass at converged h, per-particle and grouped
+        (the oracle's Sec. 3.1 form: g consecutive particles along the curve per walk,
+        centred on the group's first particle), with the speedups of grouping."""
+        o = self.oracle
+        h, dens = o.density_iterate(self.pos, self.m, self.h0)
+        args = (self.pos, self.vel, self.m, h, dens["rho"], dens["f"], self.u)
+        t = {}
+        for form, dfn, hfn in (("per_particle", lambda: o.density(self.pos, self.m, h), lambda: o.hydro(*args)),
+                               ("grouped", lambda: o.density_grouped(self.pos, self.m, h, g),
+                                lambda: o.hydro_grouped(*args, g))):
+            t0 = time.perf_counter()
+            dfn()
+            t1 = time.perf_counter()
+            hfn()
+            t[form] = {"density_s": t1 - t0, "hydro_s": time.perf_counter() - t1}
+        i, gr = t["per_particle"], t["grouped"]
+        return {"g": g, **t, "speedup": {"density": i["density_s"] / gr["density_s"],
+                                          "hydro": i["hydro_s"] / gr["hydro_s"],
+                                          "total": (i["density_s"] + i["hydro_s"]) /
+                                                   (gr["density_s"] + gr["hydro_s"])}}
+
     def describe(self, seconds: float, value: float) -> dict:
         return {"value": value, "unit": UNIT, "cores": self.oracle.threads(), "kind": "oracle",
                 "sample": f"clustered N={self.n} of the same recipe, all active: keys, order, density "
@@ -125,7 +147,9 @@ class CpuSample:
 def cpu_sample(n: int, h_scatter: float) -> dict:
     S = CpuSample(n, h_scatter)
     t = S.run()
-    return S.describe(t, n / t)
+    out = S.describe(t, n / t)
+    out["grouped_form"] = guarded(S.per_pass, 8)
+    return out
 
 
 def run_reference(a):

@@ -58,6 +58,9 @@ def lib():
             L.orc_hydro.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, dbl, dbl, dbl,
                                     dbl, i32, P, P, P, P, P]
             L.orc_threads.argtypes = []
+            L.orc_density_grouped.argtypes = [i64, P, P, P, P, P, i64, P, i32, P, P, P, P, P, P]
+            L.orc_hydro_grouped.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, i32, dbl, dbl,
+                                            dbl, dbl, P, P, P, P, P, P]
             L.orc_velocity_derivs.argtypes = [i64, P, P, P, P, P, P, P, i64, P, i32, P, P]
             L.orc_h_exact.argtypes = [i64, P, P, P, P, P, dbl, i32]
             L.orc_loss_grad.argtypes = [i64, P, P, P, P, P, P, P, P, P, dbl, dbl, dbl, dbl, dbl, i32,
@@ -188,6 +191,69 @@ def hydro(pos, vel, m, h, rho, f, u, targets=None, gamma=5.0 / 3.0, alpha=1.0, b
                     _p(u), nt, _p(t), gamma, alpha, beta, eps, int(use_tree), _p(ax), _p(ay),
                     _p(az), _p(dudt), _p(nn))
     return {"acc": np.stack([ax, ay, az], axis=1), "dudt": dudt, "nngb": nn}
+
+
+def curve_order(pos, targets=None):
+    """The targets (all particles by default) in the order of the curve (stable)."""
+    order = stable_order(hilbert_keys(pos))
+    if targets is None:
+        return order.astype(np.int32)
+    keep = np.zeros(len(order), dtype=bool)
+    keep[np.asarray(targets)] = True
+    return order[keep[order]].astype(np.int32)
+
+
+def density_grouped(pos, m, h, g, targets=None):
+    """Grouped density (Sec. 3.1): the targets in curve order, g consecutive per group,
+    one superset walk per group.  Returns the per-target outputs of ``density`` in the
+    order of ``targets`` (ascending indices when None) and the walk statistics."""
+    x, y, z = _xyz(pos)
+    n = len(x)
+    m, h = _f64(m), _f64(h)
+    ordered = curve_order(pos, targets)
+    nt = len(ordered)
+    rho, drhodh, f, neff = (np.empty(nt) for _ in range(4))
+    nngb = np.empty(nt, dtype=np.int32)
+    stats = np.zeros(3, dtype=np.int64)
+    rc = lib().orc_density_grouped(n, _p(x), _p(y), _p(z), _p(m), _p(h), nt, _p(ordered), int(g), _p(rho),
+                                   _p(drhodh), _p(f), _p(neff), _p(nngb), _p(stats))
+    if rc != 0:
+        raise ValueError("group size must be >= 1")
+    back = _back_to_targets(ordered, targets, n)
+    out = {"rho": rho, "drhodh": drhodh, "f": f, "neff": neff, "nngb": nngb}
+    out = {k: v[back] for k, v in out.items()}
+    out.update(walks=int(stats[0]), candidates=int(stats[1]), pair_tests=int(stats[2]))
+    return out
+
+
+def hydro_grouped(pos, vel, m, h, rho, f, u, g, targets=None, gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps=0.01):
+    """Grouped hydro (Sec. 3.1, symmetric criterion); outputs as ``hydro``, in the order of
+    ``targets``, plus the walk statistics."""
+    x, y, z = _xyz(pos)
+    vx, vy, vz = _xyz(vel)
+    n = len(x)
+    m, h, rho, f, u = (_f64(a) for a in (m, h, rho, f, u))
+    ordered = curve_order(pos, targets)
+    nt = len(ordered)
+    ax, ay, az, dudt = (np.empty(nt) for _ in range(4))
+    nn = np.empty(nt, dtype=np.int32)
+    stats = np.zeros(3, dtype=np.int64)
+    rc = lib().orc_hydro_grouped(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), _p(h), _p(rho), _p(f),
+                                 _p(u), nt, _p(ordered), int(g), gamma, alpha, beta, eps, _p(ax), _p(ay), _p(az),
+                                 _p(dudt), _p(nn), _p(stats))
+    if rc != 0:
+        raise ValueError("group size must be >= 1")
+    back = _back_to_targets(ordered, targets, n)
+    return {"acc": np.stack([ax, ay, az], axis=1)[back], "dudt": dudt[back], "nngb": nn[back],
+            "walks": int(stats[0]), "candidates": int(stats[1]), "pair_tests": int(stats[2])}
+
+
+def _back_to_targets(ordered, targets, n):
+    """Positions in ``ordered`` of every entry of ``targets`` (or of 0 .. n-1)."""
+    where = np.full(n, -1, dtype=np.int64)
+    where[ordered] = np.arange(len(ordered))
+    t = np.arange(n) if targets is None else np.asarray(targets)
+    return where[t]
 
 
 def velocity_derivs(pos, vel, m, h, rho, targets=None, use_tree=True):

@@ -313,6 +313,87 @@ struct DensityOut {
     int32_t n;
 };
 
+// Grouped search (Sec. 3.1, Neighbour Recycling): the members of a group share one
+// tree walk around a centre c, the group's first member as in the paper.  Density:
+// every neighbour j of member k has |x_j - c| <= |x_j - x_k| + |x_k - c| < h_k + d_k
+// with d_k = |x_k - c|, so the walk radius R = max_k (d_k + h_k) covers every member's
+// sphere.  Hydro: j is a neighbour of k through max(h_k, h_j), so the walk opens a node
+// when its box is within R_g + max(hmax_g, node hmax), R_g = max_k d_k,
+// hmax_g = max_k h_k.  Every member then applies its own exact test to the superset.
+double periodic_dist(const Particles& P, int64_t a, int64_t b) {
+    double dx, dy, dz;
+    return std::sqrt(dist2(P.x, P.y, P.z, a, b, dx, dy, dz));
+}
+
+void tree_candidates_sym(const Tree& t, const double p[3], double rg, double hmax_g,
+                         std::vector<int32_t>& out) {
+    out.clear();
+    if (t.nodes.empty()) return;
+    std::vector<int32_t> stack;
+    stack.push_back(0);
+    while (!stack.empty()) {
+        const Tree::Node& nd = t.nodes[stack.back()];
+        stack.pop_back();
+        double r = rg + std::max(hmax_g, nd.hmax);
+        double lim = r * r * (1.0 + 1e-9) + 1e-300;
+        if (box_dist2(p, nd.lo, nd.hi) > lim) continue;
+        if (nd.nchild == 0) {
+            for (int32_t k = nd.first; k < nd.first + nd.count; ++k) out.push_back(t.order[k]);
+        } else {
+            for (int c = 0; c < nd.nchild; ++c) stack.push_back(nd.child[c]);
+        }
+    }
+}
+
+// The superset of the group members[0 .. cnt) (kind 0 density, 1 hydro).
+void group_superset(const Tree& t, const Particles& P, const double* h, const int32_t* members, int cnt,
+                    int kind, std::vector<int32_t>& cand) {
+    const int64_t c = members[0];
+    const double p[3] = {P.x[c], P.y[c], P.z[c]};
+    double rs = 0.0, rg = 0.0, hmax_g = 0.0;
+    for (int k = 0; k < cnt; ++k) {
+        const double d = periodic_dist(P, c, members[k]);
+        rs = std::max(rs, d + h[members[k]]);
+        rg = std::max(rg, d);
+        hmax_g = std::max(hmax_g, h[members[k]]);
+    }
+    if (kind == 0) tree_candidates(t, p, rs, false, cand);
+    else tree_candidates_sym(t, p, rg, hmax_g, cand);
+}
+
+// Member i's own neighbours among the candidates (the same test as the per-particle
+// search), ascending.
+void filter_superset(const Particles& P, const double* h, int64_t i, int kind, const std::vector<int32_t>& cand,
+                     std::vector<int32_t>& out) {
+    out.clear();
+    const double hi2 = h[i] * h[i];
+    for (int32_t j : cand) {
+        double dx, dy, dz;
+        const double r2 = dist2(P.x, P.y, P.z, i, j, dx, dy, dz);
+        if (kind == 0) {
+            if (r2 < hi2) out.push_back(j);
+        } else if (j != i && r2 < std::max(hi2, h[j] * h[j])) {
+            out.push_back(j);
+        }
+    }
+    std::sort(out.begin(), out.end());
+}
+
+// rho_i and dRho_i/dh_i over the neighbour list nb (ascending indices), in that order
+DensityOut density_sum(const Particles& P, const double* m, double hi, int64_t i,
+                       const std::vector<int32_t>& nb) {
+    DensityOut o{0.0, 0.0, (int32_t)nb.size()};
+    for (int32_t j : nb) {
+        double dx, dy, dz;
+        double r = std::sqrt(dist2(P.x, P.y, P.z, i, j, dx, dy, dz));
+        double w, dwdr;
+        m4_kernel(r, hi, w, dwdr);
+        o.rho += m[j] * w;
+        o.drhodh += m[j] * (-(3.0 * w + r * dwdr) / hi);
+    }
+    return o;
+}
+
 DensityOut density_at(const Particles& P, const double* m, double hi, const Tree* tree,
                       int64_t i, std::vector<int32_t>& cand, std::vector<int32_t>& nb) {
     nb.clear();
@@ -331,16 +412,58 @@ DensityOut density_at(const Particles& P, const double* m, double hi, const Tree
             if (dist2(P.x, P.y, P.z, i, j, dx, dy, dz) < hi2) nb.push_back((int32_t)j);
         }
     }
-    DensityOut o{0.0, 0.0, (int32_t)nb.size()};
+    return density_sum(P, m, hi, i, nb);
+}
+
+// Inputs of the hydro sums, indexed by particle.
+struct HydroIn {
+    const double *x, *y, *z, *vx, *vy, *vz, *m, *h, *rho, *fgrad, *u;
+    double gamma, alpha, beta, eps;
+};
+
+// a_i and du_i/dt over the hydro neighbour list nb (ascending indices), in that order.
+void hydro_sum(const HydroIn& H, int64_t i, const std::vector<int32_t>& nb, double acc[3], double& du) {
+    const double gamma = H.gamma, alpha = H.alpha, beta = H.beta, eps = H.eps;
+    const double *x = H.x, *y = H.y, *z = H.z, *vx = H.vx, *vy = H.vy, *vz = H.vz;
+    const double *m = H.m, *h = H.h, *rho = H.rho, *fgrad = H.fgrad, *u = H.u;
+    double Pi = (gamma - 1.0) * rho[i] * u[i];
+    double ci = std::sqrt(gamma * Pi / rho[i]);
+    double Ai = fgrad[i] * Pi / (rho[i] * rho[i]);
+    acc[0] = acc[1] = acc[2] = 0.0;
+    du = 0.0;
     for (int32_t j : nb) {
         double dx, dy, dz;
-        double r = std::sqrt(dist2(P.x, P.y, P.z, i, j, dx, dy, dz));
-        double w, dwdr;
-        m4_kernel(r, hi, w, dwdr);
-        o.rho += m[j] * w;
-        o.drhodh += m[j] * (-(3.0 * w + r * dwdr) / hi);
+        double r2 = dist2(x, y, z, i, j, dx, dy, dz);
+        if (r2 == 0.0) continue;
+        double r = std::sqrt(r2);
+        double rij[3] = {-dx, -dy, -dz};
+        double wi, dwi, wj, dwj;
+        m4_kernel(r, h[i], wi, dwi);
+        m4_kernel(r, h[j], wj, dwj);
+        double Pj = (gamma - 1.0) * rho[j] * u[j];
+        double cj = std::sqrt(gamma * Pj / rho[j]);
+        double Aj = fgrad[j] * Pj / (rho[j] * rho[j]);
+        double vij[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
+        double vr = vij[0] * rij[0] + vij[1] * rij[1] + vij[2] * rij[2];
+        double visc = 0.0;
+        if (vr < 0.0) {
+            double hb = 0.5 * (h[i] + h[j]);
+            double mu = hb * vr / (r2 + eps * hb * hb);
+            double cb = 0.5 * (ci + cj);
+            double rb = 0.5 * (rho[i] + rho[j]);
+            visc = (-alpha * cb * mu + beta * mu * mu) / rb;
+        }
+        double gi[3], gj[3], gb[3];
+        for (int a = 0; a < 3; ++a) {
+            gi[a] = dwi * rij[a] / r;
+            gj[a] = dwj * rij[a] / r;
+            gb[a] = 0.5 * (gi[a] + gj[a]);
+        }
+        for (int a = 0; a < 3; ++a) acc[a] -= m[j] * (Ai * gi[a] + Aj * gj[a] + visc * gb[a]);
+        double vgi = vij[0] * gi[0] + vij[1] * gi[1] + vij[2] * gi[2];
+        double vgb = vij[0] * gb[0] + vij[1] * gb[1] + vij[2] * gb[2];
+        du += m[j] * (Ai * vgi + 0.5 * visc * vgb);
     }
-    return o;
 }
 
 double neff_of(double h, double rho, double m) { return 4.0 * kPi / 3.0 * h * h * h * rho / m; }
@@ -506,16 +629,6 @@ int64_t orc_density_iterate(int64_t n, const double* x, const double* y, const d
     return failed.load();
 }
 
-// SPH accelerations and du/dt of the targets.  Per-particle inputs are indexed by
-// particle: positions, velocities, masses m, smoothing lengths h, densities rho,
-// grad-h factors f, specific internal energies u.  P = (gamma - 1) rho u,
-// c = sqrt(gamma P / rho).  For j in the hydro set of i (j != i):
-//   a_i   -= m_j [ f_i P_i/rho_i^2 gW_i + f_j P_j/rho_j^2 gW_j + Pi_ij (gW_i + gW_j)/2 ]
-//   du_i  += m_j [ f_i P_i/rho_i^2 v_ij . gW_i + Pi_ij v_ij . (gW_i + gW_j)/4 ]
-// with gW_k = dW/dr(r, h_k) r_ij / r, r_ij = x_i - x_j, v_ij = v_i - v_j and the
-// Monaghan viscosity Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar for v_ij . r_ij < 0
-// (else 0), mu = hbar v_ij.r_ij / (r^2 + eps hbar^2), bars = pair means.
-// Coincident pairs (r = 0) contribute nothing (the kernel gradient vanishes there).
 // Velocity divergence and curl of the targets over their density sets (the other
 // quantities a Gadget density pass hands to the hydro loop; not in the paper).  With
 // the SPH velocity gradient at h_i,
@@ -557,6 +670,16 @@ int orc_velocity_derivs(int64_t n, const double* x, const double* y, const doubl
     return 0;
 }
 
+// SPH accelerations and du/dt of the targets.  Per-particle inputs are indexed by
+// particle: positions, velocities, masses m, smoothing lengths h, densities rho,
+// grad-h factors f, specific internal energies u.  P = (gamma - 1) rho u,
+// c = sqrt(gamma P / rho).  For j in the hydro set of i (j != i):
+//   a_i   -= m_j [ f_i P_i/rho_i^2 gW_i + f_j P_j/rho_j^2 gW_j + Pi_ij (gW_i + gW_j)/2 ]
+//   du_i  += m_j [ f_i P_i/rho_i^2 v_ij . gW_i + Pi_ij v_ij . (gW_i + gW_j)/4 ]
+// with gW_k = dW/dr(r, h_k) r_ij / r, r_ij = x_i - x_j, v_ij = v_i - v_j and the
+// Monaghan viscosity Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar for v_ij . r_ij < 0
+// (else 0), mu = hbar v_ij.r_ij / (r^2 + eps hbar^2), bars = pair means.
+// Coincident pairs (r = 0) contribute nothing (the kernel gradient vanishes there).
 int orc_hydro(int64_t n, const double* x, const double* y, const double* z,
               const double* vx, const double* vy, const double* vz, const double* m,
               const double* h, const double* rho, const double* fgrad, const double* u,
@@ -564,56 +687,94 @@ int orc_hydro(int64_t n, const double* x, const double* y, const double* z,
               double eps, int use_tree, double* ax, double* ay, double* az, double* dudt,
               int32_t* nngb) {
     Particles P{n, x, y, z};
+    const HydroIn H{x, y, z, vx, vy, vz, m, h, rho, fgrad, u, gamma, alpha, beta, eps};
     Tree tree;
     if (use_tree) build_tree(tree, n, x, y, z, h);
     parallel_for(nt, [&](int64_t t) {
         std::vector<int32_t> cand, nb;
         int64_t i = targets[t];
         neighbours(P, h, use_tree ? &tree : nullptr, i, 1, cand, nb);
-        double Pi = (gamma - 1.0) * rho[i] * u[i];
-        double ci = std::sqrt(gamma * Pi / rho[i]);
-        double Ai = fgrad[i] * Pi / (rho[i] * rho[i]);
-        double acc[3] = {0.0, 0.0, 0.0};
-        double du = 0.0;
-        for (int32_t j : nb) {
-            double dx, dy, dz;
-            double r2 = dist2(x, y, z, i, j, dx, dy, dz);
-            if (r2 == 0.0) continue;
-            double r = std::sqrt(r2);
-            double rij[3] = {-dx, -dy, -dz};
-            double wi, dwi, wj, dwj;
-            m4_kernel(r, h[i], wi, dwi);
-            m4_kernel(r, h[j], wj, dwj);
-            double Pj = (gamma - 1.0) * rho[j] * u[j];
-            double cj = std::sqrt(gamma * Pj / rho[j]);
-            double Aj = fgrad[j] * Pj / (rho[j] * rho[j]);
-            double vij[3] = {vx[i] - vx[j], vy[i] - vy[j], vz[i] - vz[j]};
-            double vr = vij[0] * rij[0] + vij[1] * rij[1] + vij[2] * rij[2];
-            double visc = 0.0;
-            if (vr < 0.0) {
-                double hb = 0.5 * (h[i] + h[j]);
-                double mu = hb * vr / (r2 + eps * hb * hb);
-                double cb = 0.5 * (ci + cj);
-                double rb = 0.5 * (rho[i] + rho[j]);
-                visc = (-alpha * cb * mu + beta * mu * mu) / rb;
-            }
-            double gi[3], gj[3], gb[3];
-            for (int a = 0; a < 3; ++a) {
-                gi[a] = dwi * rij[a] / r;
-                gj[a] = dwj * rij[a] / r;
-                gb[a] = 0.5 * (gi[a] + gj[a]);
-            }
-            for (int a = 0; a < 3; ++a) acc[a] -= m[j] * (Ai * gi[a] + Aj * gj[a] + visc * gb[a]);
-            double vgi = vij[0] * gi[0] + vij[1] * gi[1] + vij[2] * gi[2];
-            double vgb = vij[0] * gb[0] + vij[1] * gb[1] + vij[2] * gb[2];
-            du += m[j] * (Ai * vgi + 0.5 * visc * vgb);
-        }
+        double acc[3];
+        hydro_sum(H, i, nb, acc, dudt[t]);
         ax[t] = acc[0];
         ay[t] = acc[1];
         az[t] = acc[2];
-        dudt[t] = du;
         nngb[t] = (int32_t)nb.size();
     });
+    return 0;
+}
+
+// Grouped density and hydro (Sec. 3.1): the targets, given in the order of the curve,
+// are cut into groups of g consecutive entries; each group walks the tree once for its
+// superset and each member filters it.  Outputs are indexed like the targets and are
+// those of orc_density / orc_hydro bit for bit (same sets, same summation order).
+// stats[0..2] = walks, candidates (sum of superset sizes), member x candidate tests.
+int orc_density_grouped(int64_t n, const double* x, const double* y, const double* z, const double* m,
+                        const double* h, int64_t nt, const int32_t* ordered, int g, double* rho,
+                        double* drhodh, double* fgrad, double* neff, int32_t* nngb, int64_t* stats) {
+    if (g < 1) return -1;
+    Particles P{n, x, y, z};
+    Tree tree;
+    build_tree(tree, n, x, y, z, nullptr);
+    const int64_t ngroups = (nt + g - 1) / g;
+    std::atomic<int64_t> cands{0}, tests{0};
+    parallel_for(ngroups, [&](int64_t G) {
+        const int64_t b = G * g;
+        const int cnt = (int)std::min<int64_t>(g, nt - b);
+        std::vector<int32_t> cand, nb;
+        group_superset(tree, P, h, ordered + b, cnt, 0, cand);
+        cands.fetch_add((int64_t)cand.size());
+        tests.fetch_add((int64_t)cand.size() * cnt);
+        for (int k = 0; k < cnt; ++k) {
+            const int64_t t = b + k, i = ordered[t];
+            filter_superset(P, h, i, 0, cand, nb);
+            const DensityOut o = density_sum(P, m, h[i], i, nb);
+            rho[t] = o.rho;
+            drhodh[t] = o.drhodh;
+            fgrad[t] = fgrad_of(h[i], o.rho, o.drhodh);
+            neff[t] = neff_of(h[i], o.rho, m[i]);
+            nngb[t] = o.n;
+        }
+    });
+    stats[0] = ngroups;
+    stats[1] = cands.load();
+    stats[2] = tests.load();
+    return 0;
+}
+
+int orc_hydro_grouped(int64_t n, const double* x, const double* y, const double* z, const double* vx,
+                      const double* vy, const double* vz, const double* m, const double* h, const double* rho,
+                      const double* fgrad, const double* u, int64_t nt, const int32_t* ordered, int g,
+                      double gamma, double alpha, double beta, double eps, double* ax, double* ay, double* az,
+                      double* dudt, int32_t* nngb, int64_t* stats) {
+    if (g < 1) return -1;
+    Particles P{n, x, y, z};
+    const HydroIn H{x, y, z, vx, vy, vz, m, h, rho, fgrad, u, gamma, alpha, beta, eps};
+    Tree tree;
+    build_tree(tree, n, x, y, z, h);
+    const int64_t ngroups = (nt + g - 1) / g;
+    std::atomic<int64_t> cands{0}, tests{0};
+    parallel_for(ngroups, [&](int64_t G) {
+        const int64_t b = G * g;
+        const int cnt = (int)std::min<int64_t>(g, nt - b);
+        std::vector<int32_t> cand, nb;
+        group_superset(tree, P, h, ordered + b, cnt, 1, cand);
+        cands.fetch_add((int64_t)cand.size());
+        tests.fetch_add((int64_t)cand.size() * cnt);
+        for (int k = 0; k < cnt; ++k) {
+            const int64_t t = b + k, i = ordered[t];
+            filter_superset(P, h, i, 1, cand, nb);
+            double acc[3];
+            hydro_sum(H, i, nb, acc, dudt[t]);
+            ax[t] = acc[0];
+            ay[t] = acc[1];
+            az[t] = acc[2];
+            nngb[t] = (int32_t)nb.size();
+        }
+    });
+    stats[0] = ngroups;
+    stats[1] = cands.load();
+    stats[2] = tests.load();
     return 0;
 }
 
