@@ -841,7 +841,8 @@ def run_ours(a):
         "batch": batch,
     }
     if ms_i is not None:
-        _, di = roofline(col_i, peak)
+        ri, di = roofline(col_i, peak, clocks)
+        line["individual"]["roofline"] = ri
         line["individual"]["search_detail"] = di
     print(json.dumps(line), flush=True)
     if dist:
