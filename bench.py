@@ -393,8 +393,9 @@ def timed(P, fn, steps, warmup, dist):
     return ms, collect, launches
 
 
-def roofline(collect, peak_gbs, clocks=None):
-    """Dominant search kernel: algorithmic bytes per launch / event time per launch."""
+def roofline(collect, peak_gbs, clocks=None, form: str = "grouped"):
+    """Dominant search kernel: algorithmic bytes per launch / event time per launch.
+    form selects the DRAM record of the captured kernels ("grouped" or "individual")."""
     agg = {}
     for rec in collect:
         for k in ("density", "hydro"):
@@ -421,7 +422,7 @@ def roofline(collect, peak_gbs, clocks=None):
                   "pairs_per_member": v["pairs"] / max(1, v["members"]),
                   "members_per_walk": v["members"] / max(1, v["walks"]),
                   "nodes_per_walk": v["nodes"] / max(1, v["walks"])} for k, v in agg.items()}
-    traffic = measured_traffic(dom, A["members"] / max(1, A["launches"]))
+    traffic = measured_traffic(("indiv_" if form == "individual" else "") + dom, A["members"] / max(1, A["launches"]))
     # the FP32 side of the same launches: ~10 flop per member x candidate test (the
     # difference, r^2, the threshold) and ~25 per true pair (kernel and sums), against
     # 152 SMs x 128 lanes x 2 flop x the sampled SM clock
@@ -431,7 +432,8 @@ def roofline(collect, peak_gbs, clocks=None):
     alu = {"achieved_tflops": flops / per_launch_s / 1e12, "peak_tflops": alu_peak,
            "frac": flops / per_launch_s / 1e12 / alu_peak,
            "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock (derived)"}
-    return {"bound": "hbm", "kernel": f"k_group ({dom})", "achieved": achieved, "peak": peak_gbs,
+    kernel = f"k_indiv ({dom})" if form == "individual" else f"k_group ({dom})"
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak_gbs,
             "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
             "bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_s * 1e3, "alu": alu,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}, detail
@@ -841,7 +843,7 @@ def run_ours(a):
         "batch": batch,
     }
     if ms_i is not None:
-        ri, di = roofline(col_i, peak, clocks)
+        ri, di = roofline(col_i, peak, clocks, form="individual")
         line["individual"]["roofline"] = ri
         line["individual"]["search_detail"] = di
     print(json.dumps(line), flush=True)

@@ -60,3 +60,20 @@ def test_traffic_only_for_the_captured_source(tmp_path, monkeypatch):
     src.write_bytes(b"kernel source, changed")
     assert bench.measured_traffic("density", 1000) is None
 
+
+
+def test_individual_form_takes_its_own_traffic_record(tmp_path, monkeypatch):
+    import hashlib
+
+    src = tmp_path / "k.cu"
+    src.write_bytes(b"kernels")
+    (tmp_path / "profiles").mkdir()
+    rec = {"kernel_source": "k.cu", "kernel_source_sha256_16": hashlib.sha256(b"kernels").hexdigest()[:16],
+           "hydro_dram_bytes_per_member": 266.0, "indiv_hydro_dram_bytes_per_member": 240.0}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec_step = {"density": _stats(1.0, 1, 10, 10, 1, 10, 1, 1), "hydro": _stats(5.0, 1, 10, 10, 1, 10, 1, 1)}
+    g, _ = bench.roofline([rec_step], 8000.0)
+    i, _ = bench.roofline([rec_step], 8000.0, form="individual")
+    assert g["kernel"] == "k_group (hydro)" and g["traffic"] == pytest.approx(2660.0)
+    assert i["kernel"] == "k_indiv (hydro)" and i["traffic"] == pytest.approx(2400.0)
