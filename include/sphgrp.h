@@ -126,8 +126,11 @@ typedef struct sphgrp_stats {
 
 typedef struct sphgrp_ctx sphgrp_ctx;
 
-/* Creates a context for up to n_max particles.  p may be NULL (defaults).  Device
- * memory for n_max particles is allocated here; the octree grows on demand. */
+/* Creates a context for up to n_max particles, 1 <= n_max <= 2^30 (ranks and indices
+ * are int32 on the device).  p may be NULL (defaults).  Device memory for n_max
+ * particles is allocated here; the octree grows on demand.  Errors: EINVAL for n_max
+ * outside that range or bad parameters, ENOMEM if an allocation fails (nothing is
+ * left allocated). */
 int sphgrp_ctx_create(sphgrp_ctx** ctx, const sphgrp_params* p, int64_t n_max);
 int sphgrp_ctx_destroy(sphgrp_ctx* ctx);
 const char* sphgrp_last_error(void);
