@@ -50,6 +50,13 @@ BATCH_CLASSES = 8
 _IO_FIELDS = ("pos", "m", "vel", "u", "h", "active", "rho", "drhodh", "fgrad", "nngb", "acc", "dudt",
               "g_acc", "g_rho", "g_pos", "g_vel", "g_m")
 
+# element type and elements per particle of every batch io array
+_IO_LAYOUT = {"pos": ("float64", 3), "m": ("float32", 1), "vel": ("float32", 3), "u": ("float32", 1),
+              "h": ("float64", 1), "active": ("uint8", 1), "rho": ("float32", 1), "drhodh": ("float32", 1),
+              "fgrad": ("float32", 1), "nngb": ("int32", 1), "acc": ("float32", 3), "dudt": ("float32", 1),
+              "g_acc": ("float32", 3), "g_rho": ("float32", 1), "g_pos": ("float32", 3), "g_vel": ("float32", 3),
+              "g_m": ("float32", 1)}
+
 _ERRORS = {
     -1: "SPHGRP_EINVAL",
     -2: "SPHGRP_ENOMEM",
@@ -157,6 +164,31 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_F32, _F64, _I32, _I64, _U8 = "float32", "float64", "int32", "int64", "uint8"
+
+
+def _arg(t, name: str, dtype: str, numel: int, optional: bool = False, cuda: bool = True):
+    """Device pointer of tensor t after checking what the C ABI assumes of it: a dense
+    array of the given element type holding at least numel elements, on the current
+    CUDA device.  A wrong type or a short array would otherwise be read or written out
+    of bounds by the kernels."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    import torch
+
+    if str(t.dtype) != f"torch.{dtype}":
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    if cuda and (not t.is_cuda or t.device.index != torch.cuda.current_device()):
+        raise ValueError(f"{name} must be on the current CUDA device, got {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream():
     import torch
 
@@ -196,6 +228,7 @@ class Context:
         self._h = ctypes.c_void_p()
         _check(self._L.sphgrp_ctx_create(ctypes.byref(self._h), ctypes.byref(self.params), int(n_max)))
         self.n_max = int(n_max)
+        self.n = 0   # particles of the last sfc_keys_sort
 
     def close(self):
         if self._h:
@@ -210,19 +243,26 @@ class Context:
 
     # -- a1 + a2
     def sfc_keys_sort(self, pos, keys_out=None, perm_out=None):
-        _check(self._L.sphgrp_sfc_keys_sort(self._h, pos.shape[0], _ptr(pos), _ptr(keys_out),
-                                            _ptr(perm_out), _stream()))
+        n = pos.shape[0]
+        _check(self._L.sphgrp_sfc_keys_sort(self._h, n, _arg(pos, "pos", _F64, 3 * n),
+                                            _arg(keys_out, "keys_out", _I64, n, True),
+                                            _arg(perm_out, "perm_out", _I32, n, True), _stream()))
+        self.n = n
 
     # -- a3
     def tree_build(self, pos, m):
-        _check(self._L.sphgrp_tree_build(self._h, pos.shape[0], _ptr(pos), _ptr(m), _stream()))
+        n = pos.shape[0]
+        _check(self._L.sphgrp_tree_build(self._h, n, _arg(pos, "pos", _F64, 3 * n), _arg(m, "m", _F32, n),
+                                         _stream()))
 
     # -- a4 + a5 export
     def ngb_search(self, active, h, kind, mode, group_size, offsets, idx=None, cap=0) -> int:
         n_pairs = ctypes.c_int64()
-        _check(self._L.sphgrp_ngb_search(self._h, active.shape[0], _ptr(active), _ptr(h), kind, mode,
-                                         group_size, int(cap), _ptr(offsets), _ptr(idx),
-                                         ctypes.byref(n_pairs), _stream()))
+        na = active.shape[0]
+        _check(self._L.sphgrp_ngb_search(self._h, na, _arg(active, "active", _I32, na), _arg(h, "h", _F64, self.n),
+                                         kind, mode, group_size, int(cap), _arg(offsets, "offsets", _I64, na + 1),
+                                         _arg(idx, "idx", _I32, int(cap), True), ctypes.byref(n_pairs),
+                                         _stream()))
         return int(n_pairs.value)
 
     def group_supersets(self, active, h, kind, group_size, group_offsets, group_first=None, members=None,
@@ -230,33 +270,51 @@ class Context:
         """Returns (n_groups, n_candidates)."""
         ng = ctypes.c_int64()
         n = ctypes.c_int64()
-        _check(self._L.sphgrp_group_supersets(self._h, active.shape[0], _ptr(active), _ptr(h), kind,
-                                              group_size, int(cap), _ptr(group_offsets), _ptr(group_first),
-                                              _ptr(members), _ptr(cand), ctypes.byref(ng), ctypes.byref(n),
-                                              _stream()))
+        na = active.shape[0]
+        _check(self._L.sphgrp_group_supersets(self._h, na, _arg(active, "active", _I32, na),
+                                              _arg(h, "h", _F64, self.n), kind, group_size, int(cap),
+                                              _arg(group_offsets, "group_offsets", _I64, na + 1),
+                                              _arg(group_first, "group_first", _I32, na + 1, True),
+                                              _arg(members, "members", _I32, na, True),
+                                              _arg(cand, "cand", _I32, int(cap), True), ctypes.byref(ng),
+                                              ctypes.byref(n), _stream()))
         return int(ng.value), int(n.value)
 
     # -- a6 + a7
     def density(self, active, h, iterate, mode, group_size, rho, drhodh, fgrad, nngb, iters=None):
-        _check(self._L.sphgrp_density(self._h, active.shape[0], _ptr(active), _ptr(h), int(iterate), mode,
-                                      group_size, _ptr(rho), _ptr(drhodh), _ptr(fgrad), _ptr(nngb),
-                                      _ptr(iters), _stream()))
+        na, n = active.shape[0], self.n
+        _check(self._L.sphgrp_density(self._h, na, _arg(active, "active", _I32, na), _arg(h, "h", _F64, n),
+                                      int(iterate), mode, group_size, _arg(rho, "rho", _F32, n),
+                                      _arg(drhodh, "drhodh", _F32, n), _arg(fgrad, "fgrad", _F32, n),
+                                      _arg(nngb, "nngb", _I32, n), _arg(iters, "iters", _I32, n, True), _stream()))
 
     # -- a8
     def hydro_force(self, active, h, rho, fgrad, vel, u, mode, group_size, acc, dudt, nngb=None):
-        _check(self._L.sphgrp_hydro_force(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
-                                          _ptr(fgrad), _ptr(vel), _ptr(u), mode, group_size, _ptr(acc),
-                                          _ptr(dudt), _ptr(nngb), _stream()))
+        na, n = active.shape[0], self.n
+        _check(self._L.sphgrp_hydro_force(self._h, na, _arg(active, "active", _I32, na), _arg(h, "h", _F64, n),
+                                          _arg(rho, "rho", _F32, n), _arg(fgrad, "fgrad", _F32, n),
+                                          _arg(vel, "vel", _F32, 3 * n), _arg(u, "u", _F32, n), mode, group_size,
+                                          _arg(acc, "acc", _F32, 3 * n), _arg(dudt, "dudt", _F32, n),
+                                          _arg(nngb, "nngb", _I32, n, True), _stream()))
 
     def velocity_derivs(self, active, h, rho, vel, group_size, divv, curlv):
         """Velocity divergence (n,) and curl (n, 3) over the density sets (grouped walk)."""
-        _check(self._L.sphgrp_velocity_derivs(self._h, active.shape[0], _ptr(active), _ptr(h), _ptr(rho),
-                                              _ptr(vel), int(group_size), _ptr(divv), _ptr(curlv), _stream()))
+        na, n = active.shape[0], self.n
+        _check(self._L.sphgrp_velocity_derivs(self._h, na, _arg(active, "active", _I32, na),
+                                              _arg(h, "h", _F64, n), _arg(rho, "rho", _F32, n),
+                                              _arg(vel, "vel", _F32, 3 * n), int(group_size),
+                                              _arg(divv, "divv", _F32, n), _arg(curlv, "curlv", _F32, 3 * n),
+                                              _stream()))
 
     # -- a9
     def backward(self, h, vel, u, g_acc, g_rho, group_size, g_pos=None, g_vel=None, g_m=None):
-        _check(self._L.sphgrp_backward(self._h, _ptr(h), _ptr(vel), _ptr(u), _ptr(g_acc), _ptr(g_rho),
-                                       int(group_size), _ptr(g_pos), _ptr(g_vel), _ptr(g_m), _stream()))
+        n = self.n
+        _check(self._L.sphgrp_backward(self._h, _arg(h, "h", _F64, n), _arg(vel, "vel", _F32, 3 * n),
+                                       _arg(u, "u", _F32, n), _arg(g_acc, "g_acc", _F32, 3 * n),
+                                       _arg(g_rho, "g_rho", _F32, n, True), int(group_size),
+                                       _arg(g_pos, "g_pos", _F32, 3 * n, True),
+                                       _arg(g_vel, "g_vel", _F32, 3 * n, True), _arg(g_m, "g_m", _F32, n, True),
+                                       _stream()))
 
     def launch_log(self) -> list:
         import numpy as np
@@ -313,23 +371,26 @@ class Batch:
             pass
 
     @staticmethod
-    def _io(arrays: dict) -> BatchIO:
+    def _io(arrays: dict, n: int, cuda: bool = True) -> BatchIO:
+        """The io struct of n particles' arrays, each checked for type and length."""
         unknown = set(arrays) - set(_IO_FIELDS)
         if unknown:
             raise KeyError(f"unknown io arrays: {sorted(unknown)}")
         io = BatchIO()
         for f in _IO_FIELDS:
             t = arrays.get(f)
-            setattr(io, f, None if t is None else t.data_ptr())
+            dtype, per = _IO_LAYOUT[f]
+            p = _arg(t, f, dtype, per * n, optional=True, cuda=cuda)
+            setattr(io, f, None if p is None else p.value)
         return io
 
     def run(self, arrays: dict, backward: bool = False, graph: bool = False):
         flags = (BATCH_BACKWARD if backward else 0) | (BATCH_GRAPH if graph else 0)
-        io = self._io(arrays)
+        io = self._io(arrays, self.n)
         _check(self._L.sphgrp_batch_run(self._h, ctypes.byref(io), flags, _stream()))
 
     def tune(self, arrays: dict):
-        io = self._io(arrays)
+        io = self._io(arrays, self.n)
         _check(self._L.sphgrp_batch_tune(self._h, ctypes.byref(io), _stream()))
 
     def get_config(self, cls: int) -> dict:

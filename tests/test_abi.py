@@ -106,7 +106,33 @@ def test_batch_io_rejects_unknown_arrays():
 
     from paper_1810_09898_gb300 import binding
 
-    io = binding.Batch._io({"pos": torch.zeros(3), "acc": torch.zeros(3)})
+    io = binding.Batch._io({"pos": torch.zeros(3, dtype=torch.float64), "acc": torch.zeros(3)}, 1, cuda=False)
     assert io.pos and io.acc and not io.vel
     with pytest.raises(KeyError):
-        binding.Batch._io({"position": torch.zeros(3)})
+        binding.Batch._io({"position": torch.zeros(3)}, 1, cuda=False)
+    with pytest.raises(ValueError, match="holds 3 elements, needs 6"):
+        binding.Batch._io({"acc": torch.zeros(3)}, 2, cuda=False)
+    with pytest.raises(TypeError, match="pos must be float64"):
+        binding.Batch._io({"pos": torch.zeros(3)}, 1, cuda=False)
+
+
+def test_arguments_are_checked_before_the_call():
+    """Type, density, length and device of every array are checked in the binding, so a
+    wrong array never reaches a kernel."""
+    import torch
+
+    from paper_1810_09898_gb300 import binding
+
+    ok = torch.zeros((4, 3), dtype=torch.float32)
+    assert binding._arg(ok, "vel", "float32", 12, cuda=False).value == ok.data_ptr()
+    assert binding._arg(None, "nngb", "int32", 4, optional=True) is None
+    with pytest.raises(ValueError, match="required"):
+        binding._arg(None, "rho", "float32", 4)
+    with pytest.raises(TypeError, match="must be int32"):
+        binding._arg(torch.zeros(4, dtype=torch.int64), "active", "int32", 4, cuda=False)
+    with pytest.raises(ValueError, match="contiguous"):
+        binding._arg(ok.t(), "vel", "float32", 12, cuda=False)
+    with pytest.raises(ValueError, match="needs 13"):
+        binding._arg(ok, "vel", "float32", 13, cuda=False)
+    with pytest.raises(ValueError, match="CUDA device"):
+        binding._arg(ok, "vel", "float32", 12)
