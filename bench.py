@@ -117,7 +117,7 @@ class CpuSample:
 
     def per_pass(self, g: int) -> dict:
         """One density pass and one hydro pass at converged h, per-particle and grouped
-        (the oracle's Sec. 3.1 form: g consecutive particles along the curve per walk,
+        (the oracle's Sec. 2.1 form: g consecutive particles along the curve per walk,
         centred on the group's first particle), with the speedups of grouping."""
         o = self.oracle
         h, dens = o.density_iterate(self.pos, self.m, self.h0)

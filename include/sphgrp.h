@@ -4,12 +4,12 @@
  * The library computes the hot path of "Exploiting the Space Filling Curve Ordering of
  * Particles in the Neighbour Search of Gadget3" (Ragagnin et al., arXiv:1810.09898):
  * Peano-Hilbert ordering of the particles, an octree over that order, the neighbour
- * search in its two forms -- one tree walk per active particle (Sec. 2.1, "standard
- * method", Fig. 1 left) and Neighbour Recycling (Sec. 3 and 3.1, Fig. 1 right: active
+ * search in its two forms -- one tree walk per active particle (Sec. 1.1, "standard
+ * method", Fig. 1 left) and Neighbour Recycling (Sec. 2 and 2.1, Fig. 1 right: active
  * particles consecutive along the curve form a group, the group makes one walk for a
  * common superset of candidates, and each member filters the superset down to its own
  * neighbours) -- and the SPH density (with the smoothing-length iteration to a fixed
- * effective neighbour number, Sec. 3.2) and hydro-force loops that consume it.
+ * effective neighbour number, Sec. 2.2) and hydro-force loops that consume it.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -53,12 +53,12 @@ enum {
 
 /* Neighbour-search forms. */
 enum {
-    SPHGRP_INDIVIDUAL = 0, /* one walk per active particle with radius h_i (Sec. 2.1) */
+    SPHGRP_INDIVIDUAL = 0, /* one walk per active particle with radius h_i (Sec. 1.1) */
     SPHGRP_GROUPED = 1     /* Neighbour Recycling: one walk per group of group_size
-                              consecutive active particles in key order (Sec. 3.1) */
+                              consecutive active particles in key order (Sec. 2.1) */
 };
 
-/* Neighbour definitions (Sec. 2.1, last paragraph). */
+/* Neighbour definitions (Sec. 1.1, last paragraph). */
 enum {
     SPHGRP_DENSITY = 0, /* j is a neighbour of i iff |r_ij| < h_i (i itself included) */
     SPHGRP_HYDRO = 1    /* j != i is a neighbour of i iff |r_ij| < max(h_i, h_j) */
@@ -74,7 +74,7 @@ typedef struct sphgrp_params {
     double beta;      /* Monaghan viscosity beta, e.g. 2 */
     double eps;       /* viscosity softening (mu denominator r^2 + eps hbar^2), e.g. 0.01 */
     int group_centre; /* centre of a group's search sphere: SPHGRP_CENTRE_FIRST (the group's
-                         first particle, Sec. 3.1) or SPHGRP_CENTRE_BOX (the centre of the
+                         first particle, Sec. 2.1) or SPHGRP_CENTRE_BOX (the centre of the
                          members' bounding box; same superset guarantee, smaller radius) */
     double group_split; /* a group is cut in halves (recursively) while its search sphere
                            (sqrt(3)/2 * width of the members' box + smallest h)^3 exceeds
@@ -88,14 +88,14 @@ typedef struct sphgrp_params {
                            members converge).  The individual form always iterates in passes. */
     int group_mode;     /* how the grouped form cuts the active list (in key order) into groups:
                            SPHGRP_GROUP_COUNT: chunks of group_size, split as group_split says;
-                           SPHGRP_GROUP_RADIUS (Sec. 3.1, the paper's rule): a group starts at an
+                           SPHGRP_GROUP_RADIUS (Sec. 2.1, the paper's rule): a group starts at an
                            active particle and takes the following ones while they lie within
                            R = group_f * h of its first particle, at most group_size of them
                            (the scan restarts at the start of every run of 1024 actives);
                            SPHGRP_GROUP_TREE: see group_level */
     double group_f;     /* R / h of the radius mode, e.g. 0.5 */
     int group_level;    /* depth of the tree mode (SPHGRP_GROUP_TREE, the octree grouping of
-                           Sec. 3): a group is the active particles under one node of this
+                           Sec. 2): a group is the active particles under one node of this
                            depth (the actives sharing the key's first 3 * group_level bits),
                            cut into pieces of at most group_size; 1 .. 21, e.g. 7 */
     int stack_shared;   /* walk-stack entries per warp kept in shared memory (32 .. 256); deeper
@@ -135,7 +135,7 @@ int sphgrp_ctx_create(sphgrp_ctx** ctx, const sphgrp_params* p, int64_t n_max);
 int sphgrp_ctx_destroy(sphgrp_ctx* ctx);
 const char* sphgrp_last_error(void);
 
-/* a1 + a2 (Sec. 2.2: particles ordered along the Hilbert curve).
+/* a1 + a2 (Sec. 1.2: particles ordered along the Hilbert curve).
  * keys: 63-bit Peano-Hilbert key of every particle -- coordinates mapped to a 2^21
  * grid per axis, i = floor(x * 2^21), and the cell's Hilbert index by Skilling's
  * construction (axis order x, y, z, most significant level first) -- sorted
@@ -149,7 +149,7 @@ const char* sphgrp_last_error(void);
 int sphgrp_sfc_keys_sort(sphgrp_ctx* ctx, int64_t n, const double* pos, uint64_t* keys_out,
                          int32_t* perm_out, cudaStream_t stream);
 
-/* a3 (Sec. 2.2: octree over the curve-ordered particles).  Gathers pos and m into key
+/* a3 (Sec. 1.2: octree over the curve-ordered particles).  Gathers pos and m into key
  * order and builds the linear octree: a node with more than leaf_size particles is
  * split into its non-empty octants (the next 3 key bits), down to the 2^21 grid.
  * Each node keeps its tight bounding box, its particle range and the largest h of
@@ -159,7 +159,7 @@ int sphgrp_sfc_keys_sort(sphgrp_ctx* ctx, int64_t n, const double* pos, uint64_t
 int sphgrp_tree_build(sphgrp_ctx* ctx, int64_t n, const double* pos, const float* m,
                       cudaStream_t stream);
 
-/* a4 + a5 (Sec. 2.1 and 3.1): neighbour sets of the active particles, exported as
+/* a4 + a5 (Sec. 1.1 and 2.1): neighbour sets of the active particles, exported as
  * CSR for inspection.  The hot path never materialises pair lists; this call exists
  * so that sets can be compared.
  * active:  device, n_act distinct original indices (any order).
@@ -175,7 +175,7 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
                       int kind, int mode, int group_size, int64_t cap, int64_t* offsets,
                       int32_t* idx, int64_t* n_pairs, cudaStream_t stream);
 
-/* The candidate superset of every group of the grouped form (Sec. 3.1), for
+/* The candidate superset of every group of the grouped form (Sec. 2.1), for
  * inspection.  Groups are runs of consecutive active particles in key order: chunks
  * of group_size, each cut in halves while its members are spread wider than
  * params.group_split times their smallest h.
@@ -196,7 +196,7 @@ int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
  *   rho_i = sum_{j in N_i} m_j W(r_ij, h_i),   dRho_i/dh_i,
  *   f_i = 1 / (1 + h_i / (3 rho_i) dRho_i/dh_i),  n_i = |N_i|,
  * with W the M4 cubic spline of support h.  With iterate != 0, h_i is iterated per
- * particle until |4 pi rho_i h_i^3 / (3 m_i) - nngb| <= nngb_tol (Sec. 3.2 relation
+ * particle until |4 pi rho_i h_i^3 / (3 m_i) - nngb| <= nngb_tol (Sec. 2.2 relation
  * N_ngb = 4 pi rho h^3 / 3): Newton steps on that function inside a bracket, with a
  * volume bisection when a step leaves the bracket; each pass re-walks only the
  * unconverged particles, regrouped.
@@ -208,7 +208,7 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
                    int iterate, int mode, int group_size, float* rho, float* drhodh,
                    float* fgrad, int32_t* nngb, int32_t* iters, cudaStream_t stream);
 
-/* a8: SPH hydro accelerations and du/dt of the active particles (Sec. 2.1 hydro
+/* a8: SPH hydro accelerations and du/dt of the active particles (Sec. 1.1 hydro
  * neighbour definition).  For j in the hydro set of i:
  *   a_i  -= m_j [ A_i dW(h_i) + A_j dW(h_j) + Pi_ij (dW(h_i) + dW(h_j))/2 ] r_ij / r
  *   du_i += m_j [ A_i dW(h_i) + Pi_ij (dW(h_i) + dW(h_j))/4 ] v_ij . r_ij / r
@@ -224,7 +224,7 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
 
 /* Velocity divergence and curl of the active particles over their density sets (the
  * a6 neighbour definition, support h_i), the inputs of the viscosity limiters used with
- * the Sec. 2.1 hydro loop.  The paper prints no formula for them; the standard SPH
+ * the Sec. 1.1 hydro loop.  The paper prints no formula for them; the standard SPH
  * estimates are taken:
  *   div v_i  = -(1/rho_i) sum_j m_j (v_i - v_j) . grad_i W(r_ij, h_i),
  *   curl v_i =  (1/rho_i) sum_j m_j (v_i - v_j) x grad_i W(r_ij, h_i),
@@ -245,7 +245,7 @@ int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
  * where rho_k is the density (a6) at h_k and a_k the hydro acceleration (a8) with
  * rho, f = 1 / (1 + h dRho/dh / (3 rho)), A = f (gamma - 1) u / rho and
  * c = sqrt(gamma (gamma - 1) u) taken from that density, and h_k(x, m) is the function
- * defined by (4 pi / 3) h_k^3 rho_k = nngb m_k (the Sec. 3.2 relation between h, rho
+ * defined by (4 pi / 3) h_k^3 rho_k = nngb m_k (the Sec. 2.2 relation between h, rho
  * and the neighbour number, imposed exactly) through the given h: its dependence
  * enters by the implicit function theorem, including that of f through d2Rho/dh2.
  * The caller passes h satisfying the relation (e.g. sphgrp_density with a small
@@ -273,7 +273,7 @@ int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* vel, const fl
  * cube.  One call runs, for all boxes together:
  *   keys + a stable sort by (box, key); a forest of one octree per box; grouping of
  *   every box's active particles (groups never cross a box); the density with the
- *   smoothing-length iteration (Sec. 3.2) inside one persistent work-queue kernel
+ *   smoothing-length iteration (Sec. 2.2) inside one persistent work-queue kernel
  *   over every box's groups (each group iterates its members until they converge;
  *   no host loop); the hydro forces in a second persistent kernel; and, with
  *   SPHGRP_BATCH_BACKWARD, the adjoint of sphgrp_backward over every particle of every

@@ -204,7 +204,7 @@ def curve_order(pos, targets=None):
 
 
 def density_grouped(pos, m, h, g, targets=None):
-    """Grouped density (Sec. 3.1): the targets in curve order, g consecutive per group,
+    """Grouped density (Sec. 2.1): the targets in curve order, g consecutive per group,
     one superset walk per group.  Returns the per-target outputs of ``density`` in the
     order of ``targets`` (ascending indices when None) and the walk statistics."""
     x, y, z = _xyz(pos)
@@ -227,7 +227,7 @@ def density_grouped(pos, m, h, g, targets=None):
 
 
 def hydro_grouped(pos, vel, m, h, rho, f, u, g, targets=None, gamma=5.0 / 3.0, alpha=1.0, beta=2.0, eps=0.01):
-    """Grouped hydro (Sec. 3.1, symmetric criterion); outputs as ``hydro``, in the order of
+    """Grouped hydro (Sec. 2.1, symmetric criterion); outputs as ``hydro``, in the order of
     ``targets``, plus the walk statistics."""
     x, y, z = _xyz(pos)
     vx, vy, vz = _xyz(vel)

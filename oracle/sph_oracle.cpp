@@ -7,18 +7,18 @@
 // Everything here is the plain definition, in FP64, compiled with -ffp-contract=off so
 // that every product and sum is rounded exactly as written:
 //
-//  * Peano-Hilbert keys (Sec. 2: Gadget3 orders particles along the Hilbert curve;
+//  * Peano-Hilbert keys (Sec. 1: Gadget3 orders particles along the Hilbert curve;
 //    the curve variant is not stated, the reading taken is Skilling's transpose
 //    construction, "Programming the Hilbert curve", AIP Conf. Proc. 707 (2004), on a
 //    2^21 grid per axis, axis order x, y, z, interleaved most significant bit first).
 //  * stable order by key (ties keep the input order).
-//  * neighbour sets (Sec. 2.1): density  N_i = { j : |r_ij| < h_i },
+//  * neighbour sets (Sec. 1.1): density  N_i = { j : |r_ij| < h_i },
 //                               hydro    N_i = { j : |r_ij| < max(h_i, h_j) },
 //    minimum-image distances in the periodic unit cube, r^2 = dx*dx + dy*dy + dz*dz.
 //  * M4 cubic-spline kernel with compact support h (the paper fixes no kernel; this is
 //    the Gadget convention), the SPH density with its h-derivative, the grad-h
 //    correction f_i, and the smoothing-length iteration to a fixed effective
-//    neighbour number N_ngb = 4 pi rho h^3 / (3 m) (Sec. 3.2, the relation above Eq. 1).
+//    neighbour number N_ngb = 4 pi rho h^3 / (3 m) (Sec. 2.2, the relation above Eq. 1).
 //  * SPH hydro accelerations and du/dt (grad-h pressure term plus Monaghan
 //    artificial viscosity); the paper only cites its hydro scheme, the reading is the
 //    standard energy-conserving form.
@@ -313,7 +313,7 @@ struct DensityOut {
     int32_t n;
 };
 
-// Grouped search (Sec. 3.1, Neighbour Recycling): the members of a group share one
+// Grouped search (Sec. 2.1, Neighbour Recycling): the members of a group share one
 // tree walk around a centre c, the group's first member as in the paper.  Density:
 // every neighbour j of member k has |x_j - c| <= |x_j - x_k| + |x_k - c| < h_k + d_k
 // with d_k = |x_k - c|, so the walk radius R = max_k (d_k + h_k) covers every member's
@@ -704,7 +704,7 @@ int orc_hydro(int64_t n, const double* x, const double* y, const double* z,
     return 0;
 }
 
-// Grouped density and hydro (Sec. 3.1): the targets, given in the order of the curve,
+// Grouped density and hydro (Sec. 2.1): the targets, given in the order of the curve,
 // are cut into groups of g consecutive entries; each group walks the tree once for its
 // superset and each member filters it.  Outputs are indexed like the targets and are
 // those of orc_density / orc_hydro bit for bit (same sets, same summation order).

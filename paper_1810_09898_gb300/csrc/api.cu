@@ -245,7 +245,7 @@ int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s,
 
 // Groups of the grouped form over the work list U (see k_split_groups); fills
 // a->groups and a->ngroups.  Reads the group count back (stream sync).
-// Tree grouping (Sec. 3): the actives under one node of depth L share the key's first
+// Tree grouping (Sec. 2): the actives under one node of depth L share the key's first
 // 3 L bits, and every node is a contiguous range of the key order, so a group is a run
 // of consecutive actives with one prefix, cut into pieces of at most g.
 __global__ void k_prefix_runs(int nu, const int32_t* __restrict__ U, const uint64_t* __restrict__ keys, int shift,

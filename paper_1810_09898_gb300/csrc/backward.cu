@@ -1,7 +1,7 @@
 // Backward (adjoint) of the density and hydro loops: the gradient of
 //   L = sum_k w_k . a_k + sum_k s_k rho_k
 // with respect to positions, velocities and masses.  The paper has no backward pass;
-// this differentiates the density (Sec. 3.2 relation between h, rho and the
+// this differentiates the density (Sec. 2.2 relation between h, rho and the
 // neighbour number) and the hydro accelerations of the forward loops, with the
 // neighbour sets of the given state held fixed and h defined by the exact constraint
 // (4 pi / 3) h_k^3 rho_k = N_ngb m_k (implicit function theorem).

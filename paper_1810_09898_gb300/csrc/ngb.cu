@@ -1,6 +1,6 @@
 // Neighbour search and the SPH loops that consume it, forward and backward.
 //
-// Two forms (Sec. 2.1 standard search, Sec. 3.1 Neighbour Recycling):
+// Two forms (Sec. 1.1 standard search, Sec. 2.1 Neighbour Recycling):
 //  * individual: one thread per active particle walks the octree depth-first with
 //    skip pointers and radius h_i (hydro: max(h_i, node hmax)), testing the particles
 //    of every opened leaf;
@@ -1722,7 +1722,7 @@ __global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, flo
     cnt[ch] = ng;
 }
 
-// Radius grouping (Sec. 3.1): a group starts at a work-list entry and takes the entries
+// Radius grouping (Sec. 2.1): a group starts at a work-list entry and takes the entries
 // that follow while they lie closer than R = f h to its first particle (periodic
 // minimum image), at most cap of them; the first entry farther away starts the next
 // group.  One thread scans each run of kRadiusRun entries; groups go to tmp at the

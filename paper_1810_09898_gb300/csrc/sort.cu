@@ -1,5 +1,5 @@
 // Peano-Hilbert keys, the stable device radix sort of (key, index) and a device
-// exclusive scan (Sec. 2.2: Gadget3 orders its particles along the Hilbert curve).
+// exclusive scan (Sec. 1.2: Gadget3 orders its particles along the Hilbert curve).
 #include <cooperative_groups.h>
 
 #include <utility>

@@ -1,5 +1,5 @@
 // Gather into key order and the linear octree over the key-ordered particles
-// (Sec. 2.2: an octree divides the volume; particles follow the Hilbert curve, so
+// (Sec. 1.2: an octree divides the volume; particles follow the Hilbert curve, so
 // every octree cell is one contiguous range of the sorted order).
 #include <algorithm>
 

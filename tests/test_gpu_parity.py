@@ -279,7 +279,7 @@ def test_rejects_bad_input(cuda_device):
         ctx.density(act, torch.tensor([0.1], dtype=torch.float64, device="cuda"), 0, 1, 999, z, z, z, zi)
 
 
-# ---------------------------------------------------------------- radius grouping (Sec. 3.1)
+# ---------------------------------------------------------------- radius grouping (Sec. 2.1)
 
 @pytest.fixture(scope="module", params=[(0.5, 1), (1.0, 0)], ids=["f0.5-box", "f1.0-first"])
 def clu_radius(cuda_device, request):
@@ -373,7 +373,7 @@ def test_rejects_bad_parameters(cuda_device):
     sg.Context(100, stack_shared=32, group_mode=1, group_f=0.7, iteration=1).close()
 
 
-# ---------------------------------------------------------------- tree-depth grouping (Sec. 3)
+# ---------------------------------------------------------------- tree-depth grouping (Sec. 2)
 
 @pytest.fixture(scope="module", params=[5, 8], ids=["level5", "level8"])
 def clu_tree(cuda_device, request):

@@ -1,4 +1,4 @@
-"""The oracle's grouped form (Sec. 3.1, Neighbour Recycling): groups of g consecutive
+"""The oracle's grouped form (Sec. 2.1, Neighbour Recycling): groups of g consecutive
 targets along the curve, one superset walk per group, each member filtering the
 superset.  The method is exact, so every output must equal the per-particle form bit for
 bit (same neighbour sets, same summation order); the per-particle form is itself pinned

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Peano-Hilbert keys and stable order (Sec. 2: Hilbert ordering).
+"""Pins of the oracle's Peano-Hilbert keys and stable order (Sec. 1: Hilbert ordering).
 
 The curve variant is fixed by the properties that make it a Hilbert curve at all, each
 checked by brute force on small grids: the index is a bijection, consecutive indices

@@ -1,4 +1,4 @@
-"""Pins of the oracle's neighbour sets (Sec. 2.1 definitions).
+"""Pins of the oracle's neighbour sets (Sec. 1.1 definitions).
 
 density: j is a neighbour of i iff |r_ij| < h_i (strict); hydro: iff j != i and
 |r_ij| < max(h_i, h_j); distances use the minimum image in the periodic unit cube.
