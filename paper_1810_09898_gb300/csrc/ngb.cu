@@ -33,6 +33,8 @@ constexpr int kTileH = 128;   // hydro tile
 constexpr int kTileA = 128;   // adjoint tiles
 constexpr int kTileV = 128;   // velocity-derivative tile
 
+
+
 struct LocalCounters {
     unsigned long long nodes = 0, cands = 0, tests = 0, pairs = 0, retests = 0;
     int max_stack = 0;
@@ -150,13 +152,16 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
     return ok != 0u;
 }
 
-// Waits for the phase with the given parity; gives up after a bounded number of polls
-// (the copies of a tile take microseconds), setting the timeout flag.
+// Waits, with the whole warp, for the phase with the given parity; gives up after a
+// bounded number of polls (the copies of a tile take microseconds), setting the timeout
+// flag.  The result is the same on every lane: true only if every lane saw the phase
+// complete.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, unsigned* err) {
-    for (uint32_t k = 0; k < (1u << 24); ++k)
-        if (mbar_try_wait(bar, parity)) return true;
-    atomicOr(err, kErrTimeout);
-    return false;
+    bool ok = false;
+    for (uint32_t k = 0; k < (1u << 24) && !ok; ++k) ok = mbar_try_wait(bar, parity);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(err, kErrTimeout);
+    return ok;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1026,6 +1031,20 @@ __device__ __forceinline__ void filter_tile(typename K::Tile& T, const Layout& L
     }
 }
 
+// Filter of the nt converted candidates held in the tile: NaN dummies up to whole chunks of
+// 32 in every slice, then the member x candidate filter (dot form unless the group wraps).
+template <class K, int MODE, int M>
+__device__ __forceinline__ void filter_staged(typename K::Tile& T, const Layout& L, typename K::Member* mem, int nt,
+                                              const SearchArgs& a, LocalCounters& lc, int lane, bool wrap_safe) {
+    const int padded = L.S * ((((nt + L.S - 1) / L.S) + 31) >> 5) * 32;
+    const float nanv = __int_as_float(0x7fffffff);
+    for (int t = nt + lane; t < padded; t += 32) T.p[t] = make_float4(nanv, nanv, nanv, nanv);
+    __syncwarp();
+    if (wrap_safe) filter_tile<K, MODE, M, false>(T, L, mem, nt, a, lc, lane);
+    else filter_tile<K, MODE, M, true>(T, L, mem, nt, a, lc, lane);
+    __syncwarp();
+}
+
 // Work item of the grouped kernels: members U[base, base + cnt), the walk's start node
 // (a root of the forest), the group size of the member layout and the slice limit.
 struct GroupDesc {
@@ -1148,8 +1167,9 @@ __device__ __forceinline__ int walk_start(const int32_t* __restrict__ tab, int r
 // One group's walk from node `root` and the member x candidate filter of every staged
 // tile (the members are initialised relative to the centre C).  kSupFill writes the
 // superset at sup_pos + sup_n; sup_n accumulates the candidates.
+// Returns false if a tile copy timed out: the warp must then stop taking work.
 template <class K, int MODE, int M>
-__device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, typename K::Tile& T, const Layout& L,
+__device__ __forceinline__ bool group_search(const SearchArgs& a, WalkSmem& W, typename K::Tile& T, const Layout& L,
                                              typename K::Member (&mem)[M], uint32_t cx, uint32_t cy, uint32_t cz,
                                              int root, LocalCounters& lc, uint32_t& tma_phase, int lane,
                                              int64_t sup_pos, int64_t& sup_n) {
@@ -1183,9 +1203,10 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
     int sp = 1, gsp = 0;
     if (lane == 0) W.stack[0] = (uint32_t)start << 3;   // one node
     int nr = 0, pending = 0;
+    int nf = 0;   // converted candidates held in the tile, waiting for the filter
     __syncwarp();
     for (;;) {
-        while ((sp > 0 || gsp > 0) && sp <= a.stack_cap - 32 && pending < TCAP && nr <= kRangeCap - 32) {
+        while ((sp > 0 || gsp > 0) && sp <= a.stack_cap - 32 && pending < TCAP - nf && nr <= kRangeCap - 32) {
             if (sp == 0) {
                 const int m = min(gsp, 32);
                 if (lane < m) W.stack[lane] = spill[gsp - m + lane];
@@ -1248,76 +1269,82 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
             lc.max_stack = max(lc.max_stack, sp + gsp);
             __syncwarp();
         }
-        if (nr > 0) {
-            // ---- flush the pending leaf ranges in tiles
-            int run = 0;
-            for (int e0 = 0; e0 < nr; e0 += 32) {
-                int e = e0 + lane;
-                int c = e < nr ? W.ranges[e].y : 0;
-                int inc = warp_incl_scan(c, lane);
-                if (e < nr) W.rpre[e] = run + inc - c;
-                run += __shfl_sync(0xffffffffu, inc, 31);
-            }
-            if (lane == 0) W.rpre[nr] = run;
-            __syncwarp();
-            const int total = run;
-            lc.cands += (lane == 0) ? total : 0;
-            for (int t0 = 0; t0 < total; t0 += TCAP) {
-                const int nt = min(TCAP, total - t0);
-                // first range reaching into this tile
-                int e0 = 0;
-                {
-                    int lo = 0, hi = nr;
-                    while (hi - lo > 1) {
-                        int mid = (lo + hi) >> 1;
-                        if (W.rpre[mid] <= t0) lo = mid; else hi = mid;
-                    }
-                    e0 = lo;
+        const bool walk_done = (sp == 0 && gsp == 0);
+        if (kSup) {
+            if (nr > 0) {
+                // superset export: every pending range's particles, in walk order
+                int run = 0;
+                for (int e0 = 0; e0 < nr; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int c = e < nr ? W.ranges[e].y : 0;
+                    const int inc = warp_incl_scan(c, lane);
+                    if (e < nr) W.rpre[e] = run + inc - c;
+                    run += __shfl_sync(0xffffffffu, inc, 31);
                 }
-                if (kSup) {
-                    if (MODE == kSupFill) {
-                        for (int e = e0 + (lane >> 4); e < nr; e += 2) {
-                            const int rb = W.rpre[e];
-                            if (rb >= t0 + nt) break;
-                            const int2 R = W.ranges[e];
-                            const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
-                            for (int gt = lo + (lane & 15); gt < hi; gt += 16) {
-                                int64_t p = sup_pos + sup_n + gt;
-                                if (p < a.x_cap) a.x_idx[p] = a.perm[R.x + (gt - rb)];
-                                else atomicOr(a.err, kErrCap);
-                            }
+                __syncwarp();
+                lc.cands += (lane == 0) ? run : 0;
+                if (MODE == kSupFill) {
+                    for (int e = lane >> 4; e < nr; e += 2) {
+                        const int rb = W.rpre[e];
+                        const int2 R = W.ranges[e];
+                        for (int gt = rb + (lane & 15); gt < rb + R.y; gt += 16) {
+                            const int64_t q = sup_pos + sup_n + gt;
+                            if (q < a.x_cap) a.x_idx[q] = a.perm[R.x + (gt - rb)];
+                            else atomicOr(a.err, kErrCap);
                         }
                     }
-                    continue;
                 }
-                // the tile's piece of every range: bulk copies of every SoA array
+                sup_n += run;
+                nr = 0;
+                pending = 0;
+                __syncwarp();
+            }
+        } else {
+            // Stage the pending ranges from their front into the tile's free part [nf, TCAP)
+            // (what does not fit stays pending for the next tile) and filter whenever the tile
+            // is full, so that every tile but a group's last holds TCAP candidates.
+            for (;;) {
+                const int room = TCAP - nf;
+                if (!(nr > 0 && (walk_done || pending >= room || nr > kRangeCap - 32))) break;
+                const int nt = min(pending, room);
+                int run = 0;
+                for (int e0 = 0; e0 < nr; e0 += 32) {
+                    const int e = e0 + lane;
+                    const int c = e < nr ? W.ranges[e].y : 0;
+                    const int inc = warp_incl_scan(c, lane);
+                    if (e < nr) W.rpre[e] = run + inc - c;
+                    run += __shfl_sync(0xffffffffu, inc, 31);
+                }
+                __syncwarp();
+                lc.cands += (lane == 0) ? nt : 0;
+                // bulk copies of every SoA array; ranges adjacent in memory (consecutive
+                // leaves of the walk usually are) are merged into one copy, issued by the
+                // first range of the run (or of a 32-range block)
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_expect_tx(&W.bar, (uint32_t)nt * K::bytes);
                 __syncwarp();
-                // Ranges adjacent in memory (consecutive leaves of the walk usually are)
-                // are merged into one copy: the first range of a run (or of a 32-range
-                // chunk) issues the copy of the whole run.
-                for (int eb = e0; eb < nr; eb += 32) {
+                int nfull = 0;   // ranges consumed entirely by this chunk
+                for (int eb = 0; eb < nr; eb += 32) {
                     const int e = eb + lane;
                     int rb = 0, src = 0, dst = 0, cnt = 0;
                     bool valid = false, cont = false;
                     if (e < nr) {
                         rb = W.rpre[e];
-                        valid = rb < t0 + nt;
+                        valid = rb < nt;
                     }
                     if (valid) {
                         const int2 R = W.ranges[e];
-                        const int lo = max(rb, t0), hi = min(rb + R.y, t0 + nt);
-                        src = R.x + (lo - rb);
-                        dst = lo - t0;
-                        cnt = hi - lo;
-                        if (lane > 0 && e > e0) {
+                        src = R.x;
+                        dst = nf + rb;
+                        cnt = min(R.y, nt - rb);
+                        if (lane > 0) {
                             const int2 Q = W.ranges[e - 1];
                             cont = Q.x + Q.y == R.x;
                         }
                         for (int k = 0; k < cnt; ++k) T.r[dst + k] = src + k;
                     }
+                    nfull += __popc(__ballot_sync(0xffffffffu, valid && cnt == W.ranges[e < nr ? e : 0].y));
                     const unsigned vmask = __ballot_sync(0xffffffffu, valid);
                     if (vmask == 0u) break;
                     const bool head = valid && !cont;
@@ -1333,10 +1360,35 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
                     }
                     if (vmask != 0xffffffffu) break;
                 }
-                if (!mbar_wait_bounded(&W.bar, tma_phase, a.err)) mbar_wait_bounded(&W.bar, tma_phase, a.err);
+                // the chunk leaves the pending list: drop the consumed ranges, shorten a
+                // partly consumed one, move the rest to the front
+                {
+                    const int keep_n = nr - nfull;
+                    int2 r0 = make_int2(0, 0), r1 = make_int2(0, 0);
+                    if (lane < keep_n) r0 = W.ranges[nfull + lane];
+                    if (lane + 32 < keep_n) r1 = W.ranges[nfull + lane + 32];
+                    if (lane == 0 && keep_n > 0) {
+                        const int used = nt - W.rpre[nfull];   // > 0 only for a partly consumed range
+                        if (used > 0) { r0.x += used; r0.y -= used; }
+                    }
+                    __syncwarp();
+                    if (lane < keep_n) W.ranges[lane] = r0;
+                    if (lane + 32 < keep_n) W.ranges[lane + 32] = r1;
+                    __syncwarp();
+                    nr = keep_n;
+                    pending -= nt;
+                }
+                if (!mbar_wait_bounded(&W.bar, tma_phase, a.err)) {
+                    // The chunk never completed: nothing of it may be used, and the barrier's
+                    // phase no longer matches tma_phase.  Give the copies in flight one more
+                    // bounded wait to land in shared memory, then the warp abandons its work
+                    // (the timeout flag is set; the call reports ETIMEOUT).
+                    mbar_wait_bounded(&W.bar, tma_phase, a.err);
+                    return false;
+                }
                 tma_phase ^= 1u;
                 // in place: fixed point -> coordinates relative to the centre
-                for (int t = lane; t < nt; t += 32) {
+                for (int t = nf + lane; t < nf + nt; t += 32) {
                     const uint4 P = *reinterpret_cast<const uint4*>(&T.p[t]);
                     const float4 O = T.o[t];
                     const float px = rel_coord(P.x, O.x, cx), py = rel_coord(P.y, O.y, cy),
@@ -1347,20 +1399,17 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
                         T.o[t] = make_float4(hj * hj, O.w, 0.0f, 0.0f);
                     }
                 }
-                {
-                    // NaN dummies up to whole chunks of 32 in every slice
-                    const int padded = L.S * ((((nt + L.S - 1) / L.S) + 31) >> 5) * 32;
-                    const float nanv = __int_as_float(0x7fffffff);
-                    for (int t = nt + lane; t < padded; t += 32) T.p[t] = make_float4(nanv, nanv, nanv, nanv);
+                __syncwarp();
+                nf += nt;
+                if (nf >= TCAP) {
+                    filter_staged<K, MODE, M>(T, L, mem, nf, a, lc, lane, wrap_safe);
+                    nf = 0;
                 }
-                __syncwarp();
-                if (wrap_safe) filter_tile<K, MODE, M, false>(T, L, mem, nt, a, lc, lane);
-                else filter_tile<K, MODE, M, true>(T, L, mem, nt, a, lc, lane);
-                __syncwarp();
             }
-            if (kSup) sup_n += total;
-            nr = 0;
-            pending = 0;
+            if (walk_done && nf > 0) {
+                filter_staged<K, MODE, M>(T, L, mem, nf, a, lc, lane, wrap_safe);
+                nf = 0;
+            }
         }
         if (sp > a.stack_cap - 32) {
             // the next step could push 32 entries: the oldest (up to 32, the bottom of the
@@ -1381,11 +1430,13 @@ __device__ __forceinline__ void group_search(const SearchArgs& a, WalkSmem& W, t
         }
         if (sp == 0 && gsp == 0) break;
     }
+    return true;
 }
 
-// One work item of the grouped kernels: set-up, search, results.
+// One work item of the grouped kernels: set-up, search, results.  Returns false if the
+// warp must stop taking work (a tile copy timed out).
 template <class K, int MODE, int M>
-__device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, typename K::Tile& T, int gid,
+__device__ __forceinline__ bool process_group(const SearchArgs& a, WalkSmem& W, typename K::Tile& T, int gid,
                                               LocalCounters& lc, uint32_t& tma_phase, int lane) {
     using Member = typename K::Member;
     constexpr bool kSup = (MODE == kSupCount || MODE == kSupFill);
@@ -1398,7 +1449,7 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
         rk[mm] = (k >= 0 && k < d.cnt) ? a.U[d.base + k] : -1;
     }
     uint32_t cx = 0, cy = 0, cz = 0;
-    if (!group_centre<M>(a, rk, cx, cy, cz)) return;
+    if (!group_centre<M>(a, rk, cx, cy, cz)) return true;
     Member mem[M];
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) member_init(mem[mm], a, rk[mm], cx, cy, cz);
@@ -1410,7 +1461,8 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
     }
     int64_t sup_pos = 0, sup_n = 0;
     if (MODE == kSupFill) sup_pos = a.x_off[gid];
-    group_search<K, MODE, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, sup_pos, sup_n);
+    if (!group_search<K, MODE, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, sup_pos, sup_n))
+        return false;
     // the symmetric sums count the member itself as a pair at r = 0 (once, in slice 0)
     constexpr bool kSelfPair = MODE == kAcc && (K::id == kKindHydro || K::id == kKindHydroAdj);
 #pragma unroll
@@ -1418,7 +1470,7 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
         lc.pairs += mem[mm].n - ((kSelfPair && L.slice == 0 && mem[mm].rank >= 0) ? 1 : 0);
     if (kSup) {
         if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
-        return;
+        return true;
     }
     if (L.S > 1) {
 #pragma unroll
@@ -1431,6 +1483,7 @@ __device__ __forceinline__ void process_group(const SearchArgs& a, WalkSmem& W, 
             if (mem[mm].rank >= 0) write_result<MODE>(mem[mm], a);
         }
     }
+    return true;
 }
 
 __device__ __forceinline__ int next_item(const SearchArgs& a, int lane) {
@@ -1455,7 +1508,7 @@ k_group(SearchArgs a) {
     for (;;) {
         const int gid = next_item(a, lane);
         if (gid >= ng) break;
-        process_group<K, MODE, M>(a, W, T, gid, lc, tma_phase, lane);
+        if (!process_group<K, MODE, M>(a, W, T, gid, lc, tma_phase, lane)) break;
     }
     flush_counters(a, lc, lane);
 }
@@ -1481,11 +1534,12 @@ k_group_pair(SearchArgs a0, SearchArgs a1) {
     for (;;) {
         const int gid = next_item(a0, lane);
         if (gid >= n0 + n1) break;
-        if (gid < n0)
-            process_group<K0, kAcc, M>(a0, W, *reinterpret_cast<typename K0::Tile*>(tile), gid, lc, tma_phase, lane);
-        else
-            process_group<K1, kAcc, M>(a1, W, *reinterpret_cast<typename K1::Tile*>(tile), gid - n0, lc, tma_phase,
-                                       lane);
+        const bool ok =
+            gid < n0 ? process_group<K0, kAcc, M>(a0, W, *reinterpret_cast<typename K0::Tile*>(tile), gid, lc,
+                                                  tma_phase, lane)
+                     : process_group<K1, kAcc, M>(a1, W, *reinterpret_cast<typename K1::Tile*>(tile), gid - n0, lc,
+                                                  tma_phase, lane);
+        if (!ok) break;
     }
     flush_counters(a0, lc, lane);
 }
@@ -1552,7 +1606,8 @@ k_group_dens_iter(SearchArgs a, IterArgs it) {
     if (lane == 0) mbar_init(&W.bar, 1u);
     __syncwarp();
     const int ng = group_count(a);
-    for (;;) {
+    bool alive = true;
+    while (alive) {
         const int gid = next_item(a, lane);
         if (gid >= ng) break;
         const GroupDesc d = group_desc(a, gid);
@@ -1574,7 +1629,10 @@ k_group_dens_iter(SearchArgs a, IterArgs it) {
 #pragma unroll
             for (int mm = 0; mm < M; ++mm) member_init(mem[mm], a, rk[mm], cx, cy, cz);
             int64_t sup_n = 0;
-            group_search<KDens, kAcc, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, 0, sup_n);
+            if (!group_search<KDens, kAcc, M>(a, W, T, L, mem, cx, cy, cz, d.root, lc, tma_phase, lane, 0, sup_n)) {
+                alive = false;
+                break;
+            }
 #pragma unroll
             for (int mm = 0; mm < M; ++mm) lc.pairs += mem[mm].n;
             if (L.S > 1) {
