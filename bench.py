@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--active", type=float, default=1.0)
     ap.add_argument("--group", type=int, default=16)
     ap.add_argument("--h-scatter", type=float, default=0.05)
-    ap.add_argument("--iteration", choices=["passes", "in-group"], default="passes",
+    ap.add_argument("--iteration", choices=["passes", "recycle", "in-group"], default="passes",
                     help="smoothing-length iteration of the grouped density")
     ap.add_argument("--cpu-n", type=int, default=1 << 19, help="oracle sample size")
     ap.add_argument("--no-individual", action="store_true")
@@ -252,7 +252,8 @@ class Problem:
         self.m = self.host["m"].to(dev)
         self.vel = self.host["vel"].to(dev)
         self.u = self.host["u"].to(dev)
-        self.ctx = sg.Context(n, iteration=sg.ITER_IN_GROUP if a.iteration == "in-group" else sg.ITER_PASSES)
+        self.ctx = sg.Context(n, iteration={"in-group": sg.ITER_IN_GROUP, "passes": sg.ITER_PASSES,
+                                            "recycle": sg.ITER_RECYCLE}[a.iteration])
         self.perm = torch.empty(n, dtype=torch.int32, device=dev)
         f32 = dict(dtype=torch.float32, device=dev)
         self.rho = torch.zeros(n, **f32)

@@ -82,10 +82,19 @@ typedef struct sphgrp_params {
                            would filter more than group_split times its own sphere; <= 0
                            keeps plain chunks of group_size.  e.g. 2 */
     int iteration;      /* smoothing-length iteration of the grouped density:
-                           SPHGRP_ITER_PASSES (one search launch per pass over the still
-                           unconverged particles, regrouped) or SPHGRP_ITER_IN_GROUP (one
+                           SPHGRP_ITER_PASSES (default: one search launch per pass over the
+                           still unconverged particles, regrouped), SPHGRP_ITER_IN_GROUP (one
                            launch; every group repeats walk, filter and update until its
-                           members converge).  The individual form always iterates in passes. */
+                           members converge) or SPHGRP_ITER_RECYCLE (the first pass
+                           also keeps, for every member, the candidates of its group's
+                           superset within iter_widen * h; later passes of the particles
+                           whose h stays within that radius iterate on those candidates in
+                           one launch, the others take walk passes as in SPHGRP_ITER_PASSES;
+                           group_size <= 32; device memory for 192 candidate ranks per
+                           particle is allocated by the first such call, and without it the
+                           call walks every pass).  The iterates are those of the pass-by-pass
+                           iteration in every mode.  The individual form always iterates in
+                           passes. */
     int group_mode;     /* how the grouped form cuts the active list (in key order) into groups:
                            SPHGRP_GROUP_COUNT: chunks of group_size, split as group_split says;
                            SPHGRP_GROUP_RADIUS (Sec. 2.1, the paper's rule): a group starts at an
@@ -100,9 +109,11 @@ typedef struct sphgrp_params {
                            cut into pieces of at most group_size; 1 .. 21, e.g. 7 */
     int stack_shared;   /* walk-stack entries per warp kept in shared memory (32 .. 256); deeper
                            walks continue in a global overflow area.  e.g. 256 */
+    double iter_widen;  /* SPHGRP_ITER_RECYCLE: radius of the kept candidates over h, in
+                           [1, 2]; a particle whose h grows beyond it walks again.  e.g. 1.1 */
 } sphgrp_params;
 
-enum { SPHGRP_ITER_PASSES = 0, SPHGRP_ITER_IN_GROUP = 1 };
+enum { SPHGRP_ITER_PASSES = 0, SPHGRP_ITER_IN_GROUP = 1, SPHGRP_ITER_RECYCLE = 2 };
 enum { SPHGRP_GROUP_COUNT = 0, SPHGRP_GROUP_RADIUS = 1, SPHGRP_GROUP_TREE = 2 };
 
 enum { SPHGRP_CENTRE_FIRST = 0, SPHGRP_CENTRE_BOX = 1 };

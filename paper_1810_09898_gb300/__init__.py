@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     INDIVIDUAL,
     ITER_IN_GROUP,
     ITER_PASSES,
+    ITER_RECYCLE,
     SphgrpError,
     Context,
     kernel_launches,

@@ -15,7 +15,7 @@ _LIB_PATH = os.path.join(HERE, "_build", "libsphgrp.so")
 
 INDIVIDUAL, GROUPED = 0, 1
 CENTRE_FIRST, CENTRE_BOX = 0, 1
-ITER_PASSES, ITER_IN_GROUP = 0, 1
+ITER_PASSES, ITER_IN_GROUP, ITER_RECYCLE = 0, 1, 2
 GROUP_COUNT, GROUP_RADIUS, GROUP_TREE = 0, 1, 2
 DENSITY, HYDRO = 0, 1
 
@@ -91,6 +91,7 @@ class Params(ctypes.Structure):
         ("group_f", ctypes.c_double),
         ("group_level", ctypes.c_int),
         ("stack_shared", ctypes.c_int),
+        ("iter_widen", ctypes.c_double),
     ]
 
 

@@ -243,6 +243,49 @@ int prepare_active(Ctx* c, int64_t n_act, const int32_t* active, cudaStream_t s,
     return SPHGRP_OK;
 }
 
+// The work-list entries flagged in c->flag move to *U2 (order kept), which becomes the
+// work list; reads the new count back (stream sync).
+int compact_unconverged(Ctx* c, int32_t** U, int32_t** U2, int* nu, cudaStream_t s) {
+    int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
+    int rc = exclusive_scan_i32(c, c->flag, c->scan, *nu, total, s);
+    if (rc) return rc;
+    k_compact_list<<<blocks_for(*nu, 256), 256, 0, s>>>(*nu, c->flag, c->scan, *U, *U2);
+    note_launch();
+    cudaMemcpyAsync(c->host_small, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "iteration count"))) return rc;
+    *nu = c->host_small[0];
+    std::swap(*U, *U2);
+    return SPHGRP_OK;
+}
+
+// Candidate-list buffers of the recycled iteration for n_max particles (kListCap ranks
+// per particle); ENOMEM if the device cannot hold them (the caller then walks every pass).
+int list_buffers(Ctx* c) {
+    if (c->lst) return SPHGRP_OK;
+    if (c->lst_failed) return SPHGRP_ENOMEM;
+    const int64_t n = c->n_max;
+    int rc = 0;
+    rc |= dalloc(&c->lst, n * kListCap);
+    rc |= dalloc(&c->lrec, n);
+    rc |= dalloc(&c->lhw, n);
+    rc |= dalloc(&c->lslot, n);
+    rc |= dalloc(&c->npass, n);
+    if (rc) {
+        void* ptrs[] = {c->lst, c->lrec, c->lhw, c->lslot, c->npass};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        c->lst = nullptr;
+        c->lrec = nullptr;
+        c->lhw = nullptr;
+        c->lslot = nullptr;
+        c->npass = nullptr;
+        c->lst_failed = true;
+        cudaGetLastError();   // the failed allocation is not a sticky error
+        return set_error(SPHGRP_ENOMEM, "no device memory for the candidate lists");
+    }
+    return SPHGRP_OK;
+}
+
 // Groups of the grouped form over the work list U (see k_split_groups); fills
 // a->groups and a->ngroups.  Reads the group count back (stream sync).
 // Tree grouping (Sec. 2): the actives under one node of depth L share the key's first
@@ -394,6 +437,7 @@ void sphgrp_default_params(sphgrp_params* p) {
     p->group_f = 0.5;
     p->group_level = 7;
     p->stack_shared = 256;
+    p->iter_widen = 1.1;
 }
 
 const char* sphgrp_last_error(void) { return g_last_error.c_str(); }
@@ -413,7 +457,9 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     else sphgrp_default_params(&c->p);
     if (c->p.leaf_size < 1 || c->p.leaf_size > 1024 || !(c->p.nngb > 0) || !(c->p.nngb_tol >= 0) ||
         c->p.max_iter < 1 || (c->p.group_centre != SPHGRP_CENTRE_FIRST && c->p.group_centre != SPHGRP_CENTRE_BOX) ||
-        (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP) ||
+        (c->p.iteration != SPHGRP_ITER_PASSES && c->p.iteration != SPHGRP_ITER_IN_GROUP &&
+         c->p.iteration != SPHGRP_ITER_RECYCLE) ||
+        !(c->p.iter_widen >= 1.0 && c->p.iter_widen <= 2.0) ||
         (c->p.group_mode != SPHGRP_GROUP_COUNT && c->p.group_mode != SPHGRP_GROUP_RADIUS &&
          c->p.group_mode != SPHGRP_GROUP_TREE) ||
         (c->p.group_mode == SPHGRP_GROUP_TREE && (c->p.group_level < 1 || c->p.group_level > kKeyLevels)) ||
@@ -487,7 +533,7 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
                     c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
                     c->acc_s2, c->wadj, c->dadj, c->adj0, c->adj1, c->adj2, c->adj3,
                     c->stack_spill, c->start_tab, c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
-                    c->tree.nlevel};
+                    c->tree.nlevel, c->lst, c->lrec, c->lhw, c->lslot, c->npass};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_small) cudaFreeHost(c->host_small);
@@ -717,6 +763,22 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     int64_t walks = 0, members = 0;
     int it = 1;
     const int max_iter = iterate ? c->p.max_iter : 1;
+    // Recycled iteration (Sec. 2.2 iteration with the Sec. 2.1 supersets reused): the
+    // first pass keeps every member's candidates within h_w = iter_widen * h, and the
+    // later passes of the members whose h stays within h_w iterate on those lists in one
+    // kernel; the rest continue with walk passes as below.
+    bool recycle = grouped && iterate && c->p.iteration == SPHGRP_ITER_RECYCLE && group_size <= 32 && nu > 0;
+    if (recycle && (rc = list_buffers(c)) != SPHGRP_OK) {
+        if (rc != SPHGRP_ENOMEM) return rc;
+        recycle = false;   // not enough device memory for the lists: walk passes only
+    }
+    int32_t* npass = recycle ? c->npass : nullptr;
+    int* max_pass = c->work + 10;
+    int list_passes = 0;
+    if (recycle) {
+        cudaMemsetAsync(c->npass, 0, c->n * sizeof(int32_t), s);
+        cudaMemsetAsync(max_pass, 0, sizeof(int), s);
+    }
     for (it = 1; it <= max_iter && nu > 0; ++it) {
         SearchArgs a = base_args(c);
         a.U = U;
@@ -755,26 +817,69 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         ua.s0 = c->acc_rho;
         ua.s1 = c->acc_drho;
         ua.n = c->acc_n;
+        ua.npass = npass;
+        const bool lists = recycle && it == 1;
+        if (lists) {
+            a.o_list = c->lst;
+            a.o_lrec = c->lrec;
+            a.o_lhw = c->lhw;
+            a.o_lslot = c->lslot;
+            a.list_widen = c->p.iter_widen;
+        }
         timer_begin(c, s);
-        rc = launch_search(a, SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
+        rc = launch_search(a, lists ? kKindDensityList : SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
         timer_end(c, s, a.nu);
         if (rc) return rc;
         if ((rc = launch_hsml_update(ua, s))) return rc;
         if (!iterate) break;
-        int32_t* total = reinterpret_cast<int32_t*>(c->work) + 4;
-        if ((rc = exclusive_scan_i32(c, c->flag, c->scan, nu, total, s))) return rc;
-        k_compact_list<<<blocks_for(nu, 256), 256, 0, s>>>(nu, c->flag, c->scan, U, U2);
-        note_launch();
-        cudaMemcpyAsync(c->host_small, total, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if ((rc = check_cuda(cudaStreamSynchronize(s), "iteration count"))) return rc;
-        nu = c->host_small[0];
-        std::swap(U, U2);
+        if ((rc = compact_unconverged(c, &U, &U2, &nu, s))) return rc;
+        if (lists && nu > 0) {
+            // passes 2, 3, ... of the particles whose h stays within their list's h_w
+            ListIterArgs la;
+            std::memset(&la, 0, sizeof(la));
+            la.U = U;
+            la.nu = nu;
+            la.max_iter = max_iter;
+            la.nngb = c->p.nngb;
+            la.tol = c->p.nngb_tol;
+            la.pfix_in = c->pfix;
+            la.pfix = c->pfix;
+            la.poff = c->poff;
+            la.xd = c->xd;
+            la.yd = c->yd;
+            la.zd = c->zd;
+            la.h64 = c->h64;
+            la.lo = c->lo;
+            la.hi = c->hi;
+            la.lslot = c->lslot;
+            la.lrec = c->lrec;
+            la.lhw = c->lhw;
+            la.list = c->lst;
+            la.npass = c->npass;
+            la.max_pass = max_pass;
+            la.keep = c->flag;
+            la.perm = c->perm;
+            la.h_out = h;
+            la.rho = rho;
+            la.drhodh = drhodh;
+            la.fgrad = fgrad;
+            la.nngb_out = nngb;
+            la.iters = iters;
+            la.nfail = nfail;
+            la.ctr = c->ctr;
+            if ((rc = launch_list_iterate(la, s))) return rc;
+            if ((rc = compact_unconverged(c, &U, &U2, &nu, s))) return rc;
+            cudaMemcpyAsync(c->host_small + 3, max_pass, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if ((rc = check_cuda(cudaStreamSynchronize(s), "list passes"))) return rc;
+            list_passes = c->host_small[3];
+            it = std::max(it, list_passes);   // the walk passes continue the count
+        }
     }
     cudaMemcpyAsync(c->host_small + 2, nfail, sizeof(int), cudaMemcpyDeviceToHost, s);
     rc = finish(c, s, 0);
     c->last.walks = walks;
     c->last.members = members;
-    c->last.iterations = std::min(it, max_iter);
+    c->last.iterations = std::min(std::max(it, list_passes), max_iter);
     if (rc) return rc;
     if (c->host_small[2] > 0)
         return set_error(SPHGRP_ENOCONV, std::to_string(c->host_small[2]) + " particles did not converge");

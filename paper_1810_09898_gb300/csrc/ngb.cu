@@ -206,6 +206,17 @@ struct DMember : MemberPos {
     float p0, p1, p2;               // plain partial sums of the current tile
 };
 
+// density member of the recycled smoothing-length iteration: besides the sums at h it
+// keeps every candidate inside the widened radius h_w in its slice's sub-list
+struct DLMember : DMember {
+    float hwf;          // h_w (FP32): the walk radius covers it
+    float h2whi;        // widened candidate threshold of the difference form
+    float thr_dot_w;    // widened phase-A threshold of the dot form
+    int lsub;           // capacity of this lane's sub-list
+    int lcnt;           // candidates found (above lsub: the sub-list overflowed)
+    int32_t* lptr;      // this lane's sub-list
+};
+
 // members of the symmetric criterion |r| < max(h_i, h_j) (hydro and both adjoints)
 struct SymMember : MemberPos {
     float h, hinv, sk;  // sk = 8 / (pi h^4): dW/dr = sk * dw/dq
@@ -266,6 +277,27 @@ __device__ __forceinline__ void member_init(DMember& M, const SearchArgs& a, int
     M.h2hi = fmaf(h2, 1.0f + 3.0f * kBandRel, bk);
     M.h2lo = fmaf(h2, 1.0f - 3.0f * kBandRel, -bk);
     M.thr_dot = M.h2hi - m2;
+}
+
+__device__ __forceinline__ void member_init(DLMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    member_init(static_cast<DMember&>(M), a, rank, cx, cy, cz);
+    M.lsub = 0;
+    M.lcnt = 0;
+    M.lptr = nullptr;
+    if (rank < 0) {
+        M.hwf = 0.0f;
+        M.h2whi = -1.0f;
+        M.thr_dot_w = -3.0e38f;
+        return;
+    }
+    // the same band as the thresholds at h, at h_w: every candidate with an exact
+    // distance below h_w passes it
+    const double hw = a.h64[rank] * a.list_widen;
+    M.hwf = (float)hw;
+    const float m2 = M.mx * M.mx + M.my * M.my + M.mz * M.mz;
+    M.h2whi = fmaf((float)(hw * hw), 1.0f + 3.0f * kBandRel, 8.0f * kBandRel * m2);
+    M.thr_dot_w = M.h2whi - m2;
 }
 
 __device__ __forceinline__ bool sym_init(SymMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
@@ -369,6 +401,12 @@ __device__ __forceinline__ void radius_terms(const VMember& M, float& rl, float&
     rl = fmaxf(rl, mr + 1.0f / M.hinv);
 }
 
+__device__ __forceinline__ void radius_terms(const DLMember& M, float& rl, float& hl) {
+    if (M.rank < 0) return;
+    float mr = sqrtf(M.mx * M.mx + M.my * M.my + M.mz * M.mz);
+    rl = fmaxf(rl, mr + M.hwf);
+}
+
 __device__ __forceinline__ void radius_terms(const DMember& M, float& rl, float& hl) {
     if (M.rank < 0) return;
     float mr = sqrtf(M.mx * M.mx + M.my * M.my + M.mz * M.mz);
@@ -441,6 +479,15 @@ struct KDens {
     static constexpr int cap = kTileD;
     static constexpr uint32_t bytes = 32u;
     using Member = DMember;
+    using Tile = DensTile;
+};
+struct KDensList {
+    static constexpr int min_blocks = 7;   // resident blocks per SM (register budget; 0: compiler's choice)
+    static constexpr int id = kKindDensityList;
+    static constexpr bool sym = false;
+    static constexpr int cap = kTileD;
+    static constexpr uint32_t bytes = 32u;
+    using Member = DLMember;
     using Tile = DensTile;
 };
 struct KHydro {
@@ -597,6 +644,20 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
         if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
         else atomicOr(a.err, kErrCap);
     }
+}
+
+// density pair of the recycled iteration: a candidate inside the widened threshold joins
+// the member's sub-list, then the pair enters the sums at h as in density_pair
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void density_list_pair(DLMember& M, const SearchArgs& a, float4 p, float mj, int crank,
+                                                  LocalCounters& lc) {
+    const float dx = rel_diff<WRAP>(p.x, M.mx), dy = rel_diff<WRAP>(p.y, M.my), dz = rel_diff<WRAP>(p.z, M.mz);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (r2 < M.h2whi) {
+        if (M.lcnt < M.lsub) M.lptr[M.lcnt] = crank;
+        M.lcnt++;
+    }
+    density_pair<MODE, WRAP>(M, a, p, mj, crank, lc);
 }
 
 // velocity-derivative pair (density criterion): p = relative coordinates, mj the mass,
@@ -814,6 +875,11 @@ __device__ __forceinline__ void tile_pair(DMember& M, const SearchArgs& a, const
     density_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.r[j], lc);
 }
 template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(DLMember& M, const SearchArgs& a, const DensTile& T, int j,
+                                          LocalCounters& lc) {
+    density_list_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.r[j], lc);
+}
+template <int MODE, bool WRAP>
 __device__ __forceinline__ void tile_pair(VMember& M, const SearchArgs& a, const VelTile& T, int j,
                                           LocalCounters& lc) {
     vel_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.v[j], T.r[j], lc);
@@ -841,6 +907,8 @@ __device__ __forceinline__ float thr_dot(const SymMember& M, float hj2) {
     return fmaf(fmaxf(M.h2, hj2), 1.0f + 3.0f * kBandRel, M.bk_dot);
 }
 __device__ __forceinline__ float thr_diff(const DMember& M, float) { return M.h2hi; }
+__device__ __forceinline__ float thr_dot(const DLMember& M, float) { return M.thr_dot_w; }
+__device__ __forceinline__ float thr_diff(const DLMember& M, float) { return M.h2whi; }
 __device__ __forceinline__ float thr_dot(const VMember& M, float) { return M.thr_dot; }
 __device__ __forceinline__ float thr_diff(const VMember& M, float) { return M.h2hi; }
 __device__ __forceinline__ float thr_diff(const SymMember& M, float hj2) {
@@ -1453,6 +1521,15 @@ __device__ __forceinline__ bool process_group(const SearchArgs& a, WalkSmem& W, 
     Member mem[M];
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) member_init(mem[mm], a, rk[mm], cx, cy, cz);
+    if constexpr (K::id == kKindDensityList) {
+        // list slot = the member's index in the work list; sub-list of this lane's slice
+        static_assert(M == 1, "the recycled iteration keeps lists for one member per lane");
+        const int k = member_of(L, lane, 0, d.g);
+        if (mem[0].rank >= 0) {
+            mem[0].lsub = kListCap / L.S;
+            mem[0].lptr = a.o_list + (int64_t)(d.base + k) * kListCap + L.slice * mem[0].lsub;
+        }
+    }
     // export: write positions of every slot
     if (MODE == kFill) {
 #pragma unroll
@@ -1471,6 +1548,25 @@ __device__ __forceinline__ bool process_group(const SearchArgs& a, WalkSmem& W, 
     if (kSup) {
         if (MODE == kSupCount && lane == 0) a.x_cnt[gid] = sup_n;
         return true;
+    }
+    if constexpr (K::id == kKindDensityList) {
+        // the member's slice-0 lane records its sub-list lengths, S and whether all fit
+        int cnt[4];
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) {
+            const int src = L.S > 1 ? sl * d.g + (lane & (d.g - 1)) : lane;
+            const int v = __shfl_sync(0xffffffffu, mem[0].lcnt, (sl < L.S && src < 32) ? src : lane);
+            cnt[sl] = sl < L.S ? v : 0;
+        }
+        if (L.slice == 0 && mem[0].rank >= 0) {
+            const int lsub = kListCap / L.S;
+            const bool ok = cnt[0] <= lsub && cnt[1] <= lsub && cnt[2] <= lsub && cnt[3] <= lsub;
+            const int slot = d.base + member_of(L, lane, 0, d.g);
+            a.o_lrec[slot] = make_int4(ok ? cnt[0] | (cnt[1] << 16) : 0, ok ? cnt[2] | (cnt[3] << 16) : 0, L.S,
+                                       ok ? 1 : 0);
+            a.o_lhw[slot] = a.h64[mem[0].rank] * a.list_widen;
+            a.o_lslot[mem[0].rank] = slot;
+        }
     }
     if (L.S > 1) {
 #pragma unroll
@@ -1981,6 +2077,10 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
             case kKindVelocity:
                 if (mode != kAcc) return set_error(SPHGRP_EINVAL, "the velocity derivatives accumulate only");
                 return launch_group_m<KVel, kAcc>(a, sm_count, s);
+            case kKindDensityList:
+                if (mode != kAcc || a.g > 32)
+                    return set_error(SPHGRP_EINVAL, "candidate lists: accumulation, group size <= 32");
+                return launch_group_t<KDensList, kAcc, 1>(a, sm_count, s);
         }
         return set_error(SPHGRP_EINVAL, "bad kind");
     }
@@ -2006,50 +2106,90 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
 // Smoothing-length iteration: per unconverged particle, FP64
 // ---------------------------------------------------------------------------------
 
-// One particle's pass of the smoothing-length iteration (FP64): u = its work-list
-// entry, r = its rank, s0 / s1 / n its density sums at the current h.  Runs as its own
-// kernel with one particle per thread: in the search kernel's epilogue only one slice
-// of each warp would hold the members, which doubles the FP64 issue.
-__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0f, float s1f, int n) {
-    // With rho = sigma S0, dRho/dh = -(sigma / h) S1 and sigma = 8 / (pi h^3), the
-    // quantities of the iteration reduce to the sums themselves:
-    //   N_eff = (4 pi / 3) h^3 rho / m = (32 / 3) S0 / m,
-    //   f = 1 / (1 + h / (3 rho) dRho/dh) = 3 S0 / (3 S0 - S1),
-    //   g / g' = h (32 S0 - 3 N_ngb m) / (32 (3 S0 - S1))  (the Newton step).
-    const double h = a.h64[r];
-    const double m = (double)a.poff[r].w;
-    const double s0 = (double)s0f, s1 = (double)s1f;
-    const double neff = (32.0 / 3.0) * s0 / m;
-    bool done = !a.iterate || fabs(neff - a.nngb) <= a.tol;
-    bool last = a.it >= a.max_iter;
-    if (done || last) {
-        const double kPi = 3.14159265358979323846;
-        const double sigma = 8.0 / (kPi * h * h * h);
-        const int orig = a.perm[r];
-        a.rho[orig] = (float)(sigma * s0);
-        a.drhodh[orig] = (float)(-sigma / h * s1);
-        a.fgrad[orig] = (float)(3.0 * s0 / (3.0 * s0 - s1));
-        a.nngb_out[orig] = n;
-        if (a.iters) a.iters[orig] = a.it;
-        a.h_out[orig] = h;
-        a.keep[u] = 0;
-        if (!done) atomicAdd(a.nfail, 1);
-        return;
+// One particle's step of the smoothing-length iteration from its density sums at h
+// (S0 = sum m w, S1 = sum m (q w' + 3 w)) after `pass` passes.  With rho = sigma S0,
+// dRho/dh = -(sigma / h) S1 and sigma = 8 / (pi h^3), the quantities of the iteration
+// reduce to the sums themselves:
+//   N_eff = (4 pi / 3) h^3 rho / m = (32 / 3) S0 / m,
+//   f = 1 / (1 + h / (3 rho) dRho/dh) = 3 S0 / (3 S0 - S1),
+//   g / g' = h (32 S0 - 3 N_ngb m) / (32 (3 S0 - S1))  (the Newton step).
+// The convergence test |N_eff - N_ngb| <= tol is taken in FP64, as
+// |(32/3) S0 - N_ngb m| <= tol m (no division); the sums themselves are FP32, so the
+// Newton step and the bisection of the bracket carry no more than FP32 accuracy either
+// and are taken in FP32 (FP64 division is slow on this part and would buy nothing).
+// finish: converged (or no iteration asked), or the last pass; else hn is the next h and
+// [lo, hi) the updated bracket (opened at pass 1).
+struct HsmlStep {
+    bool finish, converged;
+    double hn;
+};
+
+__device__ __forceinline__ HsmlStep hsml_next(double h, float m, float s0, float s1, double nngb, double tol,
+                                              bool iterate, int pass, int max_iter, double& lo, double& hi) {
+    HsmlStep o;
+    const double t = (32.0 / 3.0) * (double)s0, nm = nngb * (double)m;
+    o.converged = !iterate || fabs(t - nm) <= tol * (double)m;
+    o.finish = o.converged || pass >= max_iter;
+    o.hn = h;
+    if (o.finish) return o;
+    if (pass == 1) {
+        lo = 0.0;
+        hi = __longlong_as_double(0x7ff0000000000000ll);
     }
-    double lo = a.it == 1 ? 0.0 : a.lo[r];
-    double hi = a.it == 1 ? __longlong_as_double(0x7ff0000000000000ll) : a.hi[r];
-    if (neff < a.nngb) lo = h; else hi = h;
-    double hn = h - h * (32.0 * s0 - 3.0 * a.nngb * m) / (32.0 * (3.0 * s0 - s1));
-    const double cbrt2 = 1.2599210498948731647672106;
+    if (t < nm) lo = h; else hi = h;
+    const float hf = (float)h;
+    const float num = fmaf(-3.0f * (float)nngb, m, 32.0f * s0);
+    const float den = 32.0f * (3.0f * s0 - s1);
+    double hn = (double)(hf - hf * (num / den));
     if (!(hn > lo && hn < hi) || !isfinite(hn)) {
-        if (isinf(hi)) hn = h * cbrt2;
-        else if (lo == 0.0) hn = h / cbrt2;
-        else hn = cbrt(0.5 * (lo * lo * lo + hi * hi * hi));
+        // volume bisection of the bracket
+        if (isinf(hi)) hn = (double)(hf * 1.25992104989487316f);
+        else if (lo == 0.0) hn = (double)(hf * 0.79370052598409974f);
+        else {
+            const float l = (float)lo, u = (float)hi;
+            hn = (double)cbrtf(0.5f * (l * l * l + u * u * u));
+        }
+    }
+    o.hn = hn;
+    return o;
+}
+
+// results of a finished particle (caller's order; rho, dRho/dh and f are FP32 outputs)
+__device__ __forceinline__ void hsml_write(int orig, double h, float s0, float s1, int n, int pass, double* h_out,
+                                          float* rho, float* drhodh, float* fgrad, int32_t* nngb_out,
+                                          int32_t* iters) {
+    const float hf = (float)h;
+    const float sigma = 2.54647908947032537f / (hf * hf * hf);   // 8 / (pi h^3)
+    rho[orig] = sigma * s0;
+    drhodh[orig] = -sigma / hf * s1;
+    fgrad[orig] = 3.0f * s0 / (3.0f * s0 - s1);
+    nngb_out[orig] = n;
+    if (iters) iters[orig] = pass;
+    h_out[orig] = h;
+}
+
+// One particle's pass of the smoothing-length iteration: u = its work-list entry, r its
+// rank, s0 / s1 / n its density sums at the current h.  Runs as its own kernel with one
+// particle per thread: in the search kernel's epilogue only one slice of each warp would
+// hold the members, which doubles the FP64 issue.
+__device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, float s0f, float s1f, int n) {
+    const double h = a.h64[r];
+    const float m = a.poff[r].w;
+    const int pass = a.npass ? a.npass[r] + 1 : a.it;
+    if (a.npass) a.npass[r] = pass;
+    double lo = pass == 1 ? 0.0 : a.lo[r];
+    double hi = pass == 1 ? __longlong_as_double(0x7ff0000000000000ll) : a.hi[r];
+    const HsmlStep st = hsml_next(h, m, s0f, s1f, a.nngb, a.tol, a.iterate != 0, pass, a.max_iter, lo, hi);
+    if (st.finish) {
+        hsml_write(a.perm[r], h, s0f, s1f, n, pass, a.h_out, a.rho, a.drhodh, a.fgrad, a.nngb_out, a.iters);
+        a.keep[u] = 0;
+        if (!st.converged) atomicAdd(a.nfail, 1);
+        return;
     }
     a.lo[r] = lo;
     a.hi[r] = hi;
-    a.h64[r] = hn;
-    a.pfix[r].w = __float_as_uint((float)hn);
+    a.h64[r] = st.hn;
+    a.pfix[r].w = __float_as_uint((float)st.hn);
     a.keep[u] = 1;
 }
 
@@ -2058,6 +2198,137 @@ __global__ void k_hsml_update(UpdateArgs a) {
     if (u >= a.nu) return;
     const int r = a.U[u];
     hsml_update(a, u, r, a.s0[r], a.s1[r], a.n[r]);
+}
+
+// Passes 2, 3, ... of the recycled iteration, one thread per unconverged particle: while
+// its h stays within the widened radius h_w of its pass-1 candidate list, the density
+// sums at h are those of the list's members inside h (the list holds every particle
+// within h_w), so the particle iterates on its own list without a tree walk.  The
+// decisions are the exact ones of the grouped kernel (FP32 on exact fixed-point
+// differences, FP64 re-test in the band).  A particle whose h leaves h_w, or whose list
+// overflowed, is flagged for a walk pass (keep = 1) with its iterate and bracket stored.
+__global__ void __launch_bounds__(128) k_list_iterate(ListIterArgs a) {
+    const int lane = threadIdx.x & 31;
+    LocalCounters lc;
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < a.nu) {
+        const int r = a.U[u];
+        const int slot = a.lslot[r];
+        const int4 rec = a.lrec[slot];
+        const double hw = a.lhw[slot];
+        int pass = a.npass[r];
+        double h = a.h64[r], lo = a.lo[r], hi = a.hi[r];
+        const uint4 P = a.pfix_in[r];
+        const float4 O = a.poff[r];
+        const float m = O.w;
+        bool walk = rec.w == 0;
+        while (!walk) {
+            if (!(h <= hw)) {
+                walk = true;
+                break;
+            }
+            ++pass;
+            const float hf = (float)h;
+            const float h2 = (float)(h * h);
+            const float h2lo = h2 * (1.0f - 3.0f * kBandRel), h2hi = h2 * (1.0f + 3.0f * kBandRel);
+            const float hinv = 1.0f / hf;
+            const double hh = __dmul_rn(h, h);
+            const int lsub = kListCap / rec.z;
+            float S0 = 0.0f, C0 = 0.0f, S1 = 0.0f, C1 = 0.0f, p0 = 0.0f, p1 = 0.0f;
+            int n = 0;
+            for (int sl = 0; sl < rec.z; ++sl) {
+                const int cnt = sl == 0 ? (rec.x & 0xffff) : sl == 1 ? (rec.x >> 16) : sl == 2 ? (rec.y & 0xffff)
+                                                                                               : (rec.y >> 16);
+                // sub-lists start at multiples of 4 entries (kListCap / S, S in {1, 2, 4}):
+                // four entries per step, read as one int4 and gathered together, so that a
+                // thread keeps eight candidate loads in flight
+                const int4* L4 = reinterpret_cast<const int4*>(a.list + (int64_t)slot * kListCap + sl * lsub);
+                for (int k0 = 0; k0 < cnt; k0 += 4) {
+                    const int4 J4 = L4[k0 >> 2];
+                    const int jj[4] = {J4.x, J4.y, J4.z, J4.w};
+                    uint4 Q[4];
+                    float4 Oj[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (k0 + e < cnt) {
+                            Q[e] = __ldg(a.pfix_in + jj[e]);
+                            Oj[e] = __ldg(a.poff + jj[e]);
+                        }
+                    }
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        if (k0 + e >= cnt) break;
+                        const float dx = fix_diff(Q[e].x, Oj[e].x, P.x, O.x);
+                        const float dy = fix_diff(Q[e].y, Oj[e].y, P.y, O.y);
+                        const float dz = fix_diff(Q[e].z, Oj[e].z, P.z, O.z);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        bool in = r2 < h2lo;
+                        if (!in && r2 < h2hi) {
+                            in = exact_r2(a.xd, a.yd, a.zd, r, jj[e]) < hh;
+                            lc.retests++;
+                        }
+                        if (!in) continue;
+                        ++n;
+                        const float q = r2 * rsqrtf(fmaxf(r2, 1.0e-30f)) * hinv;
+                        float w, dw;
+                        m4_shape(q, w, dw);
+                        p0 = fmaf(Oj[e].w, w, p0);
+                        p1 = fmaf(Oj[e].w, fmaf(q, dw, 3.0f * w), p1);
+                    }
+                    if ((k0 & 15) == 12) {
+                        kahan_add(S0, C0, p0);
+                        kahan_add(S1, C1, p1);
+                        p0 = p1 = 0.0f;
+                    }
+                }
+            }
+            kahan_add(S0, C0, p0);
+            kahan_add(S1, C1, p1);
+            lc.pairs += n;
+            const float s0 = S0 - C0, s1 = S1 - C1;
+            const HsmlStep st = hsml_next(h, m, s0, s1, a.nngb, a.tol, true, pass, a.max_iter, lo, hi);
+            if (st.finish) {
+                hsml_write(a.perm[r], h, s0, s1, n, pass, a.h_out, a.rho, a.drhodh, a.fgrad, a.nngb_out, a.iters);
+                if (!st.converged) atomicAdd(a.nfail, 1);
+                break;
+            }
+            h = st.hn;
+        }
+        // (positions are read through the read-only path: pfix is not written here; its
+        // FP32 copy of h is not read during the density call, and the hydro and velocity
+        // entry points rewrite it from the caller's h)
+        a.keep[u] = walk ? 1 : 0;
+        a.npass[r] = pass;
+        a.h64[r] = h;
+        a.lo[r] = lo;
+        a.hi[r] = hi;
+    }
+    // only pairs and re-tests are counted: the lists are not tree-search candidates
+    int mp = u < a.nu ? a.npass[a.U[u]] : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        lc.pairs += __shfl_xor_sync(0xffffffffu, lc.pairs, o);
+        lc.retests += __shfl_xor_sync(0xffffffffu, lc.retests, o);
+        mp = max(mp, __shfl_xor_sync(0xffffffffu, mp, o));
+    }
+    if (lane == 0) {
+        if (lc.pairs) atomicAdd(&a.ctr->pairs, lc.pairs);
+        if (lc.retests) atomicAdd(&a.ctr->retests, lc.retests);
+        if (a.max_pass) atomicMax(a.max_pass, mp);
+    }
+}
+
+int launch_list_iterate(const ListIterArgs& a, cudaStream_t s) {
+    if (a.nu <= 0) return SPHGRP_OK;
+    static bool configured = false;
+    if (!configured) {
+        // no shared memory: all of it as L1, which holds the candidates that neighbouring
+        // particles gather
+        cudaFuncSetAttribute(k_list_iterate, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        configured = true;
+    }
+    k_list_iterate<<<blocks_for(a.nu, 128), 128, 0, s>>>(a);
+    note_launch();
+    return check_cuda(cudaGetLastError(), "list iteration");
 }
 
 int launch_hsml_update(const UpdateArgs& a, cudaStream_t s) {

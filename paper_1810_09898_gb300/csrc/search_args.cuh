@@ -9,7 +9,14 @@ namespace sphgrp {
 enum Mode { kAcc = 0, kCount = 1, kFill = 2, kSupCount = 3, kSupFill = 4 };
 
 // pair loops of the search kernels: SPHGRP_DENSITY (0), SPHGRP_HYDRO (1) and the adjoints
-enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3, kKindVelocity = 4 };
+enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3, kKindVelocity = 4,
+            kKindDensityList = 5 };
+
+// Candidate lists of the recycled smoothing-length iteration: every member of a pass-1
+// group keeps the candidates of the group's superset that lie within its widened radius
+// h_w = widen * h, in up to four sub-lists (one per slice of the member layout) of
+// kListCap / S entries.  A record per list slot {c0 | c1 << 16, c2 | c3 << 16, S, valid}.
+constexpr int kListCap = 192;
 
 // smoothing-length update of the density passes (per unconverged particle, FP64)
 struct UpdateArgs {
@@ -37,6 +44,38 @@ struct UpdateArgs {
     int32_t* iters;
     int iterate;
     int* nfail;
+    int32_t* npass;       // optional: passes made so far per rank (null: every particle is at pass it)
+};
+
+// passes 2, 3, ... of the recycled iteration over the members' candidate lists
+struct ListIterArgs {
+    const int32_t* U;     // unconverged work list (ranks)
+    int nu;
+    int max_iter;
+    double nngb, tol;
+    const uint4* pfix_in;   // positions (read); pfix.w is written through pfix
+    uint4* pfix;
+    const float4* poff;
+    const double *xd, *yd, *zd;
+    double* h64;
+    double* lo;
+    double* hi;
+    const int32_t* lslot;   // rank -> list slot
+    const int4* lrec;       // list records
+    const double* lhw;      // widened h of every slot
+    const int32_t* list;    // kListCap entries per slot
+    int32_t* npass;
+    int* max_pass;          // largest pass count reached on a list
+    int32_t* keep;          // 1: the member needs a walk pass (h beyond h_w or a list overflowed)
+    const int32_t* perm;
+    double* h_out;
+    float* rho;
+    float* drhodh;
+    float* fgrad;
+    int32_t* nngb_out;
+    int32_t* iters;
+    int* nfail;
+    DevCounters* ctr;
 };
 
 struct SearchArgs {
@@ -85,6 +124,12 @@ struct SearchArgs {
     int64_t* x_cnt;
     int32_t* x_idx;
     int64_t x_cap;
+    // candidate lists of the recycled iteration (kind kKindDensityList)
+    int32_t* o_list;      // kListCap entries per slot; slot = pass-1 work-list index
+    int4* o_lrec;
+    double* o_lhw;
+    int32_t* o_lslot;     // rank -> slot
+    double list_widen;    // h_w / h
     // hydro constants
     float alpha, beta, eps;
     // bookkeeping
@@ -116,6 +161,7 @@ struct IterArgs {
 
 int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_count, cudaStream_t s);
 int launch_hsml_update(const UpdateArgs& a, cudaStream_t s);
+int launch_list_iterate(const ListIterArgs& a, cudaStream_t s);
 // persistent launches over a device-side group count (a.ngroups_dev), graph-capturable
 int launch_search_dev(const SearchArgs& a, int kind, int max_g, int sm_count, cudaStream_t s);
 int launch_density_iter(const SearchArgs& a, const IterArgs& it, int max_g, int sm_count, cudaStream_t s);

@@ -132,6 +132,14 @@ struct Ctx {
     float4* adj1 = nullptr;        // hydro adjoint {vb, mb of the implicit h}
     float4* adj2 = nullptr;        // hydro adjoint {hb, rhob, Ab, n}
     float4* adj3 = nullptr;        // density adjoint {xb, mb}
+    // recycled smoothing-length iteration (allocated by the first call that uses it; a
+    // failed allocation falls back to walk passes)
+    int32_t* lst = nullptr;        // candidate lists, kListCap entries per slot
+    int4* lrec = nullptr;          // list records
+    double* lhw = nullptr;         // widened h per slot
+    int32_t* lslot = nullptr;      // rank -> slot
+    int32_t* npass = nullptr;      // passes made per rank
+    bool lst_failed = false;
     // tree
     Tree tree;
     // counters and error flags

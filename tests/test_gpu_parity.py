@@ -168,10 +168,14 @@ def test_density_fixed_h(clu, mode, g):
 
 
 @pytest.mark.parametrize("dist,n,cfg", [("uniform", 32768, 1), ("clustered", 24001, 2)])
-@pytest.mark.parametrize("mode,g,iteration", [(0, 1, 0), (1, 32, 0), (1, 16, 1), (1, 64, 1)])
-def test_density_iteration(cuda_device, dist, n, cfg, mode, g, iteration):
+@pytest.mark.parametrize("mode,g,iteration,widen", [(0, 1, 0, 1.1), (1, 32, 0, 1.1), (1, 16, 1, 1.1), (1, 64, 1, 1.1),
+                                                  (1, 16, 2, 1.1), (1, 32, 2, 1.1), (1, 8, 2, 1.0), (1, 16, 2, 2.0),
+                                                  (1, 64, 2, 1.1)])
+def test_density_iteration(cuda_device, dist, n, cfg, mode, g, iteration, widen):
+    # iteration 2 (recycled): widen 1.0 sends every particle whose h grows to a walk pass,
+    # widen 2.0 overflows lists (walk passes as well), g = 64 keeps no lists at all
     d = dataset(dist, n, cfg)
-    G = Gpu(d["pos"], d["m32"], iteration=iteration)
+    G = Gpu(d["pos"], d["m32"], iteration=iteration, iter_widen=widen)
     h0 = np.full(n, d["h0"])
     act = np.arange(n, dtype=np.int32)
     out = G.density(act, h0, 1, mode, g)
@@ -367,6 +371,7 @@ def test_rejects_bad_parameters(cuda_device):
 
     for bad in ({"stack_shared": 16}, {"stack_shared": 512}, {"group_mode": 5}, {"group_mode": 1, "group_f": 0.0},
                 {"iteration": 3}, {"leaf_size": 0}, {"group_centre": 4}, {"max_iter": 0},
+                {"iter_widen": 0.99}, {"iter_widen": 2.5},
                 {"group_mode": 2, "group_level": 0}, {"group_mode": 2, "group_level": 22}):
         with pytest.raises(sg.SphgrpError, match="EINVAL"):
             sg.Context(100, **bad)
