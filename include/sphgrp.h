@@ -267,7 +267,9 @@ int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
  * every pair term from the staged candidates; no pair list is stored.
  * h:     device, n FP64, 0 < h < 0.5;
  * vel:   device, n x 3 FP32;  u: device, n FP32 (u >= 0);
- * g_acc: device, n x 3 FP32 (dL/da);  g_rho: device, n FP32 (dL/drho), or NULL for 0;
+ * g_acc: device, n x 3 FP32 (dL/da), or NULL for 0: then only the density term is
+ *        differentiated, the hydro-adjoint loop is skipped and vel and u may be NULL;
+ * g_rho: device, n FP32 (dL/drho), or NULL for 0 (not both NULL);
  * g_pos, g_vel: device, n x 3 FP32;  g_m: device, n FP32 -- outputs in original
  *        order, each may be NULL (not all three).
  * group_size in [1, 128].  The first call allocates 100 bytes per particle of n_max of
@@ -388,10 +390,12 @@ int sphgrp_get_launch_log(sphgrp_ctx* ctx, int cap, int64_t* members, int64_t* c
  * perm_out: device, n int32, receives rank -> original index (also used as scratch).
  * No context is involved and nothing is kept for later calls.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the one
- * array: calls whose work overlaps on the GPU (different streams, or different host
- * threads without ordering) race and give wrong results; serialise them.  Returns
- * after synchronising the stream (the range check is read back). */
+ * current and keeps it for the life of the process: this assumes one primary context
+ * per device for that time (do not call it after a cudaDeviceReset of the device).
+ * All calls share the one array: calls whose work overlaps on the GPU (different
+ * streams, or different host threads without ordering) race and give wrong results;
+ * serialise them.  Every call synchronises the stream to read back the range check, so
+ * it must never be called while its stream is being captured into a graph. */
 #define SPHGRP_STATIC_SORT_MAX_N (1 << 19)
 int sphgrp_sfc_keys_sort_static(int64_t n, const double* pos, uint64_t* keys_out,
                                 int32_t* perm_out, cudaStream_t stream);

@@ -26,6 +26,7 @@ from .binding import (  # noqa: F401
     Context,
     kernel_launches,
     library_path,
+    sfc_keys_sort_static,
     load_library,
 )
 from .autograd import SPHForces, sph_forces  # noqa: F401,E402

@@ -49,6 +49,9 @@ class SPHForces(torch.autograd.Function):
         dudt = torch.empty(n, dtype=torch.float32, device=dev)
         sph_ctx.hydro_force(active, h_d, rho, fgrad, vel_f, u_f, GROUPED, group_size, acc, dudt)
         fctx.save_for_backward(pos_d, vel_f, m_f, u_f, h_d)
+        # an output the loss does not use gives None (not zeros): a loss of rho alone
+        # skips the hydro adjoint
+        fctx.set_materialize_grads(False)
         fctx.sph_ctx = sph_ctx
         fctx.group_size = group_size
         fctx.dtypes = (pos.dtype, vel.dtype, m.dtype)
@@ -62,12 +65,13 @@ class SPHForces(torch.autograd.Function):
         dev = pos_d.device
         # the context may have served other calls since the forward: rebuild its state
         _build(sph_ctx, pos_d, m_f)
-        if g_acc is None:
-            g_acc = torch.zeros((n, 3), dtype=torch.float32, device=dev)
-        g_acc = g_acc.to(torch.float32).contiguous()
+        if g_acc is not None:
+            g_acc = g_acc.to(torch.float32).contiguous()
         if g_rho is not None:
             g_rho = g_rho.to(torch.float32).contiguous()
         need_x, need_v, need_m = fctx.needs_input_grad[:3]
+        if g_acc is None and g_rho is None:
+            return (None,) * 7
         gx = torch.empty((n, 3), dtype=torch.float32, device=dev) if need_x else None
         gv = torch.empty((n, 3), dtype=torch.float32, device=dev) if need_v else None
         gm = torch.empty(n, dtype=torch.float32, device=dev) if need_m else None

@@ -111,6 +111,17 @@ class Stats(ctypes.Structure):
 _lib = None
 
 
+def sfc_keys_sort_static(pos, keys_out, perm_out):
+    """sphgrp_sfc_keys_sort_static: keys and stable order without any device allocation
+    (scratch in the library's fixed device array; n <= 2^19).  pos: n x 3 float64,
+    keys_out: n int64 (the unsigned keys' bits), perm_out: n int32, all on the current
+    device.  Synchronises the current stream."""
+    n = pos.shape[0]
+    L = load_library()
+    _check(L.sphgrp_sfc_keys_sort_static(n, _arg(pos, "pos", _F64, 3 * n), _arg(keys_out, "keys_out", _I64, n),
+                                         _arg(perm_out, "perm_out", _I32, n), _stream()))
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -310,8 +321,9 @@ class Context:
     # -- a9
     def backward(self, h, vel, u, g_acc, g_rho, group_size, g_pos=None, g_vel=None, g_m=None):
         n = self.n
-        _check(self._L.sphgrp_backward(self._h, _arg(h, "h", _F64, n), _arg(vel, "vel", _F32, 3 * n),
-                                       _arg(u, "u", _F32, n), _arg(g_acc, "g_acc", _F32, 3 * n),
+        no_acc = g_acc is None
+        _check(self._L.sphgrp_backward(self._h, _arg(h, "h", _F64, n), _arg(vel, "vel", _F32, 3 * n, no_acc),
+                                       _arg(u, "u", _F32, n, no_acc), _arg(g_acc, "g_acc", _F32, 3 * n, True),
                                        _arg(g_rho, "g_rho", _F32, n, True), int(group_size),
                                        _arg(g_pos, "g_pos", _F32, 3 * n, True),
                                        _arg(g_vel, "g_vel", _F32, 3 * n, True), _arg(g_m, "g_m", _F32, n, True),

@@ -76,7 +76,7 @@ __global__ void k_bwd_chain(int64_t n, const int32_t* __restrict__ perm, const d
     const double h = d.h, rho = d.rho, rh = d.rh, f = d.f;
     const double sigma = 8.0 / (kPi * h * h * h);
     const double rhh = sigma / (h * h) * (double)s2[r];
-    const double ui = (double)u[i];
+    const double ui = u ? (double)u[i] : 0.0;   // no u: no acceleration term (Abar = 0)
     const double A = f * (gamma - 1.0) * ui / rho;
     const float4 G = adj2[r];   // {hbar, rhobar, Abar, -} of the hydro loop
     double rbar = (double)G.y + (g_rho ? (double)g_rho[i] : 0.0);
@@ -167,7 +167,11 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     if (group_size < 1 || group_size > 128) return set_error(SPHGRP_EINVAL, "group_size must be in [1, 128]");
     const int64_t n = c->n;
     int rc = SPHGRP_OK;
-    if (!h || !vel || !u || !g_acc) return set_error(SPHGRP_EINVAL, "null h, vel, u or g_acc");
+    // g_acc NULL: L = sum g_rho . rho alone; the hydro adjoint is not run, vel and u are
+    // not read
+    const bool with_acc = g_acc != nullptr;
+    if (!h || (with_acc && (!vel || !u))) return set_error(SPHGRP_EINVAL, "null h, or null vel or u with g_acc");
+    if (!with_acc && !g_rho) return set_error(SPHGRP_EINVAL, "neither g_acc nor g_rho: nothing to differentiate");
     if (!g_pos && !g_vel && !g_m) return set_error(SPHGRP_EINVAL, "no gradient requested");
     if ((rc = backward_buffers(c))) return rc;
     reset_flags(c, s);
@@ -197,18 +201,25 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     rc = launch_search(ad, kKindDensity, kAcc, true, c->sm_count, s);
     timer_end(c, s, nu);
     if (rc) return rc;
-    if ((rc = launch_bwd_prep(c, vel, u, g_acc, c->hyd0, c->hyd1, s))) return rc;
-    // 2. adjoint of sum w . a over every hydro pair
-    SearchArgs ah = a;
-    ah.o_adj0 = c->adj0;
-    ah.o_adj1 = c->adj1;
-    ah.o_adj2 = c->adj2;
-    timer_begin(c, s);
-    rc = launch_search(ah, kKindHydroAdj, kAcc, true, c->sm_count, s);
-    timer_end(c, s, nu);
-    if (rc) return rc;
+    if (with_acc) {
+        if ((rc = launch_bwd_prep(c, vel, u, g_acc, c->hyd0, c->hyd1, s))) return rc;
+        // 2. adjoint of sum w . a over every hydro pair
+        SearchArgs ah = a;
+        ah.o_adj0 = c->adj0;
+        ah.o_adj1 = c->adj1;
+        ah.o_adj2 = c->adj2;
+        timer_begin(c, s);
+        rc = launch_search(ah, kKindHydroAdj, kAcc, true, c->sm_count, s);
+        timer_end(c, s, nu);
+        if (rc) return rc;
+    } else {
+        // no acceleration term: its adjoints are zero
+        cudaMemsetAsync(c->adj0, 0, n * sizeof(float4), s);
+        cudaMemsetAsync(c->adj1, 0, n * sizeof(float4), s);
+        cudaMemsetAsync(c->adj2, 0, n * sizeof(float4), s);
+    }
     // 3. per particle: A, f, rho, h and the implicit h
-    if ((rc = launch_bwd_chain(c, u, g_rho, s))) return rc;
+    if ((rc = launch_bwd_chain(c, with_acc ? u : nullptr, g_rho, s))) return rc;
     // 4. adjoint of rho and rho' at fixed h over every density pair
     SearchArgs aa = a;
     aa.o_adj3 = c->adj3;
@@ -218,7 +229,7 @@ extern "C" int sphgrp_backward(sphgrp_ctx* ctx, const double* h, const float* ve
     if (rc) return rc;
     if ((rc = launch_bwd_combine(c, g_pos, g_vel, g_m, s))) return rc;
     rc = check_cuda(cudaGetLastError(), "backward kernels");
-    c->last.walks = 3 * (int64_t)a.ngroups;
-    c->last.members = 3 * (int64_t)nu;
+    c->last.walks = (with_acc ? 3 : 2) * (int64_t)a.ngroups;
+    c->last.members = (with_acc ? 3 : 2) * (int64_t)nu;
     return finish(c, s, rc);
 }

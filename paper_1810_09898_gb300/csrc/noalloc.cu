@@ -15,8 +15,8 @@
 
 namespace sphgrp {
 int sort_keys_scratch(int64_t n, const double* pos, uint64_t* keys_out, int32_t* perm_out,
-                      uint64_t* keys_alt, int32_t* perm_alt, uint32_t* hist, int32_t* scan_aux,
-                      int64_t scan_aux_words, unsigned* err, cudaStream_t s);
+                      uint64_t* keys_alt, int32_t* perm_alt, uint32_t* hist, int64_t hist_words,
+                      int32_t* scan_aux, int64_t scan_aux_words, unsigned* err, cudaStream_t s);
 }
 
 using namespace sphgrp;
@@ -26,7 +26,7 @@ namespace {
 constexpr int64_t kMaxN = SPHGRP_STATIC_SORT_MAX_N;
 constexpr size_t kAlign = 256;
 constexpr size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-constexpr size_t kHistWords = 256 * ((kMaxN + 2047) / 2048);
+constexpr size_t kHistWords = 256 * ((kMaxN + kSortTile - 1) / kSortTile);   // one row per sort tile
 constexpr size_t kAuxWords = 4096;
 constexpr size_t kOffErr = 0;
 constexpr size_t kOffKeys = round_up(kOffErr + sizeof(unsigned));
@@ -43,7 +43,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_base[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device and
+// kept for the process: it assumes the device keeps one primary context for that time
+// (a cudaDeviceReset that destroys it leaves a stale address behind).
 int scratch_base(unsigned char** out) {
     int dev = 0;
     int rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
@@ -76,7 +78,8 @@ extern "C" int sphgrp_sfc_keys_sort_static(int64_t n, const double* pos, uint64_
     if (rc) return rc;
     rc = sort_keys_scratch(n, pos, keys_out, perm_out, reinterpret_cast<uint64_t*>(base + kOffKeys),
                            reinterpret_cast<int32_t*>(base + kOffPerm), reinterpret_cast<uint32_t*>(base + kOffHist),
-                           reinterpret_cast<int32_t*>(base + kOffAux), (int64_t)kAuxWords, err, stream);
+                           (int64_t)kHistWords, reinterpret_cast<int32_t*>(base + kOffAux), (int64_t)kAuxWords,
+                           err, stream);
     if (rc) return rc;
     unsigned flag = 0;
     rc = check_cuda(cudaMemcpyAsync(&flag, err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream), "read error flag");

@@ -198,9 +198,6 @@ int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64
 // the input order (stability).
 // ---------------------------------------------------------------------------------
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kSortWarps = kSortThreads / 32;
 
 __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
@@ -463,13 +460,14 @@ int sort_keys_boxed(Ctx* c, int64_t n, const double* pos, const int64_t* box_off
 // The same keys + stable radix sort on caller-provided buffers: the sorted keys and
 // the permutation end in keys_out / perm_out (which also serve as one ping-pong pair;
 // eight passes return to them), keys_alt / perm_alt are the other pair, hist holds
-// 256 * ceil(n / 2048) counters and scan_aux the scan's block sums (scan_aux_words
-// entries).  err receives the range-check flag.  No allocation.
+// hist_words >= 256 * ceil(n / kSortTile) counters and scan_aux the scan's block sums
+// (scan_aux_words entries).  err receives the range-check flag.  No allocation.
 int sort_keys_scratch(int64_t n, const double* pos, uint64_t* keys_out, int32_t* perm_out,
-                      uint64_t* keys_alt, int32_t* perm_alt, uint32_t* hist, int32_t* scan_aux,
-                      int64_t scan_aux_words, unsigned* err, cudaStream_t s) {
+                      uint64_t* keys_alt, int32_t* perm_alt, uint32_t* hist, int64_t hist_words,
+                      int32_t* scan_aux, int64_t scan_aux_words, unsigned* err, cudaStream_t s) {
     const int nblocks = (int)((n + kSortTile - 1) / kSortTile);
     const int64_t nh = (int64_t)256 * nblocks;
+    if (nh > hist_words) return set_error(SPHGRP_EOVERFLOW, "histogram scratch too small");
     if (scan_aux_need(nh) > scan_aux_words) return set_error(SPHGRP_EOVERFLOW, "scan scratch too small");
     k_keys<<<blocks_for(n, 256), 256, 0, s>>>(n, pos, keys_out, err);
     note_launch();

@@ -212,11 +212,35 @@ __device__ __forceinline__ double exact_r2(const double* xd, const double* yd, c
 }
 
 // Relative half-width of the FP32 decision band: a pair whose FP32 r^2 lies within
-// kBandRel * (2|m| + H)^2 + kBandRel * H^2 of the threshold H^2 is re-decided in FP64.
-// (Bound: each FP32 relative coordinate carries at most one ulp of its magnitude,
-// the difference and the three-term sum add at most a few more; the total is below
-// 2^-20 (|p| + |m|)^2 with |p| <= |m| + r near the threshold.  2^-18 leaves a factor 4.)
+// 3 kBandRel H^2 + 8 kBandRel |m|^2 of the threshold H^2 (H = h, or max(h_i, h_j) for the
+// symmetric criterion; m = the member's coordinate relative to the group centre) is
+// re-decided from the FP64 positions.  Error bound, u = 2^-24 the FP32 unit roundoff,
+// D the exact distance, P and M the exact centre-relative candidate and member
+// coordinates, all in box units:
+//  * coordinates: p = (float(int32(X - C)) + off) 2^-32 rounds at most twice (the int32
+//    conversion above 2^24 units and the sum), the offset once at 2^-25 units: each
+//    component is within 2u |P| + 2^-57 of the exact one (same for m);
+//  * difference form (phase B, r^2 = fma(dx, dx, fma(dy, dy, dz dz)), d = p - m, also
+//    after the wrap d - rint(d), which is exact): |d - D| <= u |D| + 2u (|P| + |M|) per
+//    component, so |r^2 - D^2| <= 2 |D| |d - D| + 3u D^2 <= 9u D^2 + 4u D (|P| + |M|);
+//    with |P| <= D + |M| near D = H this is <= 13u H^2 + 4u |M|^2 + 8u H |M|
+//    <= 17u H^2 + 8u |M|^2, i.e. 0.27 kBandRel H^2 + 0.5 kBandRel |M|^2;
+//  * dot form (phase A, t = |p|^2 - 2 p.m against H^2 - |m|^2 by three FMAs, |p|^2 and
+//    |m|^2 rounded once per term): its own roundings add 6u |p|^2 + 6u |p||m| + 4u |m|^2
+//    + u H^2 to the coordinate errors above, <= 26u H^2 + 29u |M|^2 in all, i.e.
+//    0.41 kBandRel H^2 + 0.45 kBandRel |M|^2;
+//  * H^2 in FP32 from the FP64 square (and h_j^2 from the FP32 h_j): within 3u H^2.
+// The band (3 kBandRel H^2 + 8 kBandRel |m|^2) exceeds every bound at least 6-fold in
+// the H^2 term and 16-fold in the |m|^2 term, for members at any distance from the
+// centre and for wrapped groups.  Members farther than kPreciseReach h from the centre
+// take their pair physics (not their decisions) from exact fixed-point differences.
 constexpr float kBandRel = 3.814697265625e-06f;  // 2^-18
+
+// Radix sort tile (sort.cu): 256 threads x 8 keys; the digit histograms take 256
+// counters per tile.
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
 
 // launch helpers
 // at least one block: kernels bound-check their index, and an empty grid is a launch error

@@ -11,6 +11,14 @@ import oracle
 import sphgen
 
 
+# The GPU accepts a smoothing length when its own FP32 density gives |N_eff - 64| <= 2.
+# The oracle re-evaluates N_eff = 4 pi h^3 rho / (3 m) at that h in FP64; the two rho
+# differ by at most the density tolerance (rel 1e-5), so a particle accepted right at the
+# edge of the band can sit up to (64 + 2) * 1e-5 = 6.6e-4 outside it by the oracle's count.
+RHO_TOL = 1e-5
+NEFF_TOL = 2.0 + (64.0 + 2.0) * RHO_TOL
+
+
 @functools.lru_cache(maxsize=None)
 def dataset(kind: str, n: int, config: int = 1):
     d = sphgen.make(kind, n, config=config)

@@ -182,3 +182,36 @@ def test_backward_rejects_bad_calls(cuda_device):
     with pytest.raises(sg.SphgrpError, match="EINVAL"):
         g.ctx.backward(bad, z, z, z, None, 16, z)
     ctx.close()
+
+
+@pytest.mark.parametrize("kind,n,cfg", [("uniform", 32768, 1), ("clustered", 24001, 4)])
+def test_density_only_backward(cuda_device, kind, n, cfg):
+    """g_acc = NULL: the gradient of sum s . rho alone, without the hydro-adjoint loop
+    (vel and u not passed), against the oracle's gradient of the same loss (w = 0)."""
+    d, m, h, _, s = _problem(kind, n, cfg)
+    _, ox, ov, om = oracle.loss_grad(d["pos"], d["vel32"].astype(np.float64), m, d["u32"].astype(np.float64), h,
+                                     np.zeros((n, 3)), s.astype(np.float64))
+    assert np.all(ov == 0.0)
+    g = Gpu(d["pos"], d["m32"])
+    torch = g.torch
+    gx = torch.full((n, 3), np.nan, dtype=torch.float32, device=g.dev)
+    gv = torch.full((n, 3), np.nan, dtype=torch.float32, device=g.dev)
+    gm = torch.full((n,), np.nan, dtype=torch.float32, device=g.dev)
+    g.ctx.backward(g.t(h, torch.float64), None, None, None, g.t(s), 16, gx, gv, gm)
+    st = g.ctx.stats()
+    _compare(gx.cpu().numpy(), ox, "dL/dx")
+    _compare(gm.cpu().numpy(), om, "dL/dm")
+    assert np.all(gv.cpu().numpy() == 0.0)
+    assert st["search_launches"] == 2, st   # density sums and density adjoint only
+    # the autograd Function takes the same path when the loss uses rho alone
+    import paper_1810_09898_gb300 as sg
+
+    pos = torch.tensor(d["pos"], device=g.dev, requires_grad=True)
+    mm = torch.as_tensor(d["m32"], device=g.dev).clone().requires_grad_(True)
+    _, rho = sg.sph_forces(g.ctx, pos, g.t(d["vel32"]), mm, g.t(d["u32"]), g.t(h, torch.float64), 16)
+    (g.t(s) * rho).sum().backward()
+    assert g.ctx.stats()["search_launches"] == 2
+    _compare(pos.grad.cpu().numpy(), ox, "autograd dL/dx")
+    _compare(mm.grad.cpu().numpy(), om, "autograd dL/dm")
+    with pytest.raises(sg.SphgrpError, match="EINVAL"):
+        g.ctx.backward(g.t(h, torch.float64), None, None, None, None, 16, gx, gv, gm)

@@ -14,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+from gpu_common import NEFF_TOL
 import sphgen
 
 pytestmark = pytest.mark.gpu
@@ -105,6 +106,13 @@ def test_batch_density_per_box(cuda_device):
     b = _case()
     out, stats = _forward()
     assert stats["walks"] > 0 and stats["pairs"] > 0
+    _check_density_per_box(b, out)
+
+
+def _check_density_per_box(b, out):
+    """Every box's active particles against the oracle: h converged by the oracle's own
+    arithmetic, counts bit-exact, rho and f within the bars, h equal to the oracle's
+    iterate to 1e-5 for 99.9% of them; inactive particles keep their h."""
     for k, s in _boxes(b):
         act = np.flatnonzero(b["active"][s]).astype(np.int32)
         pos, m = b["pos"][s], b["m32"][s].astype(np.float64)
@@ -114,7 +122,7 @@ def test_batch_density_per_box(cuda_device):
         assert np.array_equal(h[inact], b["h0"][s][inact])
         chk = oracle.density(pos, m, h, targets=act)
         neff = 4.0 * np.pi / 3.0 * h[act] ** 3 * chk["rho"] / m[act]
-        assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3), k
+        assert np.all(np.abs(neff - 64.0) <= NEFF_TOL), k
         assert np.array_equal(out["nngb"][s][act], chk["nngb"]), k
         assert np.max(np.abs(out["rho"][s][act] / chk["rho"] - 1.0)) <= RHO_TOL, k
         assert np.max(np.abs(out["fgrad"][s][act] / chk["f"] - 1.0)) <= 1e-4, k
@@ -230,15 +238,10 @@ def test_batch_tune_and_config(cuda_device):
         assert cfg["group_size"] in (4, 8, 16, 32, 64)
         assert cfg["max_slices"] in (1, 2, 4)
         assert cfg["group_split"] in (1.5, 2.0, 4.0)
-    # a tuned run is still a correct run
+    # a tuned run is still a correct run, by the oracle
     io.reset()
     B.run(io.a, graph=True)
-    out = io.host()
-    ref, _ = _forward()
-    for k, s in _boxes(b):
-        act = np.flatnonzero(b["active"][s])
-        assert np.array_equal(out["nngb"][s][act], ref["nngb"][s][act]) or \
-            np.mean(np.abs(out["h"][s][act] / ref["h"][s][act] - 1.0) <= 1e-5) > 0.999
+    _check_density_per_box(b, io.host())
     for cls in (0, 1):
         cfg = B.get_config(cls)
         assert cfg["tuned_pass_ms"] > 0.0 and cfg["tuned_members"] == int(
@@ -307,7 +310,7 @@ def test_batch_single_box_equals_context(cuda_device):
     assert np.max(np.abs(rho.cpu().numpy() / out["rho"] - 1.0)) <= 1e-6
     ref = oracle.density(d["pos"], m32.astype(np.float64), out["h"])
     neff = 4.0 * np.pi / 3.0 * out["h"] ** 3 * ref["rho"] / m32
-    assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3)
+    assert np.all(np.abs(neff - 64.0) <= NEFF_TOL)
     ctx.close()
 
 
@@ -362,6 +365,6 @@ def test_batch_many_small_boxes(cuda_device):
         m = b["m32"][s].astype(np.float64)
         chk = oracle.density(b["pos"][s], m, out["h"][s], targets=act)
         neff = 4.0 * np.pi / 3.0 * out["h"][s][act] ** 3 * chk["rho"] / m[act]
-        assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3), k
+        assert np.all(np.abs(neff - 64.0) <= NEFF_TOL), k
         assert np.array_equal(out["nngb"][s][act], chk["nngb"]), k
         assert np.max(np.abs(out["rho"][s][act] / chk["rho"] - 1.0)) <= RHO_TOL, k

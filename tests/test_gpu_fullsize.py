@@ -17,7 +17,7 @@ import pytest
 
 import oracle
 import sphgen
-from gpu_common import Gpu, active_runs
+from gpu_common import NEFF_TOL, Gpu, active_runs
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +52,7 @@ def _check_density(d, out, sample):
     rel = np.abs(out["rho"][sample] / chk["rho"] - 1.0)
     assert rel.max() <= RHO_TOL, (int(sample[np.argmax(rel)]), float(rel.max()))
     neff = 4.0 * np.pi / 3.0 * out["h"][sample] ** 3 * chk["rho"] / m[sample]
-    assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3)
+    assert np.all(np.abs(neff - 64.0) <= NEFF_TOL)
 
 
 def _check_hydro(d, h, rho32, f32, hyd, sample):
@@ -182,7 +182,7 @@ def test_batch_fullsize_sampled_boxes(boxes):
         assert np.array_equal(out["nngb"][s][sample], chk["nngb"]), k
         assert np.max(np.abs(out["rho"][s][sample] / chk["rho"] - 1.0)) <= RHO_TOL, k
         neff = 4.0 * np.pi / 3.0 * h[sample] ** 3 * chk["rho"] / m[sample]
-        assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3), k
+        assert np.all(np.abs(neff - 64.0) <= NEFF_TOL), k
         ref = oracle.hydro(pos, b["vel"][s].astype(np.float32).astype(np.float64), m, h,
                            out["rho"][s].astype(np.float64), out["fgrad"][s].astype(np.float64),
                            b["u"][s].astype(np.float32).astype(np.float64), targets=sample)

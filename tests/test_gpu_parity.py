@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import Gpu, active_runs, converged, csr_sorted_lists, dataset
+from gpu_common import NEFF_TOL, Gpu, active_runs, converged, csr_sorted_lists, dataset
 
 pytestmark = pytest.mark.gpu
 
@@ -184,7 +184,7 @@ def test_density_iteration(cuda_device, dist, n, cfg, mode, g, iteration, widen)
     # the GPU's answer must be a converged answer under the oracle's own arithmetic
     chk = oracle.density(d["pos"], m, out["h"])
     neff = 4.0 * np.pi / 3.0 * out["h"] ** 3 * chk["rho"] / m
-    assert np.all(np.abs(neff - 64.0) <= 2.0 + 1e-3)
+    assert np.all(np.abs(neff - 64.0) <= NEFF_TOL)
     assert np.array_equal(out["nngb"], chk["nngb"])
     rel = np.abs(out["rho"] / chk["rho"] - 1.0)
     w = int(np.argmax(rel))

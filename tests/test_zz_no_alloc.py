@@ -8,8 +8,6 @@ calls in a row: the static scratch keeps the previous call's contents, so the se
 call checks that nothing depends on it.  This file is collected last.
 """
 
-import ctypes
-
 import numpy as np
 import pytest
 
@@ -19,15 +17,20 @@ pytestmark = pytest.mark.gpu
 
 
 def _static_sort(lib, pos):
+    """The entry point through the binding's checked wrapper (element types, lengths and
+    device of every array are checked before the C call); returns (status, keys, perm)."""
     import torch
+
+    import paper_1810_09898_gb300 as sg
 
     n = pos.shape[0]
     keys = torch.empty(n, dtype=torch.int64, device=pos.device)
     perm = torch.empty(n, dtype=torch.int32, device=pos.device)
-    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = lib.sphgrp_sfc_keys_sort_static(n, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(keys.data_ptr()),
-                                         ctypes.c_void_p(perm.data_ptr()), stream)
-    return rc, keys, perm
+    try:
+        sg.sfc_keys_sort_static(pos, keys, perm)
+    except sg.SphgrpError as e:
+        return e.code, keys, perm
+    return 0, keys, perm
 
 
 def test_static_scratch_sort_equals_context_sort(cuda_device):
@@ -65,6 +68,11 @@ def test_static_scratch_sort_rejects_oversize_and_bad_input(cuda_device):
     bad = torch.tensor([[0.5, 0.5, 1.5], [0.1, 0.2, 0.3]], dtype=torch.float64, device=cuda_device)
     rc, _, _ = _static_sort(lib, bad)
     assert rc == -1
+    # a short output array is refused before the C call
+    small = torch.zeros((8, 3), dtype=torch.float64, device=cuda_device)
+    with pytest.raises(ValueError, match="perm_out"):
+        sg.sfc_keys_sort_static(small, torch.empty(8, dtype=torch.int64, device=cuda_device),
+                                torch.empty(4, dtype=torch.int32, device=cuda_device))
     # the flag is cleared per call: a good input right after a bad one succeeds
     good = torch.as_tensor(np.random.default_rng(3).random((1000, 3)), device=cuda_device)
     rc, keys, _ = _static_sort(lib, good)
