@@ -56,7 +56,8 @@ def lib():
                                               P, P, P, P, P, P]
             L.orc_density_iterate.restype = i64
             L.orc_hydro.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, dbl, dbl, dbl,
-                                    dbl, i32, P, P, P, P, P]
+                                    dbl, i32, P, P, P, P, P, P]
+            L.orc_balsara.argtypes = [i64, P, P, P, P, dbl, P]
             L.orc_threads.argtypes = []
             L.orc_density_grouped.argtypes = [i64, P, P, P, P, P, i64, P, i32, P, P, P, P, P, P]
             L.orc_hydro_grouped.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, i64, P, i32, dbl, dbl,
@@ -178,19 +179,31 @@ def density_iterate(pos, m, h_init, targets=None, nngb=64.0, dn=2.0, max_iter=10
 
 
 def hydro(pos, vel, m, h, rho, f, u, targets=None, gamma=5.0 / 3.0, alpha=1.0, beta=2.0,
-          eps=0.01, use_tree=True):
+          eps=0.01, use_tree=True, fbal=None):
+    """Accelerations and du/dt of the targets; fbal (n,) scales every pair's viscosity by
+    the pair mean of the limiter (Balsara's switch, see balsara), None for the plain form."""
     x, y, z = _xyz(pos)
     vx, vy, vz = _xyz(vel)
     n = len(x)
     m, h, rho, f, u = (_f64(a) for a in (m, h, rho, f, u))
+    fb = None if fbal is None else _f64(fbal)
     t = np.arange(n, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
     nt = len(t)
     ax, ay, az, dudt = (np.empty(nt) for _ in range(4))
     nn = np.empty(nt, dtype=np.int32)
     lib().orc_hydro(n, _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(m), _p(h), _p(rho), _p(f),
                     _p(u), nt, _p(t), gamma, alpha, beta, eps, int(use_tree), _p(ax), _p(ay),
-                    _p(az), _p(dudt), _p(nn))
+                    _p(az), _p(dudt), _p(nn), None if fb is None else _p(fb))
     return {"acc": np.stack([ax, ay, az], axis=1), "dudt": dudt, "nngb": nn}
+
+
+def balsara(divv, curl, u, h, gamma=5.0 / 3.0):
+    """Balsara's limiter |div v| / (|div v| + |curl v| + 1e-4 c / h) of every particle."""
+    divv, u, h = _f64(divv), _f64(u), _f64(h)
+    curl = _f64(np.asarray(curl).reshape(-1, 3))
+    out = np.empty(len(divv))
+    lib().orc_balsara(len(divv), _p(divv), _p(curl), _p(u), _p(h), gamma, _p(out))
+    return out
 
 
 def curve_order(pos, targets=None):

@@ -20,8 +20,8 @@
 //    correction f_i, and the smoothing-length iteration to a fixed effective
 //    neighbour number N_ngb = 4 pi rho h^3 / (3 m) (Sec. 2.2, the relation above Eq. 1).
 //  * SPH hydro accelerations and du/dt (grad-h pressure term plus Monaghan
-//    artificial viscosity); the paper only cites its hydro scheme, the reading is the
-//    standard energy-conserving form.
+//    artificial viscosity, optionally limited by Balsara's switch); the paper only
+//    cites its hydro scheme, the reading is the standard energy-conserving form.
 //  * velocity divergence and curl over the density sets (no formula in the paper; the
 //    standard SPH estimates from the velocity gradient at h_i).
 //  * the backward (adjoint) of the density and the accelerations with respect to
@@ -415,10 +415,12 @@ DensityOut density_at(const Particles& P, const double* m, double hi, const Tree
     return density_sum(P, m, hi, i, nb);
 }
 
-// Inputs of the hydro sums, indexed by particle.
+// Inputs of the hydro sums, indexed by particle.  fbal: the viscosity limiter of every
+// particle (NULL: 1, the plain Monaghan viscosity).
 struct HydroIn {
     const double *x, *y, *z, *vx, *vy, *vz, *m, *h, *rho, *fgrad, *u;
     double gamma, alpha, beta, eps;
+    const double* fbal;
 };
 
 // a_i and du_i/dt over the hydro neighbour list nb (ascending indices), in that order.
@@ -452,6 +454,7 @@ void hydro_sum(const HydroIn& H, int64_t i, const std::vector<int32_t>& nb, doub
             double cb = 0.5 * (ci + cj);
             double rb = 0.5 * (rho[i] + rho[j]);
             visc = (-alpha * cb * mu + beta * mu * mu) / rb;
+            if (H.fbal) visc *= 0.5 * (H.fbal[i] + H.fbal[j]);
         }
         double gi[3], gj[3], gb[3];
         for (int a = 0; a < 3; ++a) {
@@ -680,14 +683,16 @@ int orc_velocity_derivs(int64_t n, const double* x, const double* y, const doubl
 // Monaghan viscosity Pi_ij = (-alpha cbar mu + beta mu^2) / rhobar for v_ij . r_ij < 0
 // (else 0), mu = hbar v_ij.r_ij / (r^2 + eps hbar^2), bars = pair means.
 // Coincident pairs (r = 0) contribute nothing (the kernel gradient vanishes there).
+// With fbal (not NULL) the viscosity of every pair is scaled by the pair mean of the
+// limiter, Pi_ij (fbal_i + fbal_j) / 2 (Balsara's switch; orc_balsara gives fbal).
 int orc_hydro(int64_t n, const double* x, const double* y, const double* z,
               const double* vx, const double* vy, const double* vz, const double* m,
               const double* h, const double* rho, const double* fgrad, const double* u,
               int64_t nt, const int32_t* targets, double gamma, double alpha, double beta,
               double eps, int use_tree, double* ax, double* ay, double* az, double* dudt,
-              int32_t* nngb) {
+              int32_t* nngb, const double* fbal) {
     Particles P{n, x, y, z};
-    const HydroIn H{x, y, z, vx, vy, vz, m, h, rho, fgrad, u, gamma, alpha, beta, eps};
+    const HydroIn H{x, y, z, vx, vy, vz, m, h, rho, fgrad, u, gamma, alpha, beta, eps, fbal};
     Tree tree;
     if (use_tree) build_tree(tree, n, x, y, z, h);
     parallel_for(nt, [&](int64_t t) {
@@ -749,7 +754,7 @@ int orc_hydro_grouped(int64_t n, const double* x, const double* y, const double*
                       double* dudt, int32_t* nngb, int64_t* stats) {
     if (g < 1) return -1;
     Particles P{n, x, y, z};
-    const HydroIn H{x, y, z, vx, vy, vz, m, h, rho, fgrad, u, gamma, alpha, beta, eps};
+    const HydroIn H{x, y, z, vx, vy, vz, m, h, rho, fgrad, u, gamma, alpha, beta, eps, nullptr};
     Tree tree;
     build_tree(tree, n, x, y, z, h);
     const int64_t ngroups = (nt + g - 1) / g;
@@ -775,6 +780,23 @@ int orc_hydro_grouped(int64_t n, const double* x, const double* y, const double*
     stats[0] = ngroups;
     stats[1] = cands.load();
     stats[2] = tests.load();
+    return 0;
+}
+
+// Balsara's viscosity limiter of every particle from its velocity divergence and curl
+// (Balsara 1995, in the form used with Gadget's SPH):
+//   fbal_i = |div v_i| / (|div v_i| + |curl v_i| + 1e-4 c_i / h_i),
+// c_i = sqrt(gamma (gamma - 1) u_i) the sound speed, h_i the smoothing length.  It is
+// near 1 in compression (no curl) and near 0 in shear (no divergence).
+int orc_balsara(int64_t n, const double* divv, const double* curl, const double* u, const double* h,
+                double gamma, double* fbal) {
+    for (int64_t i = 0; i < n; ++i) {
+        const double c = std::sqrt(gamma * (gamma - 1.0) * u[i]);
+        const double ad = std::fabs(divv[i]);
+        const double ac = std::sqrt(curl[3 * i] * curl[3 * i] + curl[3 * i + 1] * curl[3 * i + 1] +
+                                    curl[3 * i + 2] * curl[3 * i + 2]);
+        fbal[i] = ad / (ad + ac + 1e-4 * c / h[i]);
+    }
     return 0;
 }
 

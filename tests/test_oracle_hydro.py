@@ -190,3 +190,69 @@ def test_tree_equals_brute_force():
     b = oracle.hydro(d["pos"], d["vel"], d["m"], h, dens["rho"], dens["f"], d["u"], use_tree=True)
     assert np.array_equal(a["nngb"], b["nngb"])
     assert np.allclose(a["acc"], b["acc"], rtol=1e-13, atol=0)
+
+
+# ----------------------------------------------------------------------------------------
+# Balsara's limiter: Pi_ij is scaled by the pair mean (f_i + f_j) / 2 of
+# f = |div v| / (|div v| + |curl v| + 1e-4 c / h).
+# ----------------------------------------------------------------------------------------
+
+def test_limited_viscosity_two_particle_closed_form():
+    fb = np.array([0.25, 0.75])     # the pair mean is 1/2, neither value alone
+    ref = _pair_closed_form(1.0, 2.0, 0.01)
+    P = _PAIR
+    pos = np.array([[P["x0"], 0.5, 0.5], [P["x0"] + P["r"], 0.5, 0.5]])
+    vel = np.array([[P["v"], P["w"], 0.0], [-P["v"], 0.0, 0.0]])
+    args = (pos, vel, np.array(P["m"]), np.array(P["h"]), np.array(P["rho"]), np.array(P["f"]), np.array(P["u"]))
+    out = oracle.hydro(*args, gamma=_GAMMA, fbal=fb)
+    rest = _pair_oracle(1.0, 2.0, 0.01, moving=False)
+    half = 0.5 * ref["Pi"]
+    assert out["acc"][0, 0] == pytest.approx(rest["acc"][0, 0] + P["m"][1] * half * ref["gbar"], rel=1e-13)
+    # du_0 = m_1 [-2 v A_0 W'_0 - (Pi / 2) v W_bar']: the plain value with half the viscous term
+    assert out["dudt"][0] == pytest.approx(ref["du0"] + P["m"][1] * half * P["v"] * ref["gbar"], rel=1e-13)
+    assert out["dudt"][1] == pytest.approx(ref["du1"] + P["m"][0] * half * P["v"] * ref["gbar"], rel=1e-13)
+    # limiter 1 everywhere is the plain viscosity, 0 everywhere removes it
+    one = oracle.hydro(*args, gamma=_GAMMA, fbal=np.ones(2))
+    plain = oracle.hydro(*args, gamma=_GAMMA)
+    assert np.array_equal(one["acc"], plain["acc"]) and np.array_equal(one["dudt"], plain["dudt"])
+    zero = oracle.hydro(*args, gamma=_GAMMA, fbal=np.zeros(2))
+    assert np.allclose(zero["acc"], rest["acc"], rtol=1e-14, atol=0)
+
+
+def _lattice_flow(A, n_side=12):
+    pos = sphgen.lattice(n_side)
+    n = len(pos)
+    m = np.full(n, 1.0 / n)
+    h = np.full(n, 2.2 / n_side)
+    dens = oracle.density(pos, m, h)
+    vel = (pos - 0.5) @ np.asarray(A).T
+    u = np.ones(n)
+    inner = np.flatnonzero(np.all((pos > 2 * h[0] + 1e-9) & (pos < 1 - 2 * h[0] - 1e-9), axis=1))
+    divv, curl = oracle.velocity_derivs(pos, vel, m, h, dens["rho"])
+    fb = oracle.balsara(divv, curl, u, h)
+    args = (pos, vel, m, h, dens["rho"], dens["f"], u)
+    return args, fb, inner
+
+
+def test_limiter_switches_off_viscosity_in_pure_shear():
+    # v_x = S y: no divergence on the lattice (symmetry), curl -S z: the limiter is 0
+    args, fb, inner = _lattice_flow([[0.0, 0.4, 0.0], [0.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    assert np.max(fb[inner]) < 1e-12
+    lim = oracle.hydro(*args, targets=inner, fbal=fb)
+    plain = oracle.hydro(*args, targets=inner)
+    scale = np.max(np.abs(plain["dudt"]))
+    assert scale > 0.0                                  # the plain viscosity heats the shear
+    assert np.max(np.abs(lim["dudt"])) < 1e-10 * scale  # the limited one does not
+
+
+def test_limiter_keeps_viscosity_in_pure_compression():
+    # v = -a (x - c): no curl, the limiter is the same value close to 1 for the inner
+    # particles, and their viscous part (plain minus inviscid) scales by exactly it
+    args, fb, inner = _lattice_flow(-0.6 * np.eye(3))
+    f0 = fb[inner]
+    assert np.allclose(f0, f0[0], rtol=1e-12) and 0.99 < f0[0] < 1.0
+    far = np.flatnonzero(np.all((args[0] > 3 * args[3][0] + 1e-9) & (args[0] < 1 - 3 * args[3][0] - 1e-9), axis=1))
+    lim = oracle.hydro(*args, targets=far, fbal=fb)
+    plain = oracle.hydro(*args, targets=far)
+    inv = oracle.hydro(*args, targets=far, alpha=0.0, beta=0.0)
+    assert np.allclose(lim["dudt"] - inv["dudt"], f0[0] * (plain["dudt"] - inv["dudt"]), rtol=1e-11, atol=0)
