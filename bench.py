@@ -488,29 +488,49 @@ def per_pass(P, mode: int, g: int, reps: int = 5) -> dict:
     return {"density_ms": d, "hydro_ms": h, "value": P.n_act / ((d + h) / 1e3), "unit": UNIT}
 
 
-def velocity_pass(P, g: int, reps: int = 5) -> dict:
-    """One grouped velocity divergence + curl pass over the active particles at converged
-    h (density sets), CUDA events per pass."""
-    torch = P.torch
-    n = P.n
-    divv = torch.zeros(n, dtype=torch.float32, device=P.dev)
-    curl = torch.zeros((n, 3), dtype=torch.float32, device=P.dev)
+def _median_ms(torch, fn, reps: int) -> float:
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     t = []
     for rep in range(reps + 1):
         ev[0].record(stream)
-        P.ctx.velocity_derivs(P.act, P.h, P.rho, P.vel, g, divv, curl)
+        fn()
         ev[1].record(stream)
         torch.cuda.synchronize()
         if rep:
             t.append(ev[0].elapsed_time(ev[1]))
-        if rep == reps:
-            gbs = launch_gbs(P.ctx.launch_log()[0], *B_VEL)
-    ms = float(np.median(t))
+    return float(np.median(t))
+
+
+def velocity_pass(P, g: int, reps: int = 5) -> dict:
+    """At converged h over the active particles, CUDA events per call: one grouped
+    velocity divergence + curl pass (its own walk over the density sets); the density pass
+    alone and the density pass with div/curl summed in the same loop (fused); one hydro
+    pass with the Balsara-limited viscosity fed those div/curl."""
+    torch = P.torch
+    n = P.n
+    c = P.ctx
+    divv = torch.zeros(n, dtype=torch.float32, device=P.dev)
+    curl = torch.zeros((n, 3), dtype=torch.float32, device=P.dev)
+    ms = _median_ms(torch, lambda: c.velocity_derivs(P.act, P.h, P.rho, P.vel, g, divv, curl), reps)
+    gbs = launch_gbs(c.launch_log()[0], *B_VEL)
+    h = P.h.clone()
+    rho, drho, f = (torch.zeros(n, dtype=torch.float32, device=P.dev) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=P.dev)
+    ms_d = _median_ms(torch, lambda: c.density(P.act, h, 0, P.sg.GROUPED, g, rho, drho, f, nn), reps)
+    ms_f = _median_ms(torch, lambda: c.density_derivs(P.act, h, 0, g, P.vel, rho, drho, f, nn, divv, curl), reps)
+    acc = torch.zeros((n, 3), dtype=torch.float32, device=P.dev)
+    dudt = torch.zeros(n, dtype=torch.float32, device=P.dev)
+    ms_h = _median_ms(torch, lambda: c.hydro_force(P.act, P.h, P.rho, P.f, P.vel, P.u, P.sg.GROUPED, g, acc, dudt),
+                      reps)
+    ms_b = _median_ms(torch, lambda: c.hydro_force(P.act, P.h, P.rho, P.f, P.vel, P.u, P.sg.GROUPED, g, acc, dudt,
+                                                   divv=divv, curlv=curl), reps)
     peak = measured_peak_hbm()
     return {"ms": ms, "value": P.n_act / (ms / 1e3), "unit": UNIT, "group_size": g,
-            "roofline": {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak}}
+            "roofline": {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak},
+            "fused_in_density": {"density_ms": ms_d, "density_with_derivs_ms": ms_f,
+                                 "extra_ms": ms_f - ms_d, "separate_walk_ms": ms},
+            "hydro_balsara": {"plain_ms": ms_h, "limited_ms": ms_b}}
 
 
 def active_leg(P, frac: float, g: int, steps: int, warmup: int, dist, rank: int) -> dict:

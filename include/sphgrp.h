@@ -248,6 +248,33 @@ int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
                            const double* h, const float* rho, const float* vel,
                            int group_size, float* divv, float* curlv, cudaStream_t stream);
 
+/* a6 + a7 with the velocity derivatives of the call above accumulated in the same
+ * density loop (the same staged candidates and the same neighbour decisions), instead
+ * of a separate walk: as sphgrp_density (grouped form, walk passes in any iteration
+ * mode), plus
+ * vel:   device n x 3 FP32 velocities of all particles (read);
+ * divv:  device n FP32, curlv: device n x 3 FP32 -- div v and curl v of the active
+ *        particles at their final h, with the final rho (as sphgrp_velocity_derivs
+ *        computes them from that h and rho).
+ * Errors as sphgrp_density. */
+int sphgrp_density_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h,
+                          int iterate, int group_size, const float* vel, float* rho,
+                          float* drhodh, float* fgrad, int32_t* nngb, int32_t* iters,
+                          float* divv, float* curlv, cudaStream_t stream);
+
+/* a8 with Balsara's limiter on the viscosity (Balsara 1995, as used with Gadget's SPH;
+ * the paper names no limiter): every pair's Pi_ij is scaled by (fb_i + fb_j) / 2 with
+ *   fb_i = |div v_i| / (|div v_i| + |curl v_i| + 1e-4 c_i / h_i),
+ * c_i = sqrt(gamma (gamma - 1) u_i), formed on the device from
+ * divv:  device n FP32, curlv: device n x 3 FP32 of all particles (e.g. from
+ *        sphgrp_density_derivs or sphgrp_velocity_derivs).
+ * Everything else as sphgrp_hydro_force (fb = 1 there).  EINVAL for NULL divv or curlv. */
+int sphgrp_hydro_force_balsara(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active,
+                               const double* h, const float* rho, const float* fgrad,
+                               const float* vel, const float* u, const float* divv,
+                               const float* curlv, int mode, int group_size, float* acc,
+                               float* dudt, int32_t* nngb, cudaStream_t stream);
+
 /* a9: backward (adjoint) of the density and the hydro accelerations.  The paper has
  * no backward pass; this differentiates the a6 and a8 loops above.  For the positions
  * x and masses m of the last sphgrp_tree_build, and the given h, vel and u, it returns

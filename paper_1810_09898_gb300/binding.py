@@ -31,6 +31,8 @@ EXPORTED = [
     "sphgrp_density",
     "sphgrp_hydro_force",
     "sphgrp_velocity_derivs",
+    "sphgrp_density_derivs",
+    "sphgrp_hydro_force_balsara",
     "sphgrp_backward",
     "sphgrp_get_stats",
     "sphgrp_kernel_launches",
@@ -148,6 +150,8 @@ def load_library():
                                          ctypes.POINTER(I64), ctypes.POINTER(I64), P]
     L.sphgrp_density.argtypes = [P, I64, P, P, I32, I32, I32, P, P, P, P, P, P]
     L.sphgrp_hydro_force.argtypes = [P, I64, P, P, P, P, P, P, I32, I32, P, P, P, P]
+    L.sphgrp_hydro_force_balsara.argtypes = [P, I64, P, P, P, P, P, P, P, P, I32, I32, P, P, P, P]
+    L.sphgrp_density_derivs.argtypes = [P, I64, P, P, I32, I32, P, P, P, P, P, P, P, P, P]
     L.sphgrp_velocity_derivs.argtypes = [P, I64, P, P, P, P, I32, P, P, P]
     L.sphgrp_backward.argtypes = [P, P, P, P, P, P, I32, P, P, P, P]
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -300,14 +304,33 @@ class Context:
                                       _arg(drhodh, "drhodh", _F32, n), _arg(fgrad, "fgrad", _F32, n),
                                       _arg(nngb, "nngb", _I32, n), _arg(iters, "iters", _I32, n, True), _stream()))
 
-    # -- a8
-    def hydro_force(self, active, h, rho, fgrad, vel, u, mode, group_size, acc, dudt, nngb=None):
+    def density_derivs(self, active, h, iterate, group_size, vel, rho, drhodh, fgrad, nngb, divv, curlv,
+                       iters=None):
+        """The density (as density, grouped form) with div v (n,) and curl v (n, 3) summed in
+        the same loop, at every active particle's final h."""
         na, n = active.shape[0], self.n
-        _check(self._L.sphgrp_hydro_force(self._h, na, _arg(active, "active", _I32, na), _arg(h, "h", _F64, n),
-                                          _arg(rho, "rho", _F32, n), _arg(fgrad, "fgrad", _F32, n),
-                                          _arg(vel, "vel", _F32, 3 * n), _arg(u, "u", _F32, n), mode, group_size,
-                                          _arg(acc, "acc", _F32, 3 * n), _arg(dudt, "dudt", _F32, n),
-                                          _arg(nngb, "nngb", _I32, n, True), _stream()))
+        _check(self._L.sphgrp_density_derivs(self._h, na, _arg(active, "active", _I32, na), _arg(h, "h", _F64, n),
+                                             int(iterate), group_size, _arg(vel, "vel", _F32, 3 * n),
+                                             _arg(rho, "rho", _F32, n), _arg(drhodh, "drhodh", _F32, n),
+                                             _arg(fgrad, "fgrad", _F32, n), _arg(nngb, "nngb", _I32, n),
+                                             _arg(iters, "iters", _I32, n, True), _arg(divv, "divv", _F32, n),
+                                             _arg(curlv, "curlv", _F32, 3 * n), _stream()))
+
+    # -- a8
+    def hydro_force(self, active, h, rho, fgrad, vel, u, mode, group_size, acc, dudt, nngb=None, divv=None,
+                    curlv=None):
+        """Accelerations and du/dt; with divv and curlv (all particles) the viscosity is
+        limited by Balsara's switch (sphgrp_hydro_force_balsara)."""
+        na, n = active.shape[0], self.n
+        common = (_arg(active, "active", _I32, na), _arg(h, "h", _F64, n), _arg(rho, "rho", _F32, n),
+                  _arg(fgrad, "fgrad", _F32, n), _arg(vel, "vel", _F32, 3 * n), _arg(u, "u", _F32, n))
+        out = (_arg(acc, "acc", _F32, 3 * n), _arg(dudt, "dudt", _F32, n), _arg(nngb, "nngb", _I32, n, True),
+               _stream())
+        if divv is None and curlv is None:
+            _check(self._L.sphgrp_hydro_force(self._h, na, *common, mode, group_size, *out))
+        else:
+            _check(self._L.sphgrp_hydro_force_balsara(self._h, na, *common, _arg(divv, "divv", _F32, n),
+                                                      _arg(curlv, "curlv", _F32, 3 * n), mode, group_size, *out))
 
     def velocity_derivs(self, active, h, rho, vel, group_size, divv, curlv):
         """Velocity divergence (n,) and curl (n, 3) over the density sets (grouped walk)."""

@@ -91,11 +91,15 @@ __global__ void k_gather_h(int64_t n, const int32_t* __restrict__ perm, const do
     pfix[r].w = __float_as_uint((float)v);
 }
 
+// Hydro inputs in key order: hyd0 = {v, c}, hyd1 = {A = f P / rho^2, rho, 1/h, fbal}.
+// fbal is Balsara's viscosity limiter |div v| / (|div v| + |curl v| + 1e-4 c / h) when the
+// caller gives div v and curl v, else 1 (the plain Monaghan viscosity).
 __global__ void k_hydro_prep(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
                              const float* __restrict__ rho, const float* __restrict__ fgrad,
                              const float* __restrict__ vel, const float* __restrict__ u, float gamma,
                              double* __restrict__ h64, uint4* __restrict__ pfix, float4* __restrict__ hyd0,
-                             float4* __restrict__ hyd1, unsigned* err) {
+                             float4* __restrict__ hyd1, unsigned* err, const float* __restrict__ divv,
+                             const float* __restrict__ curlv) {
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     int i = perm[r];
@@ -109,9 +113,22 @@ __global__ void k_hydro_prep(int64_t n, const int32_t* __restrict__ perm, const 
     float cs = sqrtf(gamma * P / rh);
     float A = fgrad[i] * P / (rh * rh);
     hyd0[r] = make_float4(vel[3 * (int64_t)i], vel[3 * (int64_t)i + 1], vel[3 * (int64_t)i + 2], cs);
-    const double kPi = 3.14159265358979323846;
-    float s = (float)(8.0 / (kPi * hv * hv * hv * hv));
-    hyd1[r] = make_float4(A, rh, 1.0f / hf, s);
+    float fb = 1.0f;
+    if (divv) {
+        const float ad = fabsf(divv[i]);
+        const float cx = curlv[3 * (int64_t)i], cy = curlv[3 * (int64_t)i + 1], cz = curlv[3 * (int64_t)i + 2];
+        fb = ad / (ad + sqrtf(fmaf(cx, cx, fmaf(cy, cy, cz * cz))) + 1.0e-4f * cs / hf);
+    }
+    hyd1[r] = make_float4(A, rh, 1.0f / hf, fb);
+}
+
+// velocities in key order for the density loop with velocity derivatives: hyd0 = {v, 0}
+__global__ void k_vel_gather(int64_t n, const int32_t* __restrict__ perm, const float* __restrict__ vel,
+                             float4* __restrict__ hyd0) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t i = perm[r];
+    hyd0[r] = make_float4(vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], 0.0f);
 }
 
 // velocity-derivative inputs in key order: hyd0 = {v, 0}, hyd1 = {0, rho, 1/h, 8/(pi h^4)}
@@ -170,9 +187,9 @@ int launch_gather_h(Ctx* c, const double* h, cudaStream_t s) {
 
 // hydro inputs of every particle in key order (hyd0, hyd1, h64, pfix.w)
 int launch_hydro_prep(Ctx* c, const double* h, const float* rho, const float* fgrad, const float* vel,
-                      const float* u, cudaStream_t s) {
+                      const float* u, cudaStream_t s, const float* divv, const float* curlv) {
     k_hydro_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, rho, fgrad, vel, u, (float)c->p.gamma,
-                                                      c->h64, c->pfix, c->hyd0, c->hyd1, c->err);
+                                                      c->h64, c->pfix, c->hyd0, c->hyd1, c->err, divv, curlv);
     note_launch();
     return check_cuda(cudaGetLastError(), "hydro prep");
 }
@@ -701,16 +718,29 @@ int sphgrp_group_supersets(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
     return finish(c, s, 0);
 }
 
-int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h, int iterate,
-                   int mode, int group_size, float* rho, float* drhodh, float* fgrad, int32_t* nngb,
-                   int32_t* iters, cudaStream_t s) {
+}  // extern "C"
+
+namespace sphgrp {
+
+// The density with the smoothing-length iteration; with vel (not NULL) the same density
+// loop also sums the velocity divergence and curl (grouped form, walk passes), written to
+// divv / curlv at each particle's final h.
+int density_call(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h, int iterate, int mode,
+                 int group_size, float* rho, float* drhodh, float* fgrad, int32_t* nngb, int32_t* iters,
+                 const float* vel, float* divv, float* curlv, cudaStream_t s) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     int rc = check_common(c, n_act, active, mode, group_size);
     if (rc) return rc;
     if (!h || !rho || !drhodh || !fgrad || !nngb) return set_error(SPHGRP_EINVAL, "null output array");
+    const bool with_vel = vel != nullptr;
+    if (with_vel && (!divv || !curlv)) return set_error(SPHGRP_EINVAL, "null divv or curlv");
     reset_flags(c, s);
     k_gather_h<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, c->h64, c->pfix, c->err);
     note_launch();
+    if (with_vel) {
+        k_vel_gather<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, vel, c->hyd0);
+        note_launch();
+    }
     int nu = 0;
     if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
     const bool grouped = mode == SPHGRP_GROUPED;
@@ -718,7 +748,8 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     int32_t* U2 = c->act2;
     int* nfail = c->work + 8;
     cudaMemsetAsync(nfail, 0, sizeof(int), s);
-    if (grouped && iterate && c->p.iteration == SPHGRP_ITER_IN_GROUP) {
+    const int iteration = with_vel ? SPHGRP_ITER_PASSES : c->p.iteration;
+    if (grouped && iterate && iteration == SPHGRP_ITER_IN_GROUP) {
         // one launch: every group iterates its members to convergence
         SearchArgs a = base_args(c);
         a.U = U;
@@ -767,7 +798,7 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     // first pass keeps every member's candidates within h_w = iter_widen * h, and the
     // later passes of the members whose h stays within h_w iterate on those lists in one
     // kernel; the rest continue with walk passes as below.
-    bool recycle = grouped && iterate && c->p.iteration == SPHGRP_ITER_RECYCLE && group_size <= 32 && nu > 0;
+    bool recycle = grouped && iterate && iteration == SPHGRP_ITER_RECYCLE && group_size <= 32 && nu > 0;
     if (recycle && (rc = list_buffers(c)) != SPHGRP_OK) {
         if (rc != SPHGRP_ENOMEM) return rc;
         recycle = false;   // not enough device memory for the lists: walk passes only
@@ -818,6 +849,13 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
         ua.s1 = c->acc_drho;
         ua.n = c->acc_n;
         ua.npass = npass;
+        if (with_vel) {
+            // the raw div / curl sums of the pass in hyd1 (not used by the density loop)
+            a.o_vsum = c->hyd1;
+            ua.vsum = c->hyd1;
+            ua.divv = divv;
+            ua.curlv = curlv;
+        }
         const bool lists = recycle && it == 1;
         if (lists) {
             a.o_list = c->lst;
@@ -827,7 +865,8 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
             a.list_widen = c->p.iter_widen;
         }
         timer_begin(c, s);
-        rc = launch_search(a, lists ? kKindDensityList : SPHGRP_DENSITY, kAcc, grouped, c->sm_count, s);
+        rc = launch_search(a, lists ? kKindDensityList : with_vel ? kKindDensityVel : SPHGRP_DENSITY, kAcc, grouped,
+                           c->sm_count, s);
         timer_end(c, s, a.nu);
         if (rc) return rc;
         if ((rc = launch_hsml_update(ua, s))) return rc;
@@ -886,19 +925,16 @@ int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double
     return SPHGRP_OK;
 }
 
-int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
-                       const float* rho, const float* fgrad, const float* vel, const float* u,
-                       int mode, int group_size, float* acc, float* dudt, int32_t* nngb,
-                       cudaStream_t s) {
+// hydro forces, with Balsara's limiter when divv / curlv are given
+int hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h, const float* rho,
+                const float* fgrad, const float* vel, const float* u, const float* divv, const float* curlv,
+                int mode, int group_size, float* acc, float* dudt, int32_t* nngb, cudaStream_t s) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     int rc = check_common(c, n_act, active, mode, group_size);
     if (rc) return rc;
     if (!h || !rho || !fgrad || !vel || !u || !acc || !dudt) return set_error(SPHGRP_EINVAL, "null array");
     reset_flags(c, s);
-    k_hydro_prep<<<blocks_for(c->n, 256), 256, 0, s>>>(c->n, c->perm, h, rho, fgrad, vel, u,
-                                                      (float)c->p.gamma, c->h64, c->pfix, c->hyd0,
-                                                      c->hyd1, c->err);
-    note_launch();
+    if ((rc = launch_hydro_prep(c, h, rho, fgrad, vel, u, s, divv, curlv))) return rc;
     if ((rc = refresh_hmax(c, s))) return rc;
     int nu = 0;
     if ((rc = prepare_active(c, n_act, active, s, &nu))) return rc;
@@ -919,6 +955,42 @@ int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, co
     c->last.walks = a.ngroups;
     c->last.members = nu;
     return finish(c, s, 0);
+}
+
+}  // namespace sphgrp
+
+extern "C" {
+
+int sphgrp_density(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h, int iterate,
+                   int mode, int group_size, float* rho, float* drhodh, float* fgrad, int32_t* nngb,
+                   int32_t* iters, cudaStream_t s) {
+    return density_call(ctx, n_act, active, h, iterate, mode, group_size, rho, drhodh, fgrad, nngb, iters,
+                        nullptr, nullptr, nullptr, s);
+}
+
+int sphgrp_density_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* h, int iterate,
+                          int group_size, const float* vel, float* rho, float* drhodh, float* fgrad,
+                          int32_t* nngb, int32_t* iters, float* divv, float* curlv, cudaStream_t s) {
+    if (!vel) return set_error(SPHGRP_EINVAL, "null vel");
+    return density_call(ctx, n_act, active, h, iterate, SPHGRP_GROUPED, group_size, rho, drhodh, fgrad, nngb,
+                        iters, vel, divv, curlv, s);
+}
+
+int sphgrp_hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                       const float* rho, const float* fgrad, const float* vel, const float* u,
+                       int mode, int group_size, float* acc, float* dudt, int32_t* nngb,
+                       cudaStream_t s) {
+    return hydro_force(ctx, n_act, active, h, rho, fgrad, vel, u, nullptr, nullptr, mode, group_size, acc, dudt,
+                       nngb, s);
+}
+
+int sphgrp_hydro_force_balsara(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,
+                               const float* rho, const float* fgrad, const float* vel, const float* u,
+                               const float* divv, const float* curlv, int mode, int group_size, float* acc,
+                               float* dudt, int32_t* nngb, cudaStream_t s) {
+    if (!divv || !curlv) return set_error(SPHGRP_EINVAL, "null divv or curlv");
+    return hydro_force(ctx, n_act, active, h, rho, fgrad, vel, u, divv, curlv, mode, group_size, acc, dudt,
+                       nngb, s);
 }
 
 int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const double* h,

@@ -100,6 +100,9 @@ __device__ __forceinline__ float rel_diff(float p, float m) {
     return d;
 }
 
+// dW/dr = kSkernel h^-4 dw/dq for the M4 spline W = 8 / (pi h^3) w(r / h)
+constexpr float kSkernel = 2.54647908947032537f;   // 8 / pi
+
 // M4 shape w(q), w'(q), w''(q) (zero for q >= 1)
 __device__ __forceinline__ void m4_shape2(float q, float& w, float& dw, float& d2w) {
     float u = 1.0f - q;
@@ -206,6 +209,14 @@ struct DMember : MemberPos {
     float p0, p1, p2;               // plain partial sums of the current tile
 };
 
+// density member with the velocity derivatives over the same density set: the sums of
+// -m v_ij . grad W (divergence) and m v_ij x grad W (curl) at h_i, before the 1/rho
+struct DVMember : DMember {
+    float vx, vy, vz, sk;
+    float sd, cd, sx, cx_, sy, cy_, sz, cz_;   // compensated totals
+    float pd, px_, py_, pz_;                   // plain partial sums of the current tile
+};
+
 // density member of the recycled smoothing-length iteration: besides the sums at h it
 // keeps every candidate inside the widened radius h_w in its slice's sub-list
 struct DLMember : DMember {
@@ -225,7 +236,7 @@ struct SymMember : MemberPos {
 };
 
 struct HMember : SymMember {
-    float vx, vy, vz, cs, A, rho;
+    float vx, vy, vz, cs, A, rho, fb;   // fb: the viscosity limiter (1 without one)
     float sx, cx_, sy, cy_, sz, cz_, su, cu;   // compensated totals
     float px_, py_, pz_, pu;                   // plain partial sums of the current tile
 };
@@ -279,6 +290,20 @@ __device__ __forceinline__ void member_init(DMember& M, const SearchArgs& a, int
     M.thr_dot = M.h2hi - m2;
 }
 
+__device__ __forceinline__ void member_init(DVMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
+                                            uint32_t cz) {
+    member_init(static_cast<DMember&>(M), a, rank, cx, cy, cz);
+    M.sd = M.cd = M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = 0.0f;
+    M.pd = M.px_ = M.py_ = M.pz_ = 0.0f;
+    M.vx = M.vy = M.vz = M.sk = 0.0f;
+    if (rank < 0) return;
+    const float4 V = a.hyd0[rank];
+    M.vx = V.x;
+    M.vy = V.y;
+    M.vz = V.z;
+    M.sk = kSkernel * (M.hinv * M.hinv) * (M.hinv * M.hinv);
+}
+
 __device__ __forceinline__ void member_init(DLMember& M, const SearchArgs& a, int rank, uint32_t cx, uint32_t cy,
                                             uint32_t cz) {
     member_init(static_cast<DMember&>(M), a, rank, cx, cy, cz);
@@ -322,11 +347,13 @@ __device__ __forceinline__ void member_init(HMember& M, const SearchArgs& a, int
     M.sx = M.cx_ = M.sy = M.cy_ = M.sz = M.cz_ = M.su = M.cu = 0.0f;
     M.px_ = M.py_ = M.pz_ = M.pu = 0.0f;
     M.vx = M.vy = M.vz = M.cs = M.A = M.rho = 0.0f;
+    M.fb = 1.0f;
     if (!sym_init(M, a, rank, cx, cy, cz)) return;
     float4 H0 = a.hyd0[rank];
-    float4 H1 = a.hyd1[rank];
+    float4 H1 = a.hyd1[rank];   // {A, rho, 1/h, limiter}
     M.hinv = H1.z;
-    M.sk = H1.w;
+    M.sk = kSkernel * (H1.z * H1.z) * (H1.z * H1.z);
+    M.fb = H1.w;
     M.vx = H0.x; M.vy = H0.y; M.vz = H0.z; M.cs = H0.w;
     M.A = H1.x;
     M.rho = H1.y;
@@ -463,6 +490,14 @@ struct DAdjTile {
     uint32_t masks[kTileA];
 };
 
+struct DensVTile {
+    float4 p[kTileD];   // raw pfix -> {px, py, pz, |p|^2}
+    float4 o[kTileD];   // raw poff {ox, oy, oz, m}
+    float4 v[kTileD];   // raw hyd0 {vx, vy, vz, -}
+    int r[kTileD];
+    uint32_t masks[kTileD];
+};
+
 struct VelTile {
     float4 p[kTileV];   // raw pfix -> {px, py, pz, |p|^2}
     float4 o[kTileV];   // raw poff {ox, oy, oz, m}
@@ -480,6 +515,15 @@ struct KDens {
     static constexpr uint32_t bytes = 32u;
     using Member = DMember;
     using Tile = DensTile;
+};
+struct KDensVel {
+    static constexpr int min_blocks = 6;   // resident blocks per SM (register budget; 0: compiler's choice)
+    static constexpr int id = kKindDensityVel;
+    static constexpr bool sym = false;
+    static constexpr int cap = kTileD;
+    static constexpr uint32_t bytes = 48u;
+    using Member = DVMember;
+    using Tile = DensVTile;
 };
 struct KDensList {
     static constexpr int min_blocks = 7;   // resident blocks per SM (register budget; 0: compiler's choice)
@@ -549,6 +593,12 @@ __device__ __forceinline__ void stage_run(HAdjTile& T, const SearchArgs& a, int 
     bulk_to_smem(&T.h[dst], a.hyd1 + src, b, bar);
     bulk_to_smem(&T.w[dst], a.wadj + src, b, bar);
 }
+__device__ __forceinline__ void stage_run(DensVTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
+                                          unsigned long long* bar) {
+    bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
+    bulk_to_smem(&T.o[dst], a.poff + src, b, bar);
+    bulk_to_smem(&T.v[dst], a.hyd0 + src, b, bar);
+}
 __device__ __forceinline__ void stage_run(VelTile& T, const SearchArgs& a, int dst, int src, uint32_t b,
                                           unsigned long long* bar) {
     bulk_to_smem(&T.p[dst], a.pfix + src, b, bar);
@@ -584,6 +634,15 @@ __device__ __forceinline__ void flush(HMember& M) {
 }
 
 __device__ __forceinline__ void flush(VMember& M) {
+    kahan_add(M.sd, M.cd, M.pd);
+    kahan_add(M.sx, M.cx_, M.px_);
+    kahan_add(M.sy, M.cy_, M.py_);
+    kahan_add(M.sz, M.cz_, M.pz_);
+    M.pd = M.px_ = M.py_ = M.pz_ = 0.0f;
+}
+
+__device__ __forceinline__ void flush(DVMember& M) {
+    flush(static_cast<DMember&>(M));
     kahan_add(M.sd, M.cd, M.pd);
     kahan_add(M.sx, M.cx_, M.px_);
     kahan_add(M.sy, M.cy_, M.py_);
@@ -644,6 +703,37 @@ __device__ __forceinline__ void density_pair(DMember& M, const SearchArgs& a, fl
         if (q < a.x_cap) a.x_idx[q] = a.perm[crank];
         else atomicOr(a.err, kErrCap);
     }
+}
+
+// density pair with the velocity derivatives: the density decision and sums of
+// density_pair, then (for pairs at r > 0) the divergence and curl terms with
+// grad_i W = W'(r, h_i) (x_i - x_j) / r and v_ij = v_i - v_j
+template <int MODE, bool WRAP = false>
+__device__ __forceinline__ void densvel_pair(DVMember& M, const SearchArgs& a, float4 p, float mj, float4 vj,
+                                             int crank, LocalCounters& lc) {
+    const int n0 = M.n;
+    density_pair<MODE, WRAP>(M, a, p, mj, crank, lc);
+    if (MODE != kAcc || M.n == n0) return;
+    float dx, dy, dz, r2;
+    if (M.precise) {
+        precise_diff(M, a, crank, dx, dy, dz, r2);
+    } else {
+        dx = rel_diff<WRAP>(p.x, M.mx);
+        dy = rel_diff<WRAP>(p.y, M.my);
+        dz = rel_diff<WRAP>(p.z, M.mz);
+        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    }
+    if (r2 == 0.0f) return;
+    const float rinv = rsqrtf(r2);
+    float w, dw;
+    m4_shape(r2 * rinv * M.hinv, w, dw);
+    const float c = -M.sk * dw * rinv;   // x_i - x_j = -d
+    const float gx = c * dx, gy = c * dy, gz = c * dz;
+    const float vx = M.vx - vj.x, vy = M.vy - vj.y, vz = M.vz - vj.z;
+    M.pd = fmaf(-mj, fmaf(vx, gx, fmaf(vy, gy, vz * gz)), M.pd);
+    M.px_ = fmaf(mj, fmaf(vy, gz, -vz * gy), M.px_);
+    M.py_ = fmaf(mj, fmaf(vz, gx, -vx * gz), M.py_);
+    M.pz_ = fmaf(mj, fmaf(vx, gy, -vy * gx), M.pz_);
 }
 
 // density pair of the recycled iteration: a candidate inside the widened threshold joins
@@ -713,7 +803,7 @@ __device__ __forceinline__ bool sym_decide(const Mem& M, const SearchArgs& a, fl
 }
 
 // hydro pair: p = relative coordinates, q = {h_j^2, m_j, -, -}, v = {vx, vy, vz, c_j},
-// hh = {A_j, rho_j, 1/h_j, s_j}
+// hh = {A_j, rho_j, 1/h_j, limiter_j}
 template <int MODE, bool WRAP = false>
 __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, float4 p, float4 q,
                                            float4 v, float4 hh, int crank, LocalCounters& lc) {
@@ -738,7 +828,7 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
     m4_shape(r * M.hinv, wi, dwi);
     m4_shape(r * hh.z, wj, dwj);
     float dWi = M.sk * dwi;
-    float dWj = hh.w * dwj;
+    float dWj = kSkernel * (hh.z * hh.z) * (hh.z * hh.z) * dwj;
     float rx = -dx, ry = -dy, rz = -dz;  // r_ij = x_i - x_j
     float vx = M.vx - v.x, vy = M.vy - v.y, vz = M.vz - v.z;
     float vr = fmaf(vx, rx, fmaf(vy, ry, vz * rz));
@@ -747,8 +837,10 @@ __device__ __forceinline__ void hydro_pair(HMember& M, const SearchArgs& a, floa
         float hb = 0.5f * fmaf(q.x, hh.z, M.h);
         float mu = hb * vr * __frcp_rn(fmaf(a.eps * hb, hb, r2));
         float cb = 0.5f * (M.cs + v.w);
-        // Pi = (-alpha cbar mu + beta mu^2) / rhobar, rhobar = (rho_i + rho_j) / 2
+        // Pi = (-alpha cbar mu + beta mu^2) / rhobar, rhobar = (rho_i + rho_j) / 2, scaled by
+        // the pair mean of the limiter (1 for the plain viscosity)
         visc = 2.0f * fmaf(-a.alpha * cb, mu, a.beta * mu * mu) * __frcp_rn(M.rho + hh.y);
+        visc *= 0.5f * (M.fb + hh.w);
     }
     float gbar = 0.5f * (dWi + dWj);
     float coef = q.y * fmaf(M.A, dWi, fmaf(hh.x, dWj, visc * gbar)) * rinv;
@@ -875,6 +967,11 @@ __device__ __forceinline__ void tile_pair(DMember& M, const SearchArgs& a, const
     density_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.r[j], lc);
 }
 template <int MODE, bool WRAP>
+__device__ __forceinline__ void tile_pair(DVMember& M, const SearchArgs& a, const DensVTile& T, int j,
+                                          LocalCounters& lc) {
+    densvel_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.v[j], T.r[j], lc);
+}
+template <int MODE, bool WRAP>
 __device__ __forceinline__ void tile_pair(DLMember& M, const SearchArgs& a, const DensTile& T, int j,
                                           LocalCounters& lc) {
     density_list_pair<MODE, WRAP>(M, a, T.p[j], T.o[j].w, T.r[j], lc);
@@ -922,6 +1019,11 @@ __device__ __forceinline__ void slice_add(DMember& M, int o) {
     M.s2 = xsum(M.s2, o); M.c2 = xsum(M.c2, o);
     M.n += __shfl_xor_sync(0xffffffffu, M.n, o);
 }
+__device__ __forceinline__ void slice_add(DVMember& M, int o) {
+    slice_add(static_cast<DMember&>(M), o);
+    M.sd = xsum(M.sd, o); M.cd = xsum(M.cd, o); M.sx = xsum(M.sx, o); M.cx_ = xsum(M.cx_, o);
+    M.sy = xsum(M.sy, o); M.cy_ = xsum(M.cy_, o); M.sz = xsum(M.sz, o); M.cz_ = xsum(M.cz_, o);
+}
 __device__ __forceinline__ void slice_add(HMember& M, int o) {
     M.sx = xsum(M.sx, o); M.cx_ = xsum(M.cx_, o); M.sy = xsum(M.sy, o); M.cy_ = xsum(M.cy_, o);
     M.sz = xsum(M.sz, o); M.cz_ = xsum(M.cz_, o); M.su = xsum(M.su, o); M.cu = xsum(M.cu, o);
@@ -954,6 +1056,12 @@ __device__ __forceinline__ void write_result(const DMember& D, const SearchArgs&
     } else if (MODE == kCount) {
         a.x_cnt[a.perm[D.rank]] = D.n;
     }
+}
+template <int MODE>
+__device__ __forceinline__ void write_result(const DVMember& D, const SearchArgs& a) {
+    write_result<MODE>(static_cast<const DMember&>(D), a);
+    if (MODE == kAcc)
+        a.o_vsum[D.rank] = make_float4(D.sd - D.cd, D.sx - D.cx_, D.sy - D.cy_, D.sz - D.cz_);
 }
 template <int MODE>
 __device__ __forceinline__ void write_result(const HMember& H, const SearchArgs& a) {
@@ -2077,6 +2185,9 @@ int launch_search(const SearchArgs& a, int kind, int mode, bool grouped, int sm_
             case kKindVelocity:
                 if (mode != kAcc) return set_error(SPHGRP_EINVAL, "the velocity derivatives accumulate only");
                 return launch_group_m<KVel, kAcc>(a, sm_count, s);
+            case kKindDensityVel:
+                if (mode != kAcc) return set_error(SPHGRP_EINVAL, "velocity derivatives accumulate only");
+                return launch_group_m<KDensVel, kAcc>(a, sm_count, s);
             case kKindDensityList:
                 if (mode != kAcc || a.g > 32)
                     return set_error(SPHGRP_EINVAL, "candidate lists: accumulation, group size <= 32");
@@ -2182,6 +2293,17 @@ __device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, f
     const HsmlStep st = hsml_next(h, m, s0f, s1f, a.nngb, a.tol, a.iterate != 0, pass, a.max_iter, lo, hi);
     if (st.finish) {
         hsml_write(a.perm[r], h, s0f, s1f, n, pass, a.h_out, a.rho, a.drhodh, a.fgrad, a.nngb_out, a.iters);
+        if (a.vsum) {
+            // div v = -(1/rho) sum m v_ij . grad W, curl v = (1/rho) sum m v_ij x grad W
+            const int orig = a.perm[r];
+            const float hf = (float)h;
+            const float rinv = hf * hf * hf / (2.54647908947032537f * s0f);   // 1 / rho
+            const float4 V = a.vsum[r];
+            a.divv[orig] = V.x * rinv;
+            a.curlv[3 * (int64_t)orig] = V.y * rinv;
+            a.curlv[3 * (int64_t)orig + 1] = V.z * rinv;
+            a.curlv[3 * (int64_t)orig + 2] = V.w * rinv;
+        }
         a.keep[u] = 0;
         if (!st.converged) atomicAdd(a.nfail, 1);
         return;

@@ -10,7 +10,7 @@ enum Mode { kAcc = 0, kCount = 1, kFill = 2, kSupCount = 3, kSupFill = 4 };
 
 // pair loops of the search kernels: SPHGRP_DENSITY (0), SPHGRP_HYDRO (1) and the adjoints
 enum Kind { kKindDensity = 0, kKindHydro = 1, kKindHydroAdj = 2, kKindDensityAdj = 3, kKindVelocity = 4,
-            kKindDensityList = 5 };
+            kKindDensityList = 5, kKindDensityVel = 6 };
 
 // Candidate lists of the recycled smoothing-length iteration: every member of a pass-1
 // group keeps the candidates of the group's superset that lie within its widened radius
@@ -45,6 +45,11 @@ struct UpdateArgs {
     int iterate;
     int* nfail;
     int32_t* npass;       // optional: passes made so far per rank (null: every particle is at pass it)
+    // optional: velocity divergence / curl sums of the density pass (rank space, {div, curl}
+    // before the 1/rho); a finished particle writes div v and curl v to the caller's order
+    const float4* vsum;
+    float* divv;
+    float* curlv;
 };
 
 // passes 2, 3, ... of the recycled iteration over the members' candidate lists
@@ -107,6 +112,7 @@ struct SearchArgs {
     float* o_s1;
     float* o_s2;          // optional: d2Rho/dh2 sum (backward)
     int32_t* o_n;
+    float4* o_vsum;       // density with velocity derivatives: {div, curl} sums (rank space)
     // adjoint results (rank space)
     float4* o_adj0;       // hydro adjoint {xb, mb}
     float4* o_adj1;       // hydro adjoint {vb, -}
@@ -183,7 +189,7 @@ int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64
 // per-particle kernels shared by the entry points (api.cu, backward.cu)
 int launch_gather_h(Ctx* c, const double* h, cudaStream_t s);
 int launch_hydro_prep(Ctx* c, const double* h, const float* rho, const float* fgrad, const float* vel,
-                      const float* u, cudaStream_t s);
+                      const float* u, cudaStream_t s, const float* divv = nullptr, const float* curlv = nullptr);
 int backward_buffers(Ctx* c);
 int launch_bwd_prep(Ctx* c, const float* vel, const float* u, const float* g_acc, float4* hyd0, float4* hyd1,
                     cudaStream_t s);

@@ -106,3 +106,79 @@ def test_velocity_derivs_rejects_bad_input(cuda_device):
     with pytest.raises(sg.SphgrpError):
         _run(G, np.array([5], np.int32), np.array([0.1, 0.1]), np.ones(2, np.float32),
              np.zeros((2, 3), np.float32), 8)
+
+
+# ---------------------------------------------------------------- fused density + derivatives
+
+def _fused(G, active, h, vel32, g, iterate):
+    torch = G.torch
+    n = G.n
+    f32 = dict(dtype=torch.float32, device=G.dev)
+    hh = G.t(np.array(h, dtype=np.float64, copy=True), torch.float64)
+    rho, drho, fg = (torch.zeros(n, **f32) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=G.dev)
+    divv, curl = torch.zeros(n, **f32), torch.zeros((n, 3), **f32)
+    G.ctx.density_derivs(G.t(active, torch.int32), hh, iterate, g, G.t(vel32), rho, drho, fg, nn, divv, curl)
+    return {"h": hh.cpu().numpy(), "rho": rho.cpu().numpy(), "nngb": nn.cpu().numpy(), "div": divv.cpu().numpy(),
+            "curl": curl.cpu().numpy()}
+
+
+@pytest.mark.parametrize("iterate", [0, 1])
+@pytest.mark.parametrize("g", [8, 16, 64])
+def test_density_derivs_fused(setup, iterate, g):
+    """div v and curl v summed inside the density loop: the density as sphgrp_density, the
+    derivatives as the separate loop would give at the call's final h and rho."""
+    d, h, rho32, G, _ = setup
+    act = np.arange(G.n, dtype=np.int32)
+    h0 = h * np.exp(0.05 * np.random.default_rng(5).standard_normal(G.n)) if iterate else h
+    out = _fused(G, act, h0, d["vel32"], g, iterate)
+    m = d["m32"].astype(np.float64)
+    chk = oracle.density(d["pos"], m, out["h"])
+    assert np.array_equal(out["nngb"], chk["nngb"])
+    assert np.max(np.abs(out["rho"] / chk["rho"] - 1.0)) <= 1e-5
+    rdiv, rcurl = oracle.velocity_derivs(d["pos"], d["vel32"].astype(np.float64), m, out["h"],
+                                         out["rho"].astype(np.float64))
+    assert _rel_l2(out["div"], rdiv) <= TOL
+    assert _rel_l2(out["curl"], rcurl) <= TOL
+
+
+def test_density_derivs_partial_active(setup):
+    d, h, rho32, G, _ = setup
+    act = active_runs(G.n, 0.2, 17, G.perm.cpu().numpy())
+    out = _fused(G, act, h, d["vel32"], 16, 1)
+    m = d["m32"].astype(np.float64)
+    rdiv, rcurl = oracle.velocity_derivs(d["pos"], d["vel32"].astype(np.float64), m, out["h"],
+                                         out["rho"].astype(np.float64), targets=act)
+    assert _rel_l2(out["div"][act], rdiv) <= TOL
+    assert _rel_l2(out["curl"][act], rcurl) <= TOL
+    inactive = np.setdiff1d(np.arange(G.n), act)
+    assert np.all(out["div"][inactive] == 0.0)
+
+
+# ---------------------------------------------------------------- Balsara-limited hydro
+
+@pytest.mark.parametrize("mode,g", [(0, 1), (1, 16), (1, 32)])
+def test_hydro_balsara_matches_oracle(setup, mode, g):
+    """The limited viscosity against the oracle's, both fed the same div v and curl v."""
+    d, h, rho32, G, _ = setup
+    torch = G.torch
+    n = G.n
+    act = np.arange(n, dtype=np.int32)
+    f32 = oracle.density(d["pos"], d["m32"].astype(np.float64), h)["f"].astype(np.float32)
+    div, curl = _run(G, act, h, rho32, d["vel32"], 16)
+    acc = torch.zeros((n, 3), dtype=torch.float32, device=G.dev)
+    dudt = torch.zeros(n, dtype=torch.float32, device=G.dev)
+    nn = torch.zeros(n, dtype=torch.int32, device=G.dev)
+    G.ctx.hydro_force(G.t(act, torch.int32), G.t(h, torch.float64), G.t(rho32), G.t(f32), G.t(d["vel32"]),
+                      G.t(d["u32"]), mode, g, acc, dudt, nn, divv=G.t(div), curlv=G.t(curl))
+    fb = oracle.balsara(div, curl, d["u32"].astype(np.float64), h)
+    assert 0.0 <= fb.min() and fb.max() < 1.0 and fb.std() > 0.05   # the limiter does vary
+    ref = oracle.hydro(d["pos"], d["vel32"].astype(np.float64), d["m32"].astype(np.float64), h,
+                       rho32.astype(np.float64), f32.astype(np.float64), d["u32"].astype(np.float64), fbal=fb)
+    assert np.array_equal(nn.cpu().numpy(), ref["nngb"])
+    assert _rel_l2(acc.cpu().numpy(), ref["acc"]) <= TOL
+    assert _rel_l2(dudt.cpu().numpy(), ref["dudt"]) <= TOL
+    # and it differs from the plain viscosity
+    plain = oracle.hydro(d["pos"], d["vel32"].astype(np.float64), d["m32"].astype(np.float64), h,
+                         rho32.astype(np.float64), f32.astype(np.float64), d["u32"].astype(np.float64))
+    assert _rel_l2(plain["dudt"], ref["dudt"]) > 1e-2
