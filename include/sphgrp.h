@@ -404,6 +404,48 @@ int sphgrp_get_stats(sphgrp_ctx* ctx, sphgrp_stats* out);
 int sphgrp_get_launch_log(sphgrp_ctx* ctx, int cap, int64_t* members, int64_t* candidates,
                           int64_t* pair_tests, int64_t* nodes, double* ms, int* count);
 
+/* f3: domain decomposition with halo import.  The paper splits the particles along
+ * the Hilbert curve into one contiguous key range per process (Sec. 1.2) and finds
+ * neighbours across ranges by exporting particles in a second search phase (Sec. 1.1).
+ * Here each rank (one GPU) imports, before its search, the particles of the other ranks
+ * its own particles can reach (the halo), and then searches locally.  These are the
+ * per-rank device steps; paper_1810_09898_gb300.domain runs the exchanges.
+ *
+ * sphgrp_key_split: after sphgrp_sfc_keys_sort of the rank's particles, dest[i] (device,
+ * n uint64, caller order) = 1 << (the rank owning particle i's key), that rank being the
+ * number of splitters <= key (device, nsplit uint64 ascending, nsplit <= 63).  ESTATE
+ * without the sort. */
+int sphgrp_key_split(sphgrp_ctx* ctx, int nsplit, const uint64_t* splitters, uint64_t* dest,
+                     cudaStream_t stream);
+
+/* sphgrp_domain_boxes: after sphgrp_tree_build of the rank's particles, the tight boxes
+ * of its particles in every octree cell of depth `level` (0 .. 21) they occupy, in key
+ * order: boxes (device, cap x 8 FP64) = {lo x, y, z, hi x, y, z, hmax, count} with
+ * lo <= x < hi (box units) and hmax >= the largest h (device n FP64, caller order) in the
+ * box; *nbox (host) receives the number of boxes.  EOVERFLOW if more than cap boxes (or
+ * more than n_max / 2); ESTATE without a tree.  Synchronises the stream. */
+int sphgrp_domain_boxes(sphgrp_ctx* ctx, const double* h, int level, int cap, double* boxes,
+                        int* nbox, cudaStream_t stream);
+
+/* sphgrp_halo_select: for every particle j of the rank (device n FP64 h, caller order),
+ * the ranks that must import it: bit r of mask[j] (device n uint64) is set iff r !=
+ * self_rank and j lies within reach of one of rank r's boxes (box_rank, device nbox
+ * int32, gives each box's rank; boxes as sphgrp_domain_boxes wrote them, all ranks'
+ * concatenated): periodic distance to the box below widen * hmax (density: j is a
+ * neighbour of i iff |x_j - x_i| < h_i) or below max(widen * hmax, h_j) (hydro: iff
+ * below max(h_i, h_j)).  widen in [1, 4] covers the growth of h in a later
+ * smoothing-length iteration.  counts (device, world int64) = particles per rank.
+ * world <= 64.  Errors: EINVAL, ESTATE without a tree. */
+int sphgrp_halo_select(sphgrp_ctx* ctx, const double* h, int kind, double widen, int nbox,
+                       const double* boxes, const int32_t* box_rank, int self_rank, int world,
+                       uint64_t* mask, int64_t* counts, cudaStream_t stream);
+
+/* sphgrp_mask_compact: the particles (caller order, ascending) with bit `bit` of mask
+ * (device n uint64) set, to idx (device, n int32); *count (host) receives how many.
+ * Synchronises the stream. */
+int sphgrp_mask_compact(sphgrp_ctx* ctx, const uint64_t* mask, int bit, int32_t* idx, int64_t* count,
+                        cudaStream_t stream);
+
 /* Keys + stable sort (as sphgrp_sfc_keys_sort) without any device allocation, for
  * callers that may not call cudaMalloc / cudaFree: plug-ins whose host application
  * owns all device memory through its own pool, and latency-critical paths that cannot

@@ -32,6 +32,10 @@ EXPORTED = [
     "sphgrp_hydro_force",
     "sphgrp_velocity_derivs",
     "sphgrp_density_derivs",
+    "sphgrp_key_split",
+    "sphgrp_domain_boxes",
+    "sphgrp_halo_select",
+    "sphgrp_mask_compact",
     "sphgrp_hydro_force_balsara",
     "sphgrp_backward",
     "sphgrp_get_stats",
@@ -152,6 +156,10 @@ def load_library():
     L.sphgrp_hydro_force.argtypes = [P, I64, P, P, P, P, P, P, I32, I32, P, P, P, P]
     L.sphgrp_hydro_force_balsara.argtypes = [P, I64, P, P, P, P, P, P, P, P, I32, I32, P, P, P, P]
     L.sphgrp_density_derivs.argtypes = [P, I64, P, P, I32, I32, P, P, P, P, P, P, P, P, P]
+    L.sphgrp_key_split.argtypes = [P, I32, P, P, P]
+    L.sphgrp_domain_boxes.argtypes = [P, P, I32, I32, P, ctypes.POINTER(I32), P]
+    L.sphgrp_halo_select.argtypes = [P, P, I32, ctypes.c_double, I32, P, P, I32, I32, P, P, P]
+    L.sphgrp_mask_compact.argtypes = [P, P, I32, P, ctypes.POINTER(I64), P]
     L.sphgrp_velocity_derivs.argtypes = [P, I64, P, P, P, P, I32, P, P, P]
     L.sphgrp_backward.argtypes = [P, P, P, P, P, P, I32, P, P, P, P]
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -315,6 +323,39 @@ class Context:
                                              _arg(fgrad, "fgrad", _F32, n), _arg(nngb, "nngb", _I32, n),
                                              _arg(iters, "iters", _I32, n, True), _arg(divv, "divv", _F32, n),
                                              _arg(curlv, "curlv", _F32, 3 * n), _stream()))
+
+    # -- f3: domain decomposition (paper_1810_09898_gb300.domain drives these)
+    def key_split(self, splitters, dest):
+        """dest (n int64, caller order) = 1 << owner rank of every particle's key, from the
+        ascending splitters (int64 bit patterns of the 63-bit keys); after sfc_keys_sort."""
+        ns = splitters.shape[0]
+        _check(self._L.sphgrp_key_split(self._h, ns, _arg(splitters, "splitters", _I64, ns, ns == 0),
+                                        _arg(dest, "dest", _I64, self.n), _stream()))
+
+    def domain_boxes(self, h, level, boxes):
+        """Tight boxes {lo, hi, hmax, count} of the particles per octree cell of `level`
+        into boxes (cap x 8 float64); returns their number.  After tree_build."""
+        nb = ctypes.c_int()
+        _check(self._L.sphgrp_domain_boxes(self._h, _arg(h, "h", _F64, self.n), int(level), boxes.shape[0],
+                                           _arg(boxes, "boxes", _F64, 8 * boxes.shape[0]), ctypes.byref(nb),
+                                           _stream()))
+        return nb.value
+
+    def halo_select(self, h, kind, widen, boxes, box_rank, self_rank, world, mask, counts):
+        """mask (n int64): bit r set for the particles rank r must import; counts per rank."""
+        nb = box_rank.shape[0]
+        _check(self._L.sphgrp_halo_select(self._h, _arg(h, "h", _F64, self.n), int(kind), float(widen), nb,
+                                          _arg(boxes, "boxes", _F64, 8 * nb, nb == 0),
+                                          _arg(box_rank, "box_rank", _I32, nb, nb == 0), int(self_rank),
+                                          int(world), _arg(mask, "mask", _I64, self.n),
+                                          _arg(counts, "counts", _I64, world), _stream()))
+
+    def mask_compact(self, mask, bit, idx):
+        """The particles with bit `bit` of mask, ascending, into idx (n int32); returns how many."""
+        k = ctypes.c_int64()
+        _check(self._L.sphgrp_mask_compact(self._h, _arg(mask, "mask", _I64, self.n), int(bit),
+                                           _arg(idx, "idx", _I32, self.n), ctypes.byref(k), _stream()))
+        return k.value
 
     # -- a8
     def hydro_force(self, active, h, rho, fgrad, vel, u, mode, group_size, acc, dudt, nngb=None, divv=None,

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsphgrp.so")
-UNITS = ["sort.cu", "tree.cu", "ngb.cu", "api.cu", "backward.cu", "batch.cu", "noalloc.cu"]
+UNITS = ["sort.cu", "tree.cu", "ngb.cu", "api.cu", "backward.cu", "batch.cu", "noalloc.cu", "domain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include"), "-I" + SRC]
