@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--batch-boxes", type=int, default=96, help="boxes of the batched workload")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the uniform 32768 and the group-size sweep legs")
+    ap.add_argument("--no-halo", action="store_true", help="skip the domain-decomposition halo leg")
     ap.add_argument("--profile-pass", action="store_true",
                     help="after set-up run one grouped and one per-particle density+hydro pass inside "
                          "the NVTX range 'pass' (for ncu --nvtx-include pass/) and exit")
@@ -463,7 +465,9 @@ def guarded(fn, *args):
     try:
         return fn(*args)
     except Exception as e:  # noqa: BLE001 - any failure of an optional leg is reported
-        return {"error": f"{type(e).__name__}: {e}"}
+        import traceback
+
+        return {"error": f"{type(e).__name__}: {e}", "where": traceback.format_exc().splitlines()[-7:-1]}
 
 
 def per_pass(P, mode: int, g: int, reps: int = 5) -> dict:
@@ -754,6 +758,159 @@ def batch_leg(a, rank: int, steps: int, warmup: int):
             "tuned": tuned, "tune_seconds": tune_s}
 
 
+def small_configs_leg(a, rank: int, reps: int = 3) -> dict:
+    """The two smaller workloads, timed beside the main one (CUDA events, median of
+    reps calls after one warm-up):
+    * uniform N = 32768, all active, h iterated from the uniform-density guess: one density
+      call (keys, sort and tree excluded), per-particle form and grouped (g = 16);
+    * clustered N = 2^21, 20% active in key-order runs (mean 32), converged h: one density
+      pass and one hydro pass for every group size of the sweep and the per-particle form."""
+    import torch
+
+    import paper_1810_09898_gb300 as sg
+    import sphgen
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f32 = dict(dtype=torch.float32, device=dev)
+    out = {}
+    # uniform 32768
+    n = 32768
+    d = sphgen.make("uniform", n, config=1, seed_salt=rank)
+    pos = torch.from_numpy(d["pos"]).to(dev)
+    m = torch.from_numpy(d["m"].astype(np.float32)).to(dev)
+    c = sg.Context(n)
+    c.sfc_keys_sort(pos)
+    c.tree_build(pos, m)
+    act = torch.arange(n, dtype=torch.int32, device=dev)
+    h = torch.empty(n, dtype=torch.float64, device=dev)
+    rho, drho, fg = (torch.zeros(n, **f32) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=dev)
+    u1 = {"workload": "uniform N=32768, all active, h iterated from (3*64/(4 pi N))^(1/3)", "unit": UNIT}
+    for name, mode, g in (("individual", sg.INDIVIDUAL, 1), ("grouped", sg.GROUPED, 16)):
+        def call():
+            h.fill_(d["h0"])
+            c.density(act, h, 1, mode, g, rho, drho, fg, nn)
+        ms = _median_ms(torch, call, reps)
+        u1[name] = {"ms": ms, "value": n / (ms / 1e3), "iterations": c.stats()["iterations"]}
+    c.close()
+    out["uniform_32768"] = u1
+    # clustered 2^21, 20% active, group-size sweep
+    n = 1 << 21
+    d = sphgen.make("clustered", n, config=2, seed_salt=rank)
+    pos = torch.from_numpy(d["pos"]).to(dev)
+    m = torch.from_numpy(d["m"].astype(np.float32)).to(dev)
+    vel = torch.from_numpy(d["vel"].astype(np.float32)).to(dev)
+    u = torch.from_numpy(d["u"].astype(np.float32)).to(dev)
+    c = sg.Context(n)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    c.sfc_keys_sort(pos, None, perm)
+    c.tree_build(pos, m)
+    allact = torch.arange(n, dtype=torch.int32, device=dev)
+    h = torch.full((n,), d["h0"], dtype=torch.float64, device=dev)
+    rho, drho, fg = (torch.zeros(n, **f32) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=dev)
+    c.density(allact, h, 1, sg.GROUPED, 16, rho, drho, fg, nn)
+    mask = sphgen.active_rank_mask(n, 0.2, 32.0, np.random.default_rng(1000 + rank))
+    act = torch.from_numpy(np.sort(perm.cpu().numpy()[np.flatnonzero(mask)]).astype(np.int32)).to(dev)
+    na = int(act.shape[0])
+    acc, dudt = torch.zeros((n, 3), **f32), torch.zeros(n, **f32)
+    sweep = {"workload": f"clustered N={n}, 20% active in key-order runs (mean 32), converged h; one density and "
+                         "one hydro pass", "n_active": na, "unit": UNIT}
+    for g in (0, 1, 4, 8, 16, 32, 64, 128):
+        mode, gs = (sg.INDIVIDUAL, 1) if g == 0 else (sg.GROUPED, g)
+        md = _median_ms(torch, lambda: c.density(act, h, 0, mode, gs, rho, drho, fg, nn), reps)
+        st = c.stats()
+        mh = _median_ms(torch, lambda: c.hydro_force(act, h, rho, fg, vel, u, mode, gs, acc, dudt), reps)
+        sweep["individual" if g == 0 else f"g{g}"] = {
+            "density_ms": md, "hydro_ms": mh, "value": na / ((md + mh) / 1e3),
+            "members_per_walk": st["members"] / max(1, st["walks"]),
+            "candidates_per_member": st["candidates"] / max(1, st["members"])}
+    best = max((k for k in sweep if k.startswith("g")), key=lambda k: sweep[k]["value"])
+    sweep["best"] = best
+    sweep["speedup_best_vs_individual"] = sweep[best]["value"] / sweep["individual"]["value"]
+    c.close()
+    out["clustered_2M_20pct_sweep"] = sweep
+    return out
+
+
+def halo_leg(a, rank: int, world: int = 8) -> dict:
+    """The particle set split into `world` key-range domains (Sec. 1.2), on this one GPU:
+    how many particles the halo import moves (each domain's particles that another domain's
+    boxes reach, density and hydro), the time of the per-domain box and halo-selection
+    kernels, and the export volume of the paper's two-phase scheme (Sec. 2.3): a group
+    whose walk superset holds particles of another domain exports all its members there,
+    per group size g (g = 1: the per-particle walk)."""
+    import torch
+
+    import paper_1810_09898_gb300 as sg
+    import sphgen
+    from paper_1810_09898_gb300.domain import LibOps
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 1 << 21
+    d = sphgen.make("clustered", n, config=2, seed_salt=rank)
+    pos = torch.from_numpy(d["pos"]).to(dev)
+    m = torch.from_numpy(d["m"].astype(np.float32)).to(dev)
+    c = sg.Context(n)
+    keys = torch.empty(n, dtype=torch.int64, device=dev)
+    c.sfc_keys_sort(pos, keys)
+    c.tree_build(pos, m)
+    act = torch.arange(n, dtype=torch.int32, device=dev)
+    h = torch.full((n,), d["h0"], dtype=torch.float64, device=dev)
+    f32 = dict(dtype=torch.float32, device=dev)
+    rho, drho, fg = (torch.zeros(n, **f32) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device=dev)
+    c.density(act, h, 1, sg.GROUPED, 16, rho, drho, fg, nn)
+    split = keys[[n * j // world for j in range(1, world)]].contiguous()
+    lib = LibOps()
+    mask = lib.owner_mask(pos, split)
+    owner = sum(w * ((mask >> w) & 1) for w in range(world))   # the set bit's index
+    doms = [torch.nonzero(owner == r).flatten() for r in range(world)]
+    out = {"workload": f"clustered N={n}, converged h, {world} key-range domains"}
+    for level in (3, 4):
+        boxes, ranks = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(world):
+            b = lib.boxes(pos[doms[r]].contiguous(), m[doms[r]].contiguous(), h[doms[r]].contiguous(), level)
+            boxes.append(b)
+            ranks.append(torch.full((b.shape[0],), r, dtype=torch.int32, device=dev))
+        B, R = torch.cat(boxes).contiguous(), torch.cat(ranks).contiguous()
+        rec = {"boxes": int(B.shape[0])}
+        for kind, name in ((0, "density"), (1, "hydro")):
+            ghosts = 0
+            for r in range(world):
+                mk = lib.halo_mask(pos[doms[r]].contiguous(), m[doms[r]].contiguous(), h[doms[r]].contiguous(), kind,
+                                   1.0, B, R, r, world)
+                ghosts += int(sum(((mk >> w) & 1).sum().item() for w in range(world)))
+            rec[f"import_{name}_per_particle"] = ghosts / n
+        torch.cuda.synchronize()
+        rec["boxes_and_selection_s"] = time.perf_counter() - t0
+        out[f"level{level}"] = rec
+    lib.close()
+    # the export volume of the two-phase scheme, per group size
+    exp = {}
+    for g in (1, 4, 8, 16, 32, 64):
+        goff = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        ng, total = c.group_supersets(act, h, 0, g, goff)
+        gfirst = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        mem = torch.empty(n, dtype=torch.int32, device=dev)
+        cand = torch.empty(total, dtype=torch.int32, device=dev)
+        c.group_supersets(act, h, 0, g, goff, gfirst, mem, cand, cap=total)
+        cg = torch.repeat_interleave(torch.arange(ng, device=dev), (goff[1:ng + 1] - goff[:ng]))
+        present = torch.zeros(ng * world, dtype=torch.int64, device=dev)
+        present[cg * world + owner[cand.long()]] = 1
+        present = present.view(ng, world)
+        mg = torch.repeat_interleave(torch.arange(ng, device=dev), (gfirst[1:ng + 1] - gfirst[:ng]).long())
+        other = present.sum(1)[mg] - present[mg, owner[mem.long()]]
+        exp[f"g{g}"] = int(other.sum().item()) / n
+        del cand, goff
+    out["export_per_particle"] = exp
+    out["export_g16_over_g1"] = exp["g16"] / max(exp["g1"], 1e-30)
+    c.close()
+    return out
+
+
 def measured_peak_hbm() -> float:
     try:
         return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
@@ -827,6 +984,8 @@ def run_ours(a):
     batch = None
     if not a.no_batch:
         batch = guarded(batch_leg, a, rank, steps, warmup)
+    small = None if a.no_small else guarded(small_configs_leg, a, rank)
+    halo = None if a.no_halo else guarded(halo_leg, a, rank)
     peak = measured_peak_hbm()
     roof, detail = roofline(col_g, peak, clocks)
     cpu = None
@@ -862,6 +1021,8 @@ def run_ours(a):
         "active_10pct": low_active,
         "backward": back,
         "batch": batch,
+        "small_configs": small,
+        "domain_halo": halo,
     }
     if ms_i is not None:
         ri, di = roofline(col_i, peak, clocks, form="individual")

@@ -440,11 +440,11 @@ int sphgrp_halo_select(sphgrp_ctx* ctx, const double* h, int kind, double widen,
                        const double* boxes, const int32_t* box_rank, int self_rank, int world,
                        uint64_t* mask, int64_t* counts, cudaStream_t stream);
 
-/* sphgrp_mask_compact: the particles (caller order, ascending) with bit `bit` of mask
- * (device n uint64) set, to idx (device, n int32); *count (host) receives how many.
- * Synchronises the stream. */
-int sphgrp_mask_compact(sphgrp_ctx* ctx, const uint64_t* mask, int bit, int32_t* idx, int64_t* count,
-                        cudaStream_t stream);
+/* sphgrp_mask_compact: the entries (ascending) with bit `bit` of mask (device n uint64,
+ * 1 <= n <= n_max; the context only lends its scan workspace) set, to idx (device, n
+ * int32); *count (host) receives how many.  Synchronises the stream. */
+int sphgrp_mask_compact(sphgrp_ctx* ctx, int64_t n, const uint64_t* mask, int bit, int32_t* idx,
+                        int64_t* count, cudaStream_t stream);
 
 /* Keys + stable sort (as sphgrp_sfc_keys_sort) without any device allocation, for
  * callers that may not call cudaMalloc / cudaFree: plug-ins whose host application

@@ -159,7 +159,7 @@ def load_library():
     L.sphgrp_key_split.argtypes = [P, I32, P, P, P]
     L.sphgrp_domain_boxes.argtypes = [P, P, I32, I32, P, ctypes.POINTER(I32), P]
     L.sphgrp_halo_select.argtypes = [P, P, I32, ctypes.c_double, I32, P, P, I32, I32, P, P, P]
-    L.sphgrp_mask_compact.argtypes = [P, P, I32, P, ctypes.POINTER(I64), P]
+    L.sphgrp_mask_compact.argtypes = [P, I64, P, I32, P, ctypes.POINTER(I64), P]
     L.sphgrp_velocity_derivs.argtypes = [P, I64, P, P, P, P, I32, P, P, P]
     L.sphgrp_backward.argtypes = [P, P, P, P, P, P, I32, P, P, P, P]
     L.sphgrp_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -353,8 +353,11 @@ class Context:
     def mask_compact(self, mask, bit, idx):
         """The particles with bit `bit` of mask, ascending, into idx (n int32); returns how many."""
         k = ctypes.c_int64()
-        _check(self._L.sphgrp_mask_compact(self._h, _arg(mask, "mask", _I64, self.n), int(bit),
-                                           _arg(idx, "idx", _I32, self.n), ctypes.byref(k), _stream()))
+        n = mask.shape[0]
+        if n == 0:
+            return 0
+        _check(self._L.sphgrp_mask_compact(self._h, n, _arg(mask, "mask", _I64, n), int(bit),
+                                           _arg(idx, "idx", _I32, n), ctypes.byref(k), _stream()))
         return k.value
 
     # -- a8

@@ -219,12 +219,12 @@ int sphgrp_halo_select(sphgrp_ctx* ctx, const double* h, int kind, double widen,
     return check_cuda(cudaGetLastError(), "halo select");
 }
 
-int sphgrp_mask_compact(sphgrp_ctx* ctx, const uint64_t* mask, int bit, int32_t* idx, int64_t* count,
+int sphgrp_mask_compact(sphgrp_ctx* ctx, int64_t n, const uint64_t* mask, int bit, int32_t* idx, int64_t* count,
                         cudaStream_t s) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (!c) return set_error(SPHGRP_EINVAL, "null context");
+    if (n < 1 || n > c->n_max) return set_error(SPHGRP_EINVAL, "n outside [1, n_max]");
     if (!mask || !idx || !count || bit < 0 || bit > 63) return set_error(SPHGRP_EINVAL, "bad bit or null array");
-    const int64_t n = c->n;
     k_mask_bit<<<blocks_for(n, 256), 256, 0, s>>>(n, mask, bit, c->flag);
     note_launch();
     int32_t* total = reinterpret_cast<int32_t*>(c->work) + 25;

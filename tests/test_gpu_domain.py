@@ -48,7 +48,7 @@ def _split(d, world):
     mask = lib.owner_mask(_t(d["pos"]), torch.as_tensor(split, device="cuda:0")).cpu().numpy()
     cpu = CpuOps(oracle).owner_mask(torch.from_numpy(d["pos"]), torch.from_numpy(split)).numpy()
     assert np.array_equal(mask, cpu)
-    owner = np.log2(mask.astype(np.float64)).astype(np.int64)
+    owner = sum(w * ((mask >> w) & 1) for w in range(world))   # the set bit's index
     lib.close()
     return owner
 
