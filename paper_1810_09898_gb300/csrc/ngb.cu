@@ -82,8 +82,11 @@ __device__ __forceinline__ float radius2_units(float r_box) {
 
 // Members farther than this many smoothing lengths from the group centre (per axis)
 // evaluate the pair physics from exact fixed-point differences: the FP32 difference of
-// two large centre-relative coordinates would lose up to |m| / h ulps of r.
-constexpr float kPreciseReach = 2.0f;
+// two centre-relative coordinates loses up to |m| / h ulps of r, so below this reach the
+// pair terms carry at most about 8 ulps (1e-6 relative) of error, far inside the density
+// (1e-5) and acceleration (1e-4) bars; the decisions are exact at any reach (the band's
+// |m|^2 term).  The exact path reloads both fixed-point records from global memory.
+constexpr float kPreciseReach = 8.0f;
 
 // x_j - x_k from the fixed-point layout: exact integer minimum image plus the offsets.
 __device__ __forceinline__ float fix_diff(uint32_t Xj, float oj, uint32_t Xk, float ok) {
@@ -1935,8 +1938,11 @@ __global__ void __launch_bounds__(128) k_indiv(SearchArgs a) {
 
 // ---------------------------------------------------------------------------------
 // Grouping: chunks of g consecutive entries of the work list, each split in halves
-// (recursively) while the group's search sphere, ((sqrt(3)/2) box width + h_min)^3,
-// exceeds split * (members) member spheres h_min^3.
+// (recursively) while the group's search sphere -- centred on the members' box, radius
+// R = max_k (|x_k - c| + h_k), the walk's own radius -- exceeds split * (members)
+// spheres of the smallest h: the candidates its densest member filters, against the
+// members' own.  A member of large h beside dense ones (at the edge of a clump) widens
+// every member's superset, and the radius sees it.
 // ---------------------------------------------------------------------------------
 
 __global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, float split,
@@ -1966,11 +1972,21 @@ __global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, flo
                 loz = min(loz, dz); hiz = max(hiz, dz);
                 hmin = fminf(hmin, (float)h64[rk]);
             }
-            float ext = fmaxf(fmaxf((float)((int64_t)hix - lox), (float)((int64_t)hiy - loy)),
-                              (float)((int64_t)hiz - loz)) * kUnitToBox;
-            // search sphere of the group (box centre) relative to one member's sphere,
-            // in volume: the candidates every member filters, per member's own
-            float rel = fmaf(0.8660254f, ext / hmin, 1.0f);
+            // the search sphere about the box centre, as the walk will take it
+            const float cxf = 0.5f * (float)((int64_t)lox + hix), cyf = 0.5f * (float)((int64_t)loy + hiy),
+                        czf = 0.5f * (float)((int64_t)loz + hiz);
+            float R = 0.0f;
+            for (int k = s; k < e; ++k) {
+                int rk = U[k];
+                uint4 P = pfix[rk];
+                const float dx = ((float)(int32_t)(P.x - P0.x) - cxf) * kUnitToBox;
+                const float dy = ((float)(int32_t)(P.y - P0.y) - cyf) * kUnitToBox;
+                const float dz = ((float)(int32_t)(P.z - P0.z) - czf) * kUnitToBox;
+                R = fmaxf(R, sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) + (float)h64[rk]);
+            }
+            // relative to the densest member's sphere, in volume: the candidates that
+            // member filters, per its own
+            const float rel = R / hmin;
             keep = rel * rel * rel <= split * (float)(e - s);
         }
         if (keep) {

@@ -232,8 +232,9 @@ __device__ __forceinline__ double exact_r2(const double* xd, const double* yd, c
 //  * H^2 in FP32 from the FP64 square (and h_j^2 from the FP32 h_j): within 3u H^2.
 // The band (3 kBandRel H^2 + 8 kBandRel |m|^2) exceeds every bound at least 6-fold in
 // the H^2 term and 16-fold in the |m|^2 term, for members at any distance from the
-// centre and for wrapped groups.  Members farther than kPreciseReach h from the centre
-// take their pair physics (not their decisions) from exact fixed-point differences.
+// centre and for wrapped groups.  Members farther than kPreciseReach h (8 h) from the
+// centre take their pair physics (not their decisions) from exact fixed-point
+// differences; nearer ones lose at most about 8 ulps of r in the FP32 difference.
 constexpr float kBandRel = 3.814697265625e-06f;  // 2^-18
 
 // Radix sort tile (sort.cu): 256 threads x 8 keys; the digit histograms take 256
