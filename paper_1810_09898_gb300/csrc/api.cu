@@ -150,6 +150,36 @@ __global__ void k_velocity_prep(int64_t n, const int32_t* __restrict__ perm, con
     hyd1[r] = make_float4(0.0f, rho[i], 1.0f / hf, s);
 }
 
+// Results of the hydro loop from key order to the caller's order, over the caller's
+// active list (ascending active lists give sequential writes).
+__global__ void k_out_hydro(int64_t n_act, const int32_t* __restrict__ active, const int32_t* __restrict__ rank_of,
+                            const float4* __restrict__ res4, const int32_t* __restrict__ rcnt,
+                            float* __restrict__ acc, float* __restrict__ dudt, int32_t* __restrict__ nngb) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_act) return;
+    const int64_t i = active[k];
+    const int r = rank_of[i];
+    const float4 v = res4[r];
+    acc[3 * i] = v.x;
+    acc[3 * i + 1] = v.y;
+    acc[3 * i + 2] = v.z;
+    dudt[i] = v.w;
+    if (nngb) nngb[i] = rcnt[r];
+}
+
+// div v and curl v from key order to the caller's order
+__global__ void k_out_vel(int64_t n_act, const int32_t* __restrict__ active, const int32_t* __restrict__ rank_of,
+                          const float4* __restrict__ res4, float* __restrict__ divv, float* __restrict__ curlv) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_act) return;
+    const int64_t i = active[k];
+    const float4 v = res4[rank_of[i]];
+    divv[i] = v.x;
+    curlv[3 * i] = v.y;
+    curlv[3 * i + 1] = v.z;
+    curlv[3 * i + 2] = v.w;
+}
+
 __global__ void k_counts_by_caller(int64_t n_act, const int32_t* __restrict__ active,
                                    const int64_t* __restrict__ cnt, int64_t* __restrict__ out) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -514,6 +544,7 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     rc |= dalloc(&c->scan_aux, c->scan_aux_cap);
     rc |= dalloc(&c->lo, n);
     rc |= dalloc(&c->hi, n);
+    rc |= dalloc(&c->res4, n);
     rc |= dalloc(&c->acc_rho, n);
     rc |= dalloc(&c->acc_drho, n);
     rc |= dalloc(&c->acc_n, n);
@@ -546,7 +577,7 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
     if (!c) return SPHGRP_OK;
     void* ptrs[] = {c->keys, c->keys_alt, c->perm, c->perm_alt, c->rank_of, c->hist, c->xd, c->yd,
                     c->zd, c->pfix, c->poff, c->h64, c->hyd0, c->hyd1, c->act, c->act2, c->flag,
-                    c->scan, c->scan_aux, c->lo, c->hi, c->acc_rho, c->acc_drho, c->acc_n,
+                    c->scan, c->scan_aux, c->lo, c->hi, c->res4, c->acc_rho, c->acc_drho, c->acc_n,
                     c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
                     c->acc_s2, c->wadj, c->dadj, c->adj0, c->adj1, c->adj2, c->adj3,
                     c->stack_spill, c->start_tab, c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
@@ -945,13 +976,17 @@ int hydro_force(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, const dou
     a.g = grouped ? group_size : 1;
     a.ngroups = grouped ? (nu + group_size - 1) / group_size : nu;
     if (grouped && (rc = make_groups(c, &a, c->act, nu, group_size, s))) return rc;
-    a.o_acc = acc;
-    a.o_dudt = dudt;
-    a.o_nh = nngb;
+    a.o_res4 = c->res4;
+    a.o_rcnt = c->acc_n;
     timer_begin(c, s);
     rc = launch_search(a, SPHGRP_HYDRO, kAcc, grouped, c->sm_count, s);
     timer_end(c, s, a.nu);
     if (rc) return rc;
+    if (n_act > 0) {
+        k_out_hydro<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->rank_of, c->res4, c->acc_n, acc, dudt,
+                                                          nngb);
+        note_launch();
+    }
     c->last.walks = a.ngroups;
     c->last.members = nu;
     return finish(c, s, 0);
@@ -1013,12 +1048,15 @@ int sphgrp_velocity_derivs(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active
     a.g = group_size;
     a.ngroups = (nu + group_size - 1) / group_size;
     if ((rc = make_groups(c, &a, c->act, nu, group_size, s))) return rc;
-    a.o_divv = divv;
-    a.o_curl = curlv;
+    a.o_res4 = c->res4;
     timer_begin(c, s);
     rc = launch_search(a, kKindVelocity, kAcc, true, c->sm_count, s);
     timer_end(c, s, a.nu);
     if (rc) return rc;
+    if (n_act > 0) {
+        k_out_vel<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->rank_of, c->res4, divv, curlv);
+        note_launch();
+    }
     c->last.walks = a.ngroups;
     c->last.members = nu;
     return finish(c, s, 0);

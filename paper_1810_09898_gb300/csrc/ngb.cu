@@ -1068,6 +1068,13 @@ __device__ __forceinline__ void write_result(const DVMember& D, const SearchArgs
 }
 template <int MODE>
 __device__ __forceinline__ void write_result(const HMember& H, const SearchArgs& a) {
+    if (MODE == kAcc && a.o_res4) {
+        // key order: the members of a group are consecutive ranks, so these writes are
+        // contiguous; a gather pass moves them to the caller's order
+        a.o_res4[H.rank] = make_float4(H.sx - H.cx_, H.sy - H.cy_, H.sz - H.cz_, H.su - H.cu);
+        a.o_rcnt[H.rank] = H.n - 1;   // the member itself was counted as a pair
+        return;
+    }
     int orig = a.perm[H.rank];
     if (MODE == kAcc) {
         a.o_acc[3 * (int64_t)orig] = H.sx - H.cx_;
@@ -1089,6 +1096,11 @@ __device__ __forceinline__ void write_result(const HAMember& H, const SearchArgs
 template <int MODE>
 __device__ __forceinline__ void write_result(const VMember& V, const SearchArgs& a) {
     if (MODE != kAcc) return;
+    if (a.o_res4) {
+        a.o_res4[V.rank] = make_float4(V.rrho * (V.sd - V.cd), V.rrho * (V.sx - V.cx_), V.rrho * (V.sy - V.cy_),
+                                       V.rrho * (V.sz - V.cz_));
+        return;
+    }
     const int orig = a.perm[V.rank];
     a.o_divv[orig] = V.rrho * (V.sd - V.cd);
     a.o_curl[3 * (int64_t)orig] = V.rrho * (V.sx - V.cx_);

@@ -121,6 +121,11 @@ struct SearchArgs {
     // velocity derivatives (original order)
     float* o_divv;
     float* o_curl;        // n x 3
+    // hydro / velocity-derivative results in key order (rank space, one float4 per
+    // member: {a, du/dt} or {div v, curl v}) and the hydro neighbour counts; null: the
+    // results go straight to the caller's order below
+    float4* o_res4;
+    int32_t* o_rcnt;
     // hydro results (original order)
     float* o_acc;
     float* o_dudt;

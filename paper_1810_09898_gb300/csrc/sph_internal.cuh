@@ -116,6 +116,7 @@ struct Ctx {
     int64_t scan_aux_cap = 0;
     double* lo = nullptr;          // bracket of the iteration
     double* hi = nullptr;
+    float4* res4 = nullptr;        // per-rank results of the hydro / velocity loops (key order)
     float* acc_rho = nullptr;      // per-rank density sums of the current pass
     float* acc_drho = nullptr;
     int32_t* acc_n = nullptr;
