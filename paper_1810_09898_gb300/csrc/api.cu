@@ -94,15 +94,18 @@ __global__ void k_gather_h(int64_t n, const int32_t* __restrict__ perm, const do
 // Hydro inputs in key order: hyd0 = {v, c}, hyd1 = {A = f P / rho^2, rho, 1/h, fbal}.
 // fbal is Balsara's viscosity limiter |div v| / (|div v| + |curl v| + 1e-4 c / h) when the
 // caller gives div v and curl v, else 1 (the plain Monaghan viscosity).
+// One thread per rank: the caller-order inputs are gathered through the permutation and
+// the key-ordered records written coalesced (the scattered-store form, one thread per
+// caller index, measured 1.6x slower: its partial-sector writes cost more than these loads).
 __global__ void k_hydro_prep(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ h,
                              const float* __restrict__ rho, const float* __restrict__ fgrad,
                              const float* __restrict__ vel, const float* __restrict__ u, float gamma,
                              double* __restrict__ h64, uint4* __restrict__ pfix, float4* __restrict__ hyd0,
                              float4* __restrict__ hyd1, unsigned* err, const float* __restrict__ divv,
                              const float* __restrict__ curlv) {
-    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
-    int i = perm[r];
+    const int i = perm[r];
     double hv = h[i];
     if (!(hv > 0.0 && hv < 0.5)) atomicOr(err, kErrH);
     h64[r] = hv;

@@ -195,7 +195,9 @@ int exclusive_scan_i64(Ctx* c, const int64_t* in, int64_t* out, int64_t n, int64
 // exclusive scan, and a scatter that ranks keys inside the tile with warp matching.
 // A tile is 256 threads x 8 keys; warp w owns the contiguous 256 keys
 // [w*256, w*256+256) of the tile, processed 32 at a time in order, so ranks follow
-// the input order (stability).
+// the input order (stability).  The scatter first sorts the tile by digit in shared
+// memory, then writes every digit's run with consecutive threads on consecutive
+// addresses (about 8 keys per run and tile), instead of one scattered store per key.
 // ---------------------------------------------------------------------------------
 
 constexpr int kSortWarps = kSortThreads / 32;
@@ -215,17 +217,23 @@ __global__ void k_radix_hist(const uint64_t* __restrict__ keys, int64_t n, int s
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t* __restrict__ vin,
-                                uint64_t* __restrict__ kout, int32_t* __restrict__ vout,
-                                int64_t n, int shift, const uint32_t* __restrict__ offs,
-                                int nblocks) {
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint64_t* __restrict__ kin,
+                                                                const int32_t* __restrict__ vin,
+                                                                uint64_t* __restrict__ kout,
+                                                                int32_t* __restrict__ vout, int64_t n, int shift,
+                                                                const uint32_t* __restrict__ offs, int nblocks) {
     __shared__ uint32_t wh[kSortWarps][256];
-    __shared__ uint32_t gbase[256];
+    __shared__ uint32_t gbase[256];    // global position of the tile's run of every digit
+    __shared__ uint32_t lbase[256];    // tile-local position of the same run
+    __shared__ uint32_t wsum[kSortWarps];
+    __shared__ uint64_t sk[kSortTile];  // the tile, sorted by digit (stable)
+    __shared__ int32_t sv[kSortTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < kSortWarps * 256; d += kSortThreads) (&wh[0][0])[d] = 0;
     gbase[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
     __syncthreads();
-    const int64_t base = blockIdx.x * (int64_t)kSortTile + w * 256;
+    const int64_t tile0 = blockIdx.x * (int64_t)kSortTile;
+    const int64_t base = tile0 + w * 256;
     const uint32_t lt = (1u << lane) - 1u;
     uint64_t kk[kSortItems];
     int32_t vv[kSortItems];
@@ -246,7 +254,8 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t*
         rk[r] = prev + __popc(peers & lt);
     }
     __syncthreads();
-    // exclusive prefix over warps for every digit (thread t owns digit t)
+    // per digit (thread t owns digit t): exclusive prefix over the warps, then the
+    // tile-local start of the digit's run (exclusive scan of the digit totals)
     {
         uint32_t run = 0;
         const int d = threadIdx.x;
@@ -256,17 +265,39 @@ __global__ void k_radix_scatter(const uint64_t* __restrict__ kin, const int32_t*
             wh[ww][d] = run;
             run += c;
         }
+        uint32_t v = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane == 31) wsum[w] = v;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int ww = 0; ww < w; ++ww) off += wsum[ww];
+        lbase[d] = off + v - run;
     }
     __syncthreads();
+    // the tile in digit order in shared memory
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         int64_t i = base + r * 32 + lane;
         if (i < n) {
-            uint32_t d = (uint32_t)((kk[r] >> shift) & 0xffu);
-            uint32_t p = gbase[d] + wh[w][d] + rk[r];
-            kout[p] = kk[r];
-            vout[p] = vv[r];
+            const uint32_t d = (uint32_t)((kk[r] >> shift) & 0xffu);
+            const uint32_t p = lbase[d] + wh[w][d] + rk[r];
+            sk[p] = kk[r];
+            sv[p] = vv[r];
         }
+    }
+    __syncthreads();
+    // runs of equal digits go out with consecutive threads on consecutive addresses
+    const int cnt = (int)min((int64_t)kSortTile, n - tile0);
+    for (int e = threadIdx.x; e < cnt; e += kSortThreads) {
+        const uint64_t key = sk[e];
+        const uint32_t d = (uint32_t)((key >> shift) & 0xffu);
+        const uint32_t p = gbase[d] + ((uint32_t)e - lbase[d]);
+        kout[p] = key;
+        vout[p] = sv[e];
     }
 }
 

@@ -33,14 +33,33 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const doub
 
 __device__ __forceinline__ int key_digit(uint64_t key, int shift) { return (int)((key >> shift) & 7u); }
 
-// first index in [lo, hi) whose digit is >= d (digits are non-decreasing in the range)
-__device__ __forceinline__ int lower_digit(const uint64_t* keys, int lo, int hi, int shift, int d) {
-    while (lo < hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        if (key_digit(keys[mid], shift) < d) lo = mid + 1;
-        else hi = mid;
+// Octant boundaries of the key range [lo, hi) (hi > lo) at the digit of `shift`: b[d] is
+// the first index whose digit is >= d, b[0] = lo, b[8] = hi (digits are non-decreasing
+// in the range).  The seven lower bounds run in lockstep: each step halves a range of
+// the same length for all of them, so their loads are independent and a node's search
+// costs the latency of one binary search, not of seven in a row.
+__device__ __forceinline__ void octant_bounds(const uint64_t* __restrict__ keys, int lo, int hi, int shift,
+                                              int (&b)[9]) {
+    int base[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) base[d] = lo;
+    // invariant: indices below base[d] have digit < d + 1, and the bound lies in
+    // [base[d], base[d] + n]
+    int n = hi - lo;
+    while (n > 1) {
+        const int half = n >> 1;
+        int dg[7];
+#pragma unroll
+        for (int d = 0; d < 7; ++d) dg[d] = key_digit(keys[base[d] + half], shift);
+#pragma unroll
+        for (int d = 0; d < 7; ++d)
+            if (dg[d] < d + 1) base[d] += half;
+        n -= half;
     }
-    return lo;
+    b[0] = lo;
+    b[8] = hi;
+#pragma unroll
+    for (int d = 0; d < 7; ++d) b[d + 1] = base[d] + (key_digit(keys[base[d]], shift) < d + 1 ? 1 : 0);
 }
 
 // Number of non-empty octants of every node of one level that must split.
@@ -51,14 +70,10 @@ __global__ void k_split_count(const uint64_t* __restrict__ keys, const int4* __r
     int4 L = nlink[a + k];
     int cnt = 0;
     if (L.y > leaf_size && level < kKeyLevels) {
-        int shift = 3 * (kKeyLevels - 1 - level);
-        int lo = L.x, hi = L.x + L.y;
-        int prev = lo;
-        for (int d = 1; d <= 8; ++d) {
-            int b = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
-            if (b > prev) ++cnt;
-            prev = b;
-        }
+        int b[9];
+        octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), b);
+#pragma unroll
+        for (int d = 0; d < 8; ++d) cnt += b[d + 1] > b[d] ? 1 : 0;
     }
     nchild[k] = cnt;
 }
@@ -74,20 +89,19 @@ __global__ void k_split_write(const uint64_t* __restrict__ keys, int4* __restric
     int4 L = nlink[a + k];
     next[a + k].w = __int_as_float(nc);
     if (nc == 0) return;
-    int shift = 3 * (kKeyLevels - 1 - level);
     int child0 = b + coff[k];
-    int lo = L.x, hi = L.x + L.y;
-    int prev = lo, c = 0;
-    for (int d = 1; d <= 8; ++d) {
-        int e = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
-        if (e > prev) {
+    int bd[9];
+    octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), bd);
+    int c = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        if (bd[d + 1] > bd[d]) {
             int id = child0 + c;
             int skip = (c + 1 < nc) ? id + 1 : L.w;
-            nlink[id] = make_int4(prev, e - prev, -1, skip);
+            nlink[id] = make_int4(bd[d], bd[d + 1] - bd[d], -1, skip);
             nlevel[id] = level + 1;
             ++c;
         }
-        prev = e;
     }
     L.z = child0;
     nlink[a + k] = L;
@@ -324,14 +338,10 @@ __global__ void k_split_count_dev(const uint64_t* __restrict__ keys, const int4*
         int4 L = nlink[a + k];
         int cnt = 0;
         if (L.y > leaf_size && level < kKeyLevels) {
-            int shift = 3 * (kKeyLevels - 1 - level);
-            int lo = L.x, hi = L.x + L.y;
-            int prev = lo;
-            for (int d = 1; d <= 8; ++d) {
-                int b = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
-                if (b > prev) ++cnt;
-                prev = b;
-            }
+            int b[9];
+            octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), b);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) cnt += b[d + 1] > b[d] ? 1 : 0;
         }
         nchild[k] = cnt;
     }
@@ -354,20 +364,19 @@ __global__ void k_split_write_dev(const uint64_t* __restrict__ keys, int4* __res
             continue;
         }
         next[a + k].w = __int_as_float(nc);
-        const int shift = 3 * (kKeyLevels - 1 - level);
-        const int lo = L.x, hi = L.x + L.y;
-        int prev = lo, c = 0;
-        for (int d = 1; d <= 8; ++d) {
-            const int e = (d == 8) ? hi : lower_digit(keys, prev, hi, shift, d);
-            if (e > prev) {
+        int bd[9];
+        octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), bd);
+        int c = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            if (bd[d + 1] > bd[d]) {
                 const int id = child0 + c;
                 const int skip = (c + 1 < nc) ? id + 1 : L.w;
-                nlink[id] = make_int4(prev, e - prev, -1, skip);
+                nlink[id] = make_int4(bd[d], bd[d + 1] - bd[d], -1, skip);
                 next[id] = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(0));
                 nlevel[id] = level + 1;
                 ++c;
             }
-            prev = e;
         }
         L.z = child0;
         nlink[a + k] = L;
