@@ -2293,19 +2293,6 @@ __device__ __forceinline__ HsmlStep hsml_next(double h, float m, float s0, float
     return o;
 }
 
-// results of a finished particle (caller's order; rho, dRho/dh and f are FP32 outputs)
-__device__ __forceinline__ void hsml_write(int orig, double h, float s0, float s1, int n, int pass, double* h_out,
-                                          float* rho, float* drhodh, float* fgrad, int32_t* nngb_out,
-                                          int32_t* iters) {
-    const float hf = (float)h;
-    const float sigma = 2.54647908947032537f / (hf * hf * hf);   // 8 / (pi h^3)
-    rho[orig] = sigma * s0;
-    drhodh[orig] = -sigma / hf * s1;
-    fgrad[orig] = 3.0f * s0 / (3.0f * s0 - s1);
-    nngb_out[orig] = n;
-    if (iters) iters[orig] = pass;
-    h_out[orig] = h;
-}
 
 // One particle's pass of the smoothing-length iteration: u = its work-list entry, r its
 // rank, s0 / s1 / n its density sums at the current h.  Runs as its own kernel with one
@@ -2320,8 +2307,12 @@ __device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, f
     double hi = pass == 1 ? __longlong_as_double(0x7ff0000000000000ll) : a.hi[r];
     const HsmlStep st = hsml_next(h, m, s0f, s1f, a.nngb, a.tol, a.iterate != 0, pass, a.max_iter, lo, hi);
     if (st.finish) {
-        hsml_write(a.perm[r], h, s0f, s1f, n, pass, a.h_out, a.rho, a.drhodh, a.fgrad, a.nngb_out, a.iters);
-        if (a.vsum) {
+        if (a.pass_k) {
+            a.pass_k[r] = pass;
+        } else {
+            hsml_write(a.perm[r], h, s0f, s1f, n, pass, a.h_out, a.rho, a.drhodh, a.fgrad, a.nngb_out, a.iters);
+        }
+        if (a.vsum && !a.pass_k) {
             // div v = -(1/rho) sum m v_ij . grad W, curl v = (1/rho) sum m v_ij x grad W
             const int orig = a.perm[r];
             const float hf = (float)h;

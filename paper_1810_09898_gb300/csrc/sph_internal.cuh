@@ -120,6 +120,7 @@ struct Ctx {
     float* acc_rho = nullptr;      // per-rank density sums of the current pass
     float* acc_drho = nullptr;
     int32_t* acc_n = nullptr;
+    int32_t* pass_k = nullptr;     // pass count of every finished particle (rank space)
     int64_t* cnt64 = nullptr;      // per-target pair counts (export)
     int2* groups = nullptr;        // group list of the current search (first, count)
     int2* groups_tmp = nullptr;
@@ -267,5 +268,19 @@ int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uin
                  int32_t* tot, const int32_t* box_of_rank, int32_t* start_tabs, cudaStream_t s); // tree.cu
 int refresh_hmax_forest(Ctx* c, const int32_t* lvl, cudaStream_t s);                       // tree.cu
 void note_launches(long long k);                                                           // api.cu
+
+// results of a finished particle (caller's order; rho, dRho/dh and f are FP32 outputs)
+__device__ __forceinline__ void hsml_write(int orig, double h, float s0, float s1, int n, int pass, double* h_out,
+                                          float* rho, float* drhodh, float* fgrad, int32_t* nngb_out,
+                                          int32_t* iters) {
+    const float hf = (float)h;
+    const float sigma = 2.54647908947032537f / (hf * hf * hf);   // 8 / (pi h^3)
+    rho[orig] = sigma * s0;
+    drhodh[orig] = -sigma / hf * s1;
+    fgrad[orig] = 3.0f * s0 / (3.0f * s0 - s1);
+    nngb_out[orig] = n;
+    if (iters) iters[orig] = pass;
+    h_out[orig] = h;
+}
 
 }  // namespace sphgrp

@@ -7,6 +7,27 @@
 
 namespace sphgrp {
 
+// x * 2^32 is exact; its floor is the fixed-point coordinate, the remainder (exact in
+// FP64, < 1) keeps the rest of the position and is rounded once to FP32.  For
+// 2^-32 <= x < 1 both come from the bits of x with integer operations (FP64 arithmetic
+// is a slow pipe on this part): x 2^32 = M 2^-s with M = 2^52 + f and s = 1043 - e in
+// [21, 52], so the floor is M >> s and the remainder (M mod 2^s) 2^-s, whose integer
+// part converts to FP32 with one rounding and scales by 2^-s exactly.  Other x take
+// the FP64 form.
+__device__ __forceinline__ uint32_t fix_split(double x, float& rem) {
+    const uint64_t b = __double_as_longlong(x);
+    const int e = (int)(b >> 52);   // biased exponent; the sign bit makes it >= 2048
+    const int s = 1043 - e;
+    if (s >= 21 && s <= 52) {
+        const uint64_t M = (b & 0xfffffffffffffull) | (1ull << 52);
+        rem = __ull2float_rn(M & ((1ull << s) - 1ull)) * __int_as_float((127 - s) << 23);
+        return (uint32_t)(M >> s);
+    }
+    const double sx = x * kBoxToUnit, fx = floor(sx);
+    rem = (float)(sx - fx);
+    return (uint32_t)fx;
+}
+
 // pos/m (original order) -> key-ordered FP64 copies and the fixed-point layout.
 __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const double* __restrict__ pos,
                          const float* __restrict__ m, double* __restrict__ xd, double* __restrict__ yd,
@@ -15,17 +36,14 @@ __global__ void k_gather(int64_t n, const int32_t* __restrict__ perm, const doub
     if (r >= n) return;
     int i = perm[r];
     double x = pos[3 * (int64_t)i], y = pos[3 * (int64_t)i + 1], z = pos[3 * (int64_t)i + 2];
-    // x * 2^32 is exact; its floor is the fixed-point coordinate, the remainder (exact in
-    // FP64, < 1) keeps the rest of the position and is rounded once to FP32.
-    double sx = x * kBoxToUnit, sy = y * kBoxToUnit, sz = z * kBoxToUnit;
-    double fx = floor(sx), fy = floor(sy), fz = floor(sz);
+    float ox, oy, oz;
     uint4 P;
-    P.x = (uint32_t)fx;
-    P.y = (uint32_t)fy;
-    P.z = (uint32_t)fz;
+    P.x = fix_split(x, ox);
+    P.y = fix_split(y, oy);
+    P.z = fix_split(z, oz);
     P.w = 0u;
     pfix[r] = P;
-    poff[r] = make_float4((float)(sx - fx), (float)(sy - fy), (float)(sz - fz), m[i]);
+    poff[r] = make_float4(ox, oy, oz, m[i]);
     xd[r] = x;
     yd[r] = y;
     zd[r] = z;
