@@ -2004,7 +2004,24 @@ __global__ void k_split_groups(const int32_t* __restrict__ U, int nu, int g, flo
         if (keep) {
             tmp[s0 + ng++] = make_int2(s, e - s);
         } else {
+            // Cut at the largest gap in key order (ties: the one nearest the middle): an
+            // active set made of runs along the curve splits where one run ends and the
+            // next begins; contiguous members split in the middle.  The stack holds one
+            // pending range per level of the current path; gap cuts, which may peel one
+            // member at a time, are taken while it holds fewer than 8, so that the
+            // halving below them (at most log2(128) = 7 more levels) stays within 16.
             int mid = s + (e - s + 1) / 2;
+            if (sp < 8) {
+                int best = 1, bk = mid;
+                for (int k = s + 1; k < e; ++k) {
+                    const int gap = U[k] - U[k - 1];
+                    if (gap > best || (gap == best && abs(k - mid) < abs(bk - mid))) {
+                        best = gap;
+                        bk = k;
+                    }
+                }
+                mid = bk;
+            }
             st[sp++] = make_int2(mid, e);
             st[sp++] = make_int2(s, mid);
         }

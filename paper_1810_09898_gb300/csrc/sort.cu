@@ -28,7 +28,7 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v) {
 // lower bits with axis 0 (bit clear); then a Gray code across the axes and a common
 // correction; the index interleaves the transposed words, axis 0 most significant.
 __device__ __forceinline__ uint64_t hilbert_key(uint32_t a0, uint32_t a1, uint32_t a2) {
-#pragma unroll 1
+#pragma unroll
     for (uint32_t q = 1u << (kKeyLevels - 1); q > 1u; q >>= 1) {
         const uint32_t lowmask = q - 1u;
         if (a0 & q) a0 ^= lowmask;
@@ -50,7 +50,7 @@ __device__ __forceinline__ uint64_t hilbert_key(uint32_t a0, uint32_t a1, uint32
     a1 ^= a0;
     a2 ^= a1;
     uint32_t corr = 0;
-#pragma unroll 1
+#pragma unroll
     for (uint32_t q = 1u << (kKeyLevels - 1); q > 1u; q >>= 1)
         if (a2 & q) corr ^= q - 1u;
     a0 ^= corr;

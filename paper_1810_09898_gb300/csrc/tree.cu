@@ -80,16 +80,60 @@ __device__ __forceinline__ void octant_bounds(const uint64_t* __restrict__ keys,
     for (int d = 0; d < 7; ++d) b[d + 1] = base[d] + (key_digit(keys[base[d]], shift) < d + 1 ? 1 : 0);
 }
 
+// Cells of the top levels 1 .. kTopLevels: the first index of every non-empty cell, in a
+// direct-indexed table per level (8^l entries at offset top_offset(l); -1 = empty).  A
+// level-l node (l < kTopLevels) then reads its octant bounds from the 8 entries of its
+// children instead of searching a key range of up to n keys, which at these levels is
+// one long chain of dependent loads for a handful of threads.
+constexpr int kTopLevels = 6;
+constexpr int kTopTableSize = 299592;   // 8 + 8^2 + ... + 8^6
+__host__ __device__ constexpr int top_offset(int l) { return ((1 << (3 * l)) - 8) / 7; }   // 8 + ... + 8^(l-1)
+static_assert(top_offset(kTopLevels + 1) == kTopTableSize, "top-level cell table size");
+
+// i starts a cell at every level deeper than the number of leading digits its key shares
+// with key i - 1 (digit j of a 63-bit key is bits 62 - 3j .. 60 - 3j, so the first
+// differing digit of x = k_i ^ k_{i-1} is (clz(x) - 1) / 3)
+__global__ void k_top_cells(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ tab) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = keys[i];
+    int d = 0;
+    if (i > 0) {
+        const uint64_t x = k ^ keys[i - 1];
+        d = x == 0 ? kKeyLevels : (__clzll((long long)x) - 1) / 3;
+    }
+    for (int l = d + 1; l <= kTopLevels; ++l) tab[top_offset(l) + (int)(k >> (3 * (kKeyLevels - l)))] = (int32_t)i;
+}
+
+// octant bounds of a node of level `level` over the keys [lo, hi): from the top-cell
+// table above the top levels (tab non-null), else by the lockstep search
+__device__ __forceinline__ void node_bounds(const uint64_t* __restrict__ keys, const int32_t* __restrict__ tab,
+                                            int level, int lo, int hi, int (&b)[9]) {
+    if (tab && level < kTopLevels) {
+        const int P = level == 0 ? 0 : (int)(keys[lo] >> (3 * (kKeyLevels - level)));
+        const int32_t* ch = tab + top_offset(level + 1) + 8 * P;
+        int st[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) st[d] = ch[d];
+        b[8] = hi;
+#pragma unroll
+        for (int d = 7; d >= 0; --d) b[d] = st[d] >= 0 ? st[d] : b[d + 1];
+        return;
+    }
+    octant_bounds(keys, lo, hi, 3 * (kKeyLevels - 1 - level), b);
+}
+
 // Number of non-empty octants of every node of one level that must split.
 __global__ void k_split_count(const uint64_t* __restrict__ keys, const int4* __restrict__ nlink,
-                              int a, int nf, int level, int leaf_size, int32_t* __restrict__ nchild) {
+                              int a, int nf, int level, int leaf_size, int32_t* __restrict__ nchild,
+                              const int32_t* __restrict__ tab) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nf) return;
     int4 L = nlink[a + k];
     int cnt = 0;
     if (L.y > leaf_size && level < kKeyLevels) {
         int b[9];
-        octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), b);
+        node_bounds(keys, tab, level, L.x, L.x + L.y, b);
 #pragma unroll
         for (int d = 0; d < 8; ++d) cnt += b[d + 1] > b[d] ? 1 : 0;
     }
@@ -100,7 +144,7 @@ __global__ void k_split_count(const uint64_t* __restrict__ keys, const int4* __r
 __global__ void k_split_write(const uint64_t* __restrict__ keys, int4* __restrict__ nlink,
                               float4* __restrict__ next, int32_t* __restrict__ nlevel, int a,
                               int nf, int level, const int32_t* __restrict__ nchild,
-                              const int32_t* __restrict__ coff, int b) {
+                              const int32_t* __restrict__ coff, int b, const int32_t* __restrict__ tab) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nf) return;
     int nc = nchild[k];
@@ -109,7 +153,7 @@ __global__ void k_split_write(const uint64_t* __restrict__ keys, int4* __restric
     if (nc == 0) return;
     int child0 = b + coff[k];
     int bd[9];
-    octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), bd);
+    node_bounds(keys, tab, level, L.x, L.x + L.y, bd);
     int c = 0;
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
@@ -261,29 +305,47 @@ int build_tree(Ctx* c, cudaStream_t s) {
     t.count = 1;
     int level = 0;
     int32_t* total_dev = reinterpret_cast<int32_t*>(c->work) + 12;
+    int32_t* top = nullptr;
+    if (cudaMallocAsync(&top, kTopTableSize * sizeof(int32_t), s) != cudaSuccess)
+        return set_error(SPHGRP_ENOMEM, "octree top-cell table");
+    cudaMemsetAsync(top, 0xff, kTopTableSize * sizeof(int32_t), s);
+    if (n > 0) {
+        k_top_cells<<<blocks_for(n, 256), 256, 0, s>>>(c->keys, n, top);
+        note_launch();
+    }
     for (level = 0; level <= kKeyLevels; ++level) {
         int a = t.level_begin[level], b = t.level_begin[level + 1];
         int nf = b - a;
         if (nf == 0) break;
         k_split_count<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, a, nf, level,
-                                                          c->p.leaf_size, c->flag);
+                                                          c->p.leaf_size, c->flag, top);
         note_launch();
         rc = exclusive_scan_i32(c, c->flag, c->scan, nf, total_dev, s);
-        if (rc) return rc;
+        if (rc) {
+            cudaFreeAsync(top, s);
+            return rc;
+        }
         cudaMemcpyAsync(c->host_small, total_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if ((rc = check_cuda(cudaStreamSynchronize(s), "octree level"))) return rc;
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "octree level"))) {
+            cudaFreeAsync(top, s);
+            return rc;
+        }
         int total = c->host_small[0];
         if (b + (int64_t)total > t.cap) {
-            if ((rc = grow_tree(c, b + (int64_t)total, s))) return rc;
+            if ((rc = grow_tree(c, b + (int64_t)total, s))) {
+                cudaFreeAsync(top, s);
+                return rc;
+            }
         }
         k_split_write<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, t.next, t.nlevel, a, nf,
-                                                          level, c->flag, c->scan, b);
+                                                          level, c->flag, c->scan, b, top);
         note_launch();
         t.level_begin[level + 2] = b + total;
         t.count = b + total;
         if (total == 0) { ++level; break; }
     }
     t.nlevels = level;
+    cudaFreeAsync(top, s);
     // boxes bottom-up (scratch for lo/hi boxes: the radix-sort key buffers, >= 16 B/node?)
     uint4* blo;
     uint4* bhi;
