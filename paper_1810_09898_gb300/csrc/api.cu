@@ -154,26 +154,26 @@ __global__ void k_velocity_prep(int64_t n, const int32_t* __restrict__ perm, con
 }
 
 // Results of the density loop and its smoothing-length iteration from key order to the
-// caller's order, over the caller's active list: the final h, the sums at that h and
-// the neighbour count stay in rank space (h64, s0, s1, n) when a particle finishes,
-// with its pass count, so that the outputs are written here in one coalesced pass
+// caller's order, over the caller's active list: the final h stays in h64 and the sums at
+// that h, the neighbour count and the pass count in one float4 (rank space) when a
+// particle finishes, so that the outputs are written here in one coalesced pass
 // instead of by scattered stores from the update kernel.  Indices outside [0, n) were
 // flagged by k_mark_active and are skipped.
 __global__ void k_out_density(int64_t n_act, const int32_t* __restrict__ active, int64_t n,
                               const int32_t* __restrict__ rank_of, const double* __restrict__ h64,
-                              const float* __restrict__ s0, const float* __restrict__ s1,
-                              const int32_t* __restrict__ cnt, const int32_t* __restrict__ pass_k,
-                              const float4* __restrict__ vsum, double* __restrict__ h_out, float* __restrict__ rho,
-                              float* __restrict__ drhodh, float* __restrict__ fgrad, int32_t* __restrict__ nngb,
-                              int32_t* __restrict__ iters, float* __restrict__ divv, float* __restrict__ curlv) {
+                              const float4* __restrict__ res_k, const float4* __restrict__ vsum,
+                              double* __restrict__ h_out, float* __restrict__ rho, float* __restrict__ drhodh,
+                              float* __restrict__ fgrad, int32_t* __restrict__ nngb, int32_t* __restrict__ iters,
+                              float* __restrict__ divv, float* __restrict__ curlv) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n_act) return;
     const int64_t i = active[k];
     if (i < 0 || i >= n) return;
     const int r = rank_of[i];
     const double h = h64[r];
-    const float a0 = s0[r], a1 = s1[r];
-    hsml_write((int)i, h, a0, a1, cnt[r], pass_k[r], h_out, rho, drhodh, fgrad, nngb, iters);
+    const float4 R = res_k[r];   // {s0, s1, count, pass count}
+    const float a0 = R.x, a1 = R.y;
+    hsml_write((int)i, h, a0, a1, __float_as_int(R.z), __float_as_int(R.w), h_out, rho, drhodh, fgrad, nngb, iters);
     if (vsum) {
         // div v = -(1/rho) sum m v_ij . grad W, curl v = (1/rho) sum m v_ij x grad W
         const float hf = (float)h;
@@ -588,7 +588,6 @@ int sphgrp_ctx_create(sphgrp_ctx** out, const sphgrp_params* p, int64_t n_max) {
     rc |= dalloc(&c->acc_rho, n);
     rc |= dalloc(&c->acc_drho, n);
     rc |= dalloc(&c->acc_n, n);
-    rc |= dalloc(&c->pass_k, n);
     rc |= dalloc(&c->cnt64, n + 1);
     rc |= dalloc(&c->groups, n + 1);
     rc |= dalloc(&c->groups_tmp, n + 1);
@@ -618,7 +617,7 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
     if (!c) return SPHGRP_OK;
     void* ptrs[] = {c->keys, c->keys_alt, c->perm, c->perm_alt, c->rank_of, c->hist, c->xd, c->yd,
                     c->zd, c->pfix, c->poff, c->h64, c->hyd0, c->hyd1, c->act, c->act2, c->flag,
-                    c->scan, c->scan_aux, c->lo, c->hi, c->res4, c->acc_rho, c->acc_drho, c->acc_n, c->pass_k,
+                    c->scan, c->scan_aux, c->lo, c->hi, c->res4, c->acc_rho, c->acc_drho, c->acc_n,
                     c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
                     c->acc_s2, c->wadj, c->dadj, c->adj0, c->adj1, c->adj2, c->adj3,
                     c->stack_spill, c->start_tab, c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
@@ -923,7 +922,7 @@ int density_call(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* 
         ua.npass = npass;
         // the recycled iteration's list passes write their finished particles directly;
         // the walk passes leave theirs in rank space for one gather after the loop
-        ua.pass_k = recycle ? nullptr : c->pass_k;
+        ua.res_k = recycle ? nullptr : c->res4;
         if (with_vel) {
             // the raw div / curl sums of the pass in hyd1 (not used by the density loop)
             a.o_vsum = c->hyd1;
@@ -990,8 +989,7 @@ int density_call(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, double* 
         }
     }
     if (!recycle && n_act > 0) {
-        k_out_density<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->n, c->rank_of, c->h64, c->acc_rho,
-                                                            c->acc_drho, c->acc_n, c->pass_k,
+        k_out_density<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->n, c->rank_of, c->h64, c->res4,
                                                             with_vel ? c->hyd1 : nullptr, h, rho, drhodh, fgrad,
                                                             nngb, iters, divv, curlv);
         note_launch();

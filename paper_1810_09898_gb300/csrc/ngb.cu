@@ -2324,12 +2324,12 @@ __device__ __forceinline__ void hsml_update(const UpdateArgs& a, int u, int r, f
     double hi = pass == 1 ? __longlong_as_double(0x7ff0000000000000ll) : a.hi[r];
     const HsmlStep st = hsml_next(h, m, s0f, s1f, a.nngb, a.tol, a.iterate != 0, pass, a.max_iter, lo, hi);
     if (st.finish) {
-        if (a.pass_k) {
-            a.pass_k[r] = pass;
+        if (a.res_k) {
+            a.res_k[r] = make_float4(s0f, s1f, __int_as_float(n), __int_as_float(pass));
         } else {
             hsml_write(a.perm[r], h, s0f, s1f, n, pass, a.h_out, a.rho, a.drhodh, a.fgrad, a.nngb_out, a.iters);
         }
-        if (a.vsum && !a.pass_k) {
+        if (a.vsum && !a.res_k) {
             // div v = -(1/rho) sum m v_ij . grad W, curl v = (1/rho) sum m v_ij x grad W
             const int orig = a.perm[r];
             const float hf = (float)h;

@@ -50,10 +50,10 @@ struct UpdateArgs {
     const float4* vsum;
     float* divv;
     float* curlv;
-    // optional: a finished particle only records its pass count here (rank space); its
-    // h, sums and count stay in h64 / s0 / s1 / n and the caller's outputs are written
-    // after the iteration by one gather over the active list (k_out_density)
-    int32_t* pass_k;
+    // optional: a finished particle only records {s0, s1, count, pass count} here (rank
+    // space, one float4; its h stays in h64) and the caller's outputs are written after
+    // the iteration by one gather over the active list (k_out_density)
+    float4* res_k;
 };
 
 // passes 2, 3, ... of the recycled iteration over the members' candidate lists

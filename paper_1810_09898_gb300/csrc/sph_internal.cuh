@@ -120,7 +120,6 @@ struct Ctx {
     float* acc_rho = nullptr;      // per-rank density sums of the current pass
     float* acc_drho = nullptr;
     int32_t* acc_n = nullptr;
-    int32_t* pass_k = nullptr;     // pass count of every finished particle (rank space)
     int64_t* cnt64 = nullptr;      // per-target pair counts (export)
     int2* groups = nullptr;        // group list of the current search (first, count)
     int2* groups_tmp = nullptr;

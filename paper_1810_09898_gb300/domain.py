@@ -16,6 +16,9 @@ exporting particles in a second search phase (Sec. 1.1).  Here each rank imports
    that and the particle's own h.  A rank's local set (its own particles and the
    imported ones) then holds every neighbour of its own particles, and its searches are
    purely local, with its own particles active.
+3. ``exchange_columns``: values computed after the halo was sent (rho and f of the
+   density loop, which hydro needs for its imported particles too) follow the same
+   plan, one all-to-all of the columns.
 
 The device steps (keys, owner masks, boxes, halo masks, compaction) are the library's
 kernels (``LibOps``); the exchanges and the row gathers around them are the only host
@@ -111,6 +114,7 @@ class Decomposition:
         self.level = level
         self.samples = samples
         self.splitters = None
+        self.plans = {}   # halo kind -> (send index lists, send counts, receive counts)
 
     # -- collectives
     def _all_gather_rows(self, t):
@@ -132,23 +136,52 @@ class Decomposition:
         dist.all_gather(outs, pad, group=self.group)
         return torch.cat([o[:k] for o, k in zip(outs, counts)]), counts
 
-    def _exchange(self, rows, mask):
-        """Every rank receives the rows whose mask has its bit, in rank order."""
+    def _exchange(self, rows, mask, plan_key=None):
+        """Every rank receives the rows whose mask has its bit, in rank order.  With
+        plan_key the send index lists and the counts are kept for exchange_columns."""
+        import torch
+
+        idx = [self.ops.compact(mask, r) for r in range(self.world)]
+        send_counts = [int(i.shape[0]) for i in idx]
+        recv_counts = self._counts(send_counts, rows.device)
+        if plan_key is not None:
+            self.plans[plan_key] = (idx, send_counts, recv_counts)
+        return self._send(rows, idx, send_counts, recv_counts)
+
+    def _counts(self, send_counts, device):
+        """Every rank's count for this rank, from every rank's counts (one all-to-all)."""
         import torch
         import torch.distributed as dist
 
-        parts = [rows[self.ops.compact(mask, r)] for r in range(self.world)]
+        if self.world == 1:
+            return list(send_counts)
+        sc = torch.tensor(send_counts, dtype=torch.int64, device=device)
+        rc = torch.empty_like(sc)
+        dist.all_to_all_single(rc, sc, group=self.group)
+        return [int(x) for x in rc.tolist()]
+
+    def _send(self, rows, idx, send_counts, recv_counts):
+        import torch
+        import torch.distributed as dist
+
+        parts = [rows[i] for i in idx]
         if self.world == 1:
             return parts[0]
         send = torch.cat(parts)
-        sc = torch.tensor([p.shape[0] for p in parts], dtype=torch.int64, device=rows.device)
-        rc = torch.empty_like(sc)
-        dist.all_to_all_single(rc, sc, group=self.group)
-        recv_counts = [int(x) for x in rc.tolist()]
-        recv = torch.empty((sum(recv_counts), rows.shape[1]), dtype=rows.dtype, device=rows.device)
-        dist.all_to_all_single(recv, send, output_split_sizes=recv_counts,
-                               input_split_sizes=[p.shape[0] for p in parts], group=self.group)
+        recv = torch.empty((sum(recv_counts),) + tuple(rows.shape[1:]), dtype=rows.dtype, device=rows.device)
+        dist.all_to_all_single(recv, send, output_split_sizes=recv_counts, input_split_sizes=send_counts,
+                               group=self.group)
         return recv
+
+    def exchange_columns(self, kind: int, values):
+        """Values of the own particles (rows in the order of `own` given to halo(kind))
+        sent along the same halo plan: the imported particles' values, in the order of
+        the rows halo(kind) returned.  Between density and hydro this carries rho and f
+        (and so P and c) of the hydro halo, whose rows were sent before they existed."""
+        if kind not in self.plans:
+            raise RuntimeError("exchange_columns needs a halo() of the same kind first")
+        idx, sc, rc = self.plans[kind]
+        return self._send(values, idx, sc, rc)
 
     # -- steps
     def partition(self, rows):
@@ -184,5 +217,5 @@ class Decomposition:
         box_rank = torch.cat([torch.full((k,), r, dtype=torch.int32, device=own.device)
                               for r, k in enumerate(counts)])
         mask = self.ops.halo_mask(pos, m, h, kind, widen, all_boxes.contiguous(), box_rank, self.rank, self.world)
-        return self._exchange(own, mask)
+        return self._exchange(own, mask, plan_key=kind)
 

@@ -11,7 +11,9 @@ kernels are compared with these CPU versions on the GPU in test_gpu_domain.py).
 Each rank then evaluates its own particles over its local set (own + imported) with the
 oracle, the local set sorted by global index so that the oracle's sums run in the same
 order as over the whole set: neighbour sets, density, hydro accelerations and the
-smoothing-length iteration must equal the single-domain results bit for bit.
+smoothing-length iteration must equal the single-domain results bit for bit.  Hydro
+takes rho and f of the imported particles from their own ranks' density, sent along the
+hydro halo's plan (``exchange_columns``), not from the single-domain run.
 """
 
 import os
@@ -118,10 +120,12 @@ def _rank(rank, world, port, out):
     D = Decomposition(world, rank, ops=CpuOps(oracle), level=LEVEL)
     own = D.partition(torch.from_numpy(rows[start == rank]))
     res = {"own": own[:, 9].numpy().astype(np.int64), "splitters": D.splitters.numpy()}
+    own_rf = None   # rho and f of the own particles, in the order of the rows of `own`
     for kind, widen in ((0, 1.0), (1, 1.0), (0, 2.0)):
         ghosts = D.halo(own, kind, widen)
-        local = torch.cat([own, ghosts]).numpy()
-        local = local[np.argsort(local[:, 9])]
+        cat = torch.cat([own, ghosts]).numpy()
+        srt = np.argsort(cat[:, 9])
+        local = cat[srt]
         gid = local[:, 9].astype(np.int64)
         tgt = np.flatnonzero(np.isin(gid, res["own"])).astype(np.int32)
         pos, h, m = local[:, :3], local[:, 3], local[:, 4]
@@ -131,10 +135,18 @@ def _rank(rank, world, port, out):
             off, idx = oracle.ngb_sets(pos, h, tgt, kind)
             res["sets_" + key] = (gid[tgt], off, gid[idx])
         if kind == 0 and widen == 1.0:
-            res["rho"] = oracle.density(pos, m, h, targets=tgt)["rho"]
+            dl = oracle.density(pos, m, h, targets=tgt)
+            res["rho"] = dl["rho"]
+            # tgt runs in global-index order: back to the order of the rows of `own`
+            own_rf = np.empty((len(own), 2))
+            own_rf[np.argsort(res["own"])] = np.column_stack([dl["rho"], dl["f"]])
         if kind == 1:
-            rho, f = dens["rho"][gid], dens["f"][gid]
-            res["acc"] = oracle.hydro(pos, local[:, 5:8], m, h, rho, f, local[:, 8], targets=tgt)["acc"]
+            # rho and f of the imported particles were computed on their own ranks after
+            # the hydro halo was sent: they follow its plan
+            imp = D.exchange_columns(1, torch.from_numpy(own_rf)).numpy()
+            assert imp.shape == (len(ghosts), 2)
+            rf = np.concatenate([own_rf, imp])[srt]
+            res["acc"] = oracle.hydro(pos, local[:, 5:8], m, h, rf[:, 0], rf[:, 1], local[:, 8], targets=tgt)["acc"]
         if kind == 0 and widen == 2.0:
             # the smoothing-length iteration of the own particles from scattered h
             h0 = h * np.exp(0.05 * np.random.default_rng(9).standard_normal(N))[gid]
@@ -171,8 +183,9 @@ def test_two_ranks_reproduce_the_single_domain():
             tg, lo, li = res[r][f"sets_{kind}_1.0"]
             for k, g in enumerate(tg):
                 assert np.array_equal(li[lo[k]:lo[k + 1]], idx[off[g]:off[g + 1]]), (kind, r, g)
-    full_rho = oracle.density(pos, m, h)["rho"]
-    full_acc = oracle.hydro(pos, rows[:, 5:8], m, h, dens["rho"], dens["f"], rows[:, 8])["acc"]
+    full_d = oracle.density(pos, m, h)
+    full_rho = full_d["rho"]
+    full_acc = oracle.hydro(pos, rows[:, 5:8], m, h, full_d["rho"], full_d["f"], rows[:, 8])["acc"]
     h0 = h * np.exp(0.05 * np.random.default_rng(9).standard_normal(N))
     hi_full, di_full = oracle.density_iterate(pos, m, h0)
     for r in (0, 1):
