@@ -76,12 +76,13 @@ typedef struct sphgrp_params {
     int group_centre; /* centre of a group's search sphere: SPHGRP_CENTRE_FIRST (the group's
                          first particle, Sec. 2.1) or SPHGRP_CENTRE_BOX (the centre of the
                          members' bounding box; same superset guarantee, smaller radius) */
-    double group_split; /* a group is cut in halves (recursively) while its search sphere
-                           (about the members' box centre, radius max over members of
-                           distance + h) exceeds group_split * members * (smallest h)^3 in
-                           volume, i.e. while its densest member would filter more than
-                           group_split * members times its own sphere; <= 0 keeps plain
-                           chunks of group_size.  e.g. 2 */
+    double group_split; /* a group is cut (recursively) while its search sphere,
+                           ((sqrt(3)/2) * largest extent of the members' box + smallest h)^3,
+                           exceeds group_split * members * (smallest h)^3 in volume, i.e.
+                           while a member would filter more than group_split * members times
+                           its own sphere; the cut is at the largest gap in key order between
+                           consecutive members (the middle when they are contiguous); <= 0
+                           keeps plain chunks of group_size.  e.g. 2 */
     int iteration;      /* smoothing-length iteration of the grouped density:
                            SPHGRP_ITER_PASSES (default: one search launch per pass over the
                            still unconverged particles, regrouped), SPHGRP_ITER_IN_GROUP (one
