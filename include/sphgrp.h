@@ -374,19 +374,22 @@ int sphgrp_batch_run(sphgrp_batch* b, const sphgrp_batch_io* io, int flags, cuda
 
 /* Autotuner: runs one step (updating io like sphgrp_batch_run), then for every class
  * present times a density + hydro pass over that class's boxes for every candidate
- * (group size 4..64, slice limit, split factor) and keeps the fastest.  Drops the
- * captured graph. */
+ * (group size 4..64, slice limit, split factor) and keeps the fastest; then, at that
+ * grouping, the octree leaf size of the class's boxes (the context's, 8, 12, 24, 32;
+ * each candidate rebuilds the forest before its timed pass).  Drops the captured
+ * graph. */
 int sphgrp_batch_tune(sphgrp_batch* b, const sphgrp_batch_io* io, cudaStream_t stream);
 
 /* Read / set the configuration of one class (group_size in [1, 128], max_slices in
- * {1, 2, 4}, group_split >= 0; 0 = no splitting).  Setting drops the captured graph.
- * pass_ms / pass_members (host, may be NULL) receive the autotuner's best time of one
- * density + hydro pass over the class's active particles and their count (0 when the
- * class was not tuned): the class's own throughput. */
+ * {1, 2, 4}, group_split >= 0; 0 = no splitting; leaf_size: octree leaf bucket of the
+ * class's boxes, 0 = the context's params.leaf_size, else in [8, 255]).  Setting drops
+ * the captured graph.  pass_ms / pass_members (host, may be NULL) receive the
+ * autotuner's best time of one density + hydro pass over the class's active particles
+ * and their count (0 when the class was not tuned): the class's own throughput. */
 int sphgrp_batch_get_config(sphgrp_batch* b, int cls, int* group_size, int* max_slices,
-                            double* group_split, double* pass_ms, int64_t* pass_members);
+                            double* group_split, int* leaf_size, double* pass_ms, int64_t* pass_members);
 int sphgrp_batch_set_config(sphgrp_batch* b, int cls, int group_size, int max_slices,
-                            double group_split);
+                            double group_split, int leaf_size);
 
 /* Counters of the last sphgrp_batch_run (no device work): walks and members summed
  * over its grouped launches (density, hydro, and the backward's three), candidates,

@@ -171,9 +171,9 @@ def load_library():
     L.sphgrp_batch_run.argtypes = [P, ctypes.POINTER(BatchIO), I32, P]
     L.sphgrp_batch_tune.argtypes = [P, ctypes.POINTER(BatchIO), P]
     L.sphgrp_batch_get_config.argtypes = [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32),
-                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                                          ctypes.POINTER(I64)]
-    L.sphgrp_batch_set_config.argtypes = [P, I32, I32, I32, ctypes.c_double]
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I32),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]
+    L.sphgrp_batch_set_config.argtypes = [P, I32, I32, I32, ctypes.c_double, I32]
     L.sphgrp_batch_stats.argtypes = [P, ctypes.POINTER(Stats)]
     for name in EXPORTED:
         if name not in ("sphgrp_default_params", "sphgrp_last_error"):
@@ -474,16 +474,17 @@ class Batch:
         _check(self._L.sphgrp_batch_tune(self._h, ctypes.byref(io), _stream()))
 
     def get_config(self, cls: int) -> dict:
-        g, sm = ctypes.c_int(), ctypes.c_int()
+        g, sm, lf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         sp, ms = ctypes.c_double(), ctypes.c_double()
         nm = ctypes.c_int64()
         _check(self._L.sphgrp_batch_get_config(self._h, cls, ctypes.byref(g), ctypes.byref(sm), ctypes.byref(sp),
-                                               ctypes.byref(ms), ctypes.byref(nm)))
-        return {"group_size": g.value, "max_slices": sm.value, "group_split": sp.value,
+                                               ctypes.byref(lf), ctypes.byref(ms), ctypes.byref(nm)))
+        return {"group_size": g.value, "max_slices": sm.value, "group_split": sp.value, "leaf_size": lf.value,
                 "tuned_pass_ms": ms.value, "tuned_members": nm.value}
 
-    def set_config(self, cls: int, group_size: int, max_slices: int, group_split: float):
-        _check(self._L.sphgrp_batch_set_config(self._h, cls, group_size, max_slices, float(group_split)))
+    def set_config(self, cls: int, group_size: int, max_slices: int, group_split: float, leaf_size: int = 0):
+        _check(self._L.sphgrp_batch_set_config(self._h, cls, group_size, max_slices, float(group_split),
+                                               int(leaf_size)))
 
     def stats(self) -> dict:
         st = Stats()

@@ -26,6 +26,8 @@ namespace {
 constexpr int kGrid = 1024;   // blocks of the grid-stride kernels
 constexpr int kLevels = kKeyLevels + 3;
 constexpr int kMaxTableBoxes = 256;   // boxes that get a walk start table
+constexpr int kMinBatchLeaf = 8;      // smallest per-class leaf size: the forest's node
+                                      // capacity (n/2 + 64 per box) holds trees of leaves >= 8
 
 // device scalars of a batch call
 enum Scalar {
@@ -45,6 +47,7 @@ struct ClassCfg {
     float split = 2.0f;
     float tuned_ms = 0.0f;        // the tuner's best density + hydro pass over the class
     int64_t tuned_members = 0;    // active particles of that pass
+    int leaf = 0;                 // octree leaf size of the class's boxes (0: the context's)
 };
 
 struct Batch {
@@ -57,7 +60,7 @@ struct Batch {
     int max_g = 16;
     // device
     int64_t* box_off = nullptr;     // nbox + 1
-    int32_t* box_g = nullptr;       // nbox: g | smax << 8
+    int32_t* box_g = nullptr;       // nbox: g | smax << 8 | leaf size << 16
     float* box_split = nullptr;     // nbox
     int32_t* box_cls = nullptr;     // nbox
     int32_t* box_of_rank = nullptr; // n
@@ -250,7 +253,7 @@ int upload_box_cfg(Batch* b, cudaStream_t s) {
     b->max_g = 1;
     for (int k = 0; k < b->nbox; ++k) {
         const ClassCfg& cc = b->cfg[b->cls_h[k]];
-        g[k] = cc.g | (cc.smax << 8);
+        g[k] = cc.g | (cc.smax << 8) | (cc.leaf << 16);
         sp[k] = cc.split;
         b->max_g = std::max(b->max_g, cc.g);
     }
@@ -326,7 +329,7 @@ int issue_step(Batch* b, const sphgrp_batch_io* io, int flags, cudaStream_t s) {
     if ((rc = gather_particles(c, io->pos, io->m, s))) return rc;
     if ((rc = launch_gather_h(c, io->h, s))) return rc;
     if ((rc = build_forest(c, b->nbox, b->box_off, b->lvl, b->blo, b->bhi, b->dsc + kTot, b->box_of_rank,
-                           b->start_tabs, s)))
+                           b->start_tabs, s, b->box_g)))
         return rc;
     // density with the smoothing-length iteration over the active groups
     if ((rc = make_batch_groups(b, false, -1, io->active, s))) return rc;
@@ -599,7 +602,7 @@ int sphgrp_batch_run(sphgrp_batch* w, const sphgrp_batch_io* io, int flags, cuda
 }
 
 int sphgrp_batch_get_config(sphgrp_batch* w, int cls, int* group_size, int* max_slices, double* group_split,
-                            double* pass_ms, int64_t* pass_members) {
+                            int* leaf_size, double* pass_ms, int64_t* pass_members) {
     if (!w || cls < 0 || cls >= SPHGRP_BATCH_CLASSES) return set_error(SPHGRP_EINVAL, "bad batch or class");
     const ClassCfg& cc = w->b.cfg[cls];
     if (pass_ms) *pass_ms = cc.tuned_ms;
@@ -607,16 +610,20 @@ int sphgrp_batch_get_config(sphgrp_batch* w, int cls, int* group_size, int* max_
     if (group_size) *group_size = cc.g;
     if (max_slices) *max_slices = cc.smax;
     if (group_split) *group_split = cc.split;
+    if (leaf_size) *leaf_size = cc.leaf;
     return SPHGRP_OK;
 }
 
-int sphgrp_batch_set_config(sphgrp_batch* w, int cls, int group_size, int max_slices, double group_split) {
+int sphgrp_batch_set_config(sphgrp_batch* w, int cls, int group_size, int max_slices, double group_split,
+                            int leaf_size) {
     if (!w || cls < 0 || cls >= SPHGRP_BATCH_CLASSES) return set_error(SPHGRP_EINVAL, "bad batch or class");
     if (group_size < 1 || group_size > 128) return set_error(SPHGRP_EINVAL, "group_size outside [1, 128]");
     if (max_slices != 1 && max_slices != 2 && max_slices != 4) return set_error(SPHGRP_EINVAL, "max_slices not 1, 2, 4");
     if (!(group_split >= 0.0)) return set_error(SPHGRP_EINVAL, "group_split < 0");
+    if (leaf_size != 0 && (leaf_size < kMinBatchLeaf || leaf_size > 255))
+        return set_error(SPHGRP_EINVAL, "leaf_size not 0 or in [8, 255]");
     Batch* b = &w->b;
-    b->cfg[cls] = ClassCfg{group_size, max_slices, (float)group_split, 0.0f, 0};
+    b->cfg[cls] = ClassCfg{group_size, max_slices, (float)group_split, 0.0f, 0, leaf_size};
     drop_graph(b);
     return upload_box_cfg(b, b->cap_stream);
 }
@@ -647,38 +654,84 @@ int sphgrp_batch_tune(sphgrp_batch* w, const sphgrp_batch_io* io, cudaStream_t s
     cudaEventCreate(&e1);
     float* acc_scratch = reinterpret_cast<float*>(c->adj0);   // n x 4 floats
     float* dudt_scratch = reinterpret_cast<float*>(c->adj3);
+    // best of two density + hydro passes over the class's active particles
+    auto time_class = [&](int cls, float* out) -> int {
+        float t_best = 3.0e38f;
+        int r = SPHGRP_OK;
+        for (int rep = 0; rep < 2 && !r; ++rep) {
+            cudaEventRecord(e0, s);
+            if ((r = make_batch_groups(b, false, cls, io->active, s))) break;
+            SearchArgs ad = batch_args(b, false);
+            ad.o_s0 = c->acc_rho;
+            ad.o_s1 = c->acc_drho;
+            ad.o_n = c->acc_n;
+            if ((r = launch_search_dev(ad, kKindDensity, b->max_g, c->sm_count, s))) break;
+            SearchArgs ah = batch_args(b, false);
+            ah.o_acc = acc_scratch;
+            ah.o_dudt = dudt_scratch;
+            if ((r = launch_search_dev(ah, kKindHydro, b->max_g, c->sm_count, s))) break;
+            cudaEventRecord(e1, s);
+            if ((r = check_cuda(cudaEventSynchronize(e1), "tuning step"))) break;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t_best = std::min(t_best, ms);
+        }
+        *out = t_best;
+        return r;
+    };
+    // the forest again (the order is unchanged) with the classes' current leaf sizes,
+    // and its node hmax at the converged h; reports whether it fit the node capacity
+    auto rebuild = [&](bool* fits) -> int {
+        int r = build_forest(c, b->nbox, b->box_off, b->lvl, b->blo, b->bhi, b->dsc + kTot, b->box_of_rank,
+                             b->start_tabs, s, b->box_g);
+        if (!r) r = refresh_hmax_forest(c, b->lvl, s);
+        unsigned err = 0;
+        if (!r) r = check_cuda(cudaMemcpyAsync(b->host, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                               "forest status");
+        if (!r) r = check_cuda(cudaStreamSynchronize(s), "forest status");
+        if (!r) std::memcpy(&err, b->host, sizeof(unsigned));
+        *fits = (err & kErrNodes) == 0u;
+        if (!r && !*fits) cudaMemsetAsync(c->err, 0, sizeof(unsigned), s);
+        return r;
+    };
     for (int cls = 0; cls < SPHGRP_BATCH_CLASSES && !rc; ++cls) {
         if (std::find(b->cls_h.begin(), b->cls_h.end(), cls) == b->cls_h.end()) continue;
         const ClassCfg keep = b->cfg[cls];
         float best = 3.0e38f;
         ClassCfg best_cfg = keep;
         for (const Cand& cd : cands) {
-            b->cfg[cls] = ClassCfg{cd.g, cd.smax, cd.split, 0.0f, 0};
+            b->cfg[cls] = ClassCfg{cd.g, cd.smax, cd.split, 0.0f, 0, keep.leaf};
             if ((rc = upload_box_cfg(b, s))) break;
-            float t_best = 3.0e38f;
-            for (int rep = 0; rep < 2 && !rc; ++rep) {
-                cudaEventRecord(e0, s);
-                if ((rc = make_batch_groups(b, false, cls, io->active, s))) break;
-                SearchArgs ad = batch_args(b, false);
-                ad.o_s0 = c->acc_rho;
-                ad.o_s1 = c->acc_drho;
-                ad.o_n = c->acc_n;
-                if ((rc = launch_search_dev(ad, kKindDensity, b->max_g, c->sm_count, s))) break;
-                SearchArgs ah = batch_args(b, false);
-                ah.o_acc = acc_scratch;
-                ah.o_dudt = dudt_scratch;
-                if ((rc = launch_search_dev(ah, kKindHydro, b->max_g, c->sm_count, s))) break;
-                cudaEventRecord(e1, s);
-                if ((rc = check_cuda(cudaEventSynchronize(e1), "tuning step"))) break;
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                t_best = std::min(t_best, ms);
-            }
-            if (rc) break;
-            if (t_best < best) {
-                best = t_best;
+            float t = 0.0f;
+            if ((rc = time_class(cls, &t))) break;
+            if (t < best) {
+                best = t;
                 best_cfg = b->cfg[cls];
             }
+        }
+        // then the octree leaf size of the class's boxes, at its best grouping: each
+        // candidate rebuilds the forest before its timed passes; one that overflows the
+        // node capacity is skipped
+        for (int leaf : {0, 8, 12, 24, 32}) {
+            if (rc || leaf == keep.leaf) continue;
+            ClassCfg cd = best_cfg;
+            cd.leaf = leaf;
+            b->cfg[cls] = cd;
+            bool fits = true;
+            if ((rc = upload_box_cfg(b, s)) || (rc = rebuild(&fits))) break;
+            if (!fits) continue;
+            float t = 0.0f;
+            if ((rc = time_class(cls, &t))) break;
+            if (t < best) {
+                best = t;
+                best_cfg = cd;
+            }
+        }
+        if (!rc) {
+            // the class's chosen forest for the passes that follow
+            bool fits = true;
+            b->cfg[cls] = best_cfg;
+            if (!(rc = upload_box_cfg(b, s))) rc = rebuild(&fits);
         }
         b->cfg[cls] = rc ? keep : best_cfg;
         if (!rc) {

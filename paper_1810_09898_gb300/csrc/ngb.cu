@@ -1253,7 +1253,7 @@ __device__ __forceinline__ GroupDesc group_desc(const SearchArgs& a, int gid) {
         d.cnt = G.y;
         d.root = G.z;
         d.g = G.w & 0xff;
-        d.smax = G.w >> 8;
+        d.smax = (G.w >> 8) & 0xff;   // bits 16.. carry the box's leaf size
     } else if (a.groups) {
         const int2 G = a.groups[gid];
         d.base = G.x;

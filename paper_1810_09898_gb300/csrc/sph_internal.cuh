@@ -264,7 +264,8 @@ int sort_keys_boxed(Ctx* c, int64_t n, const double* pos, const int64_t* box_off
                     cudaStream_t s);                                                        // sort.cu
 int alloc_forest(Ctx* c, int64_t cap);                                                     // tree.cu
 int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uint4* blo, uint4* bhi,
-                 int32_t* tot, const int32_t* box_of_rank, int32_t* start_tabs, cudaStream_t s); // tree.cu
+                 int32_t* tot, const int32_t* box_of_rank, int32_t* start_tabs, cudaStream_t s,
+                 const int32_t* box_cfg = nullptr);                                         // tree.cu
 int refresh_hmax_forest(Ctx* c, const int32_t* lvl, cudaStream_t s);                       // tree.cu
 void note_launches(long long k);                                                           // api.cu
 

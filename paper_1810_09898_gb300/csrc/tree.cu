@@ -410,14 +410,22 @@ __global__ void k_forest_roots(int nbox, const int64_t* __restrict__ box_off, in
     if (k <= kKeyLevels + 2) lvl[k] = (k == 0) ? 0 : nbox;
 }
 
+// box_cfg (optional): per box, bits 16..23 = that box's leaf size (0: leaf_size); the
+// node's box is the box of its first particle
 __global__ void k_split_count_dev(const uint64_t* __restrict__ keys, const int4* __restrict__ nlink,
                                   const int32_t* __restrict__ lvl, int level, int leaf_size,
-                                  int32_t* __restrict__ nchild) {
+                                  int32_t* __restrict__ nchild, const int32_t* __restrict__ box_cfg,
+                                  const int32_t* __restrict__ box_of_rank) {
     const int a = lvl[level], nf = lvl[level + 1] - a;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
         int4 L = nlink[a + k];
         int cnt = 0;
-        if (L.y > leaf_size && level < kKeyLevels) {
+        int leaf = leaf_size;
+        if (box_cfg && L.y > 0) {
+            const int lb = (box_cfg[box_of_rank[L.x]] >> 16) & 0xff;
+            if (lb > 0) leaf = lb;
+        }
+        if (L.y > leaf && level < kKeyLevels) {
             int b[9];
             octant_bounds(keys, L.x, L.x + L.y, 3 * (kKeyLevels - 1 - level), b);
 #pragma unroll
@@ -578,7 +586,7 @@ int alloc_forest(Ctx* c, int64_t cap) {
 // lvl: device, kKeyLevels + 3 entries; blo/bhi: device scratch of t.cap entries;
 // tot: one device int.  Uses c->flag and c->scan as per-level scratch.
 int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uint4* blo, uint4* bhi, int32_t* tot,
-                 const int32_t* box_of_rank, int32_t* start_tabs, cudaStream_t s) {
+                 const int32_t* box_of_rank, int32_t* start_tabs, cudaStream_t s, const int32_t* box_cfg) {
     Tree& t = c->tree;
     c->start_valid = false;   // the single-box table does not describe a forest
     const int64_t n = c->n;
@@ -587,7 +595,8 @@ int build_forest(Ctx* c, int nbox, const int64_t* box_off_dev, int32_t* lvl, uin
     note_launch();
     int rc = SPHGRP_OK;
     for (int level = 0; level < kKeyLevels; ++level) {
-        k_split_count_dev<<<kForestGrid, 256, 0, s>>>(c->keys, t.nlink, lvl, level, c->p.leaf_size, c->flag);
+        k_split_count_dev<<<kForestGrid, 256, 0, s>>>(c->keys, t.nlink, lvl, level, c->p.leaf_size, c->flag,
+                                                      box_cfg, box_of_rank);
         note_launch();
         if ((rc = exclusive_scan_i32_dev(c, c->flag, c->scan, lvl + level + 1, lvl + level, n, tot, s))) return rc;
         k_split_write_dev<<<kForestGrid, 256, 0, s>>>(c->keys, t.nlink, t.next, t.nlevel, lvl, level, c->flag,

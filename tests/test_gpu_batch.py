@@ -238,6 +238,7 @@ def test_batch_tune_and_config(cuda_device):
         assert cfg["group_size"] in (4, 8, 16, 32, 64)
         assert cfg["max_slices"] in (1, 2, 4)
         assert cfg["group_split"] in (1.5, 2.0, 4.0)
+        assert cfg["leaf_size"] in (0, 8, 12, 24, 32)
     # a tuned run is still a correct run, by the oracle
     io.reset()
     B.run(io.a, graph=True)
@@ -247,12 +248,22 @@ def test_batch_tune_and_config(cuda_device):
         assert cfg["tuned_pass_ms"] > 0.0 and cfg["tuned_members"] == int(
             sum(b["active"][b["box_off"][k]:b["box_off"][k + 1]].sum() for k in range(5) if b["box_class"][k] == cls))
     B.set_config(1, 8, 2, 2.0)
-    assert B.get_config(1) == {"group_size": 8, "max_slices": 2, "group_split": 2.0, "tuned_pass_ms": 0.0,
-                               "tuned_members": 0}
+    assert B.get_config(1) == {"group_size": 8, "max_slices": 2, "group_split": 2.0, "leaf_size": 0,
+                               "tuned_pass_ms": 0.0, "tuned_members": 0}
+    # per-class leaf sizes: the forest of each class's boxes splits at its own bucket size,
+    # and the run still agrees with the oracle box by box
+    B.set_config(0, 16, 2, 2.0, leaf_size=8)
+    B.set_config(1, 8, 4, 2.0, leaf_size=32)
+    assert B.get_config(0)["leaf_size"] == 8 and B.get_config(1)["leaf_size"] == 32
+    io.reset()
+    B.run(io.a)
+    _check_density_per_box(b, io.host())
     with pytest.raises(sg.SphgrpError, match="EINVAL"):
         B.set_config(1, 0, 2, 2.0)
     with pytest.raises(sg.SphgrpError, match="EINVAL"):
         B.set_config(1, 16, 3, 2.0)
+    with pytest.raises(sg.SphgrpError, match="EINVAL"):
+        B.set_config(1, 16, 2, 2.0, leaf_size=4)
     B.close()
 
 
