@@ -556,9 +556,10 @@ def active_leg(P, frac: float, g: int, steps: int, warmup: int, dist, rank: int)
     out = {"fraction": frac, "n_active": P.n_act}
     try:
         # the group size is the method's tuning knob (Sec. 3.2 finds its optimum numerically):
-        # one untimed step at each candidate size picks the one this active set runs fastest at
+        # one timed step at each candidate size (after two untimed ones) picks the size this
+        # active set runs fastest at
         trial = {}
-        for gs in sorted({8, g}):
+        for gs in sorted({8, 16, 32, g}):
             for _ in range(2):
                 P.step(sg.GROUPED, gs)
             trial[gs], _, _ = timed(P, lambda cl, gs=gs: P.step(sg.GROUPED, gs, cl), 1, 0, dist)
