@@ -621,7 +621,8 @@ int sphgrp_ctx_destroy(sphgrp_ctx* ctx) {
                     c->cnt64, c->groups, c->groups_tmp, c->grp_cnt, c->grp_off,
                     c->acc_s2, c->wadj, c->dadj, c->adj0, c->adj1, c->adj2, c->adj3,
                     c->stack_spill, c->start_tab, c->ctr, c->err, c->work, c->ctr_log, c->tree.ncen, c->tree.next, c->tree.nlink,
-                    c->tree.nlevel, c->lst, c->lrec, c->lhw, c->lslot, c->npass};
+                    c->tree.nlevel, c->tree.box_lo, c->tree.box_hi, c->tree.top_cells, c->lst, c->lrec, c->lhw,
+                    c->lslot, c->npass};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->host_small) cudaFreeHost(c->host_small);

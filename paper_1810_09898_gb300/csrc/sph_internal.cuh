@@ -22,7 +22,7 @@ namespace sphgrp {
 //   poff      float4   {x 2^32 - X, ..., m}: sub-unit offsets in [0,1) and the mass
 //   h64       double   smoothing length (FP64 master)
 //   hyd0      float4   {vx, vy, vz, c}                        (hydro candidates)
-//   hyd1      float4   {A = f P / rho^2, rho, 1/h, 8/(pi h^4)} (hydro candidates)
+//   hyd1      float4   {A = f P / rho^2, rho, 1/h, Balsara limiter or 1} (hydro candidates)
 //
 // A coordinate relative to a fixed-point centre C is
 //   float(int32(X - C)) + off, scaled by 2^-32:
@@ -65,6 +65,12 @@ struct Tree {
     int64_t count = 0;             // nodes in the current tree
     int level_begin[kKeyLevels + 3] = {0};  // node ranges per level (host copy)
     int nlevels = 0;
+    // build scratch kept between builds (no allocation per call): fixed-point node
+    // boxes of the bottom-up pass (box_cap nodes) and the top levels' cell table
+    uint4* box_lo = nullptr;
+    uint4* box_hi = nullptr;
+    int64_t box_cap = 0;
+    int32_t* top_cells = nullptr;
 };
 
 struct DevCounters {
@@ -116,7 +122,8 @@ struct Ctx {
     int64_t scan_aux_cap = 0;
     double* lo = nullptr;          // bracket of the iteration
     double* hi = nullptr;
-    float4* res4 = nullptr;        // per-rank results of the hydro / velocity loops (key order)
+    float4* res4 = nullptr;        // per-rank results (key order): hydro {a, du/dt}, velocity
+                                   // {div, curl}, density {S0, S1, count, passes} of finished particles
     float* acc_rho = nullptr;      // per-rank density sums of the current pass
     float* acc_drho = nullptr;
     int32_t* acc_n = nullptr;

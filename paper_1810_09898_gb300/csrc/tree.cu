@@ -305,9 +305,11 @@ int build_tree(Ctx* c, cudaStream_t s) {
     t.count = 1;
     int level = 0;
     int32_t* total_dev = reinterpret_cast<int32_t*>(c->work) + 12;
-    int32_t* top = nullptr;
-    if (cudaMallocAsync(&top, kTopTableSize * sizeof(int32_t), s) != cudaSuccess)
+    if (!t.top_cells && cudaMalloc(&t.top_cells, kTopTableSize * sizeof(int32_t)) != cudaSuccess) {
+        t.top_cells = nullptr;
         return set_error(SPHGRP_ENOMEM, "octree top-cell table");
+    }
+    int32_t* top = t.top_cells;
     cudaMemsetAsync(top, 0xff, kTopTableSize * sizeof(int32_t), s);
     if (n > 0) {
         k_top_cells<<<blocks_for(n, 256), 256, 0, s>>>(c->keys, n, top);
@@ -321,21 +323,12 @@ int build_tree(Ctx* c, cudaStream_t s) {
                                                           c->p.leaf_size, c->flag, top);
         note_launch();
         rc = exclusive_scan_i32(c, c->flag, c->scan, nf, total_dev, s);
-        if (rc) {
-            cudaFreeAsync(top, s);
-            return rc;
-        }
+        if (rc) return rc;
         cudaMemcpyAsync(c->host_small, total_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-        if ((rc = check_cuda(cudaStreamSynchronize(s), "octree level"))) {
-            cudaFreeAsync(top, s);
-            return rc;
-        }
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "octree level"))) return rc;
         int total = c->host_small[0];
         if (b + (int64_t)total > t.cap) {
-            if ((rc = grow_tree(c, b + (int64_t)total, s))) {
-                cudaFreeAsync(top, s);
-                return rc;
-            }
+            if ((rc = grow_tree(c, b + (int64_t)total, s))) return rc;
         }
         k_split_write<<<blocks_for(nf, 256), 256, 0, s>>>(c->keys, t.nlink, t.next, t.nlevel, a, nf,
                                                           level, c->flag, c->scan, b, top);
@@ -345,13 +338,22 @@ int build_tree(Ctx* c, cudaStream_t s) {
         if (total == 0) { ++level; break; }
     }
     t.nlevels = level;
-    cudaFreeAsync(top, s);
-    // boxes bottom-up (scratch for lo/hi boxes: the radix-sort key buffers, >= 16 B/node?)
-    uint4* blo;
-    uint4* bhi;
-    if (cudaMallocAsync(&blo, t.count * sizeof(uint4), s) != cudaSuccess ||
-        cudaMallocAsync(&bhi, t.count * sizeof(uint4), s) != cudaSuccess)
-        return set_error(SPHGRP_ENOMEM, "octree box scratch");
+    // boxes bottom-up, in scratch kept by the tree (grown to the node count when needed)
+    if (t.box_cap < t.count) {
+        if (t.box_lo) cudaFree(t.box_lo);
+        if (t.box_hi) cudaFree(t.box_hi);
+        t.box_lo = t.box_hi = nullptr;
+        t.box_cap = 0;
+        const int64_t cap = t.count + t.count / 4 + 1024;
+        if (cudaMalloc(&t.box_lo, cap * sizeof(uint4)) != cudaSuccess ||
+            cudaMalloc(&t.box_hi, cap * sizeof(uint4)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(SPHGRP_ENOMEM, "octree box scratch");
+        }
+        t.box_cap = cap;
+    }
+    uint4* blo = t.box_lo;
+    uint4* bhi = t.box_hi;
     for (int lv = t.nlevels - 1; lv >= 0; --lv) {
         int a = t.level_begin[lv], nf = t.level_begin[lv + 1] - a;
         if (nf > 0) {
@@ -372,8 +374,6 @@ int build_tree(Ctx* c, cudaStream_t s) {
         }
         c->start_valid = true;
     }
-    cudaFreeAsync(blo, s);
-    cudaFreeAsync(bhi, s);
     return check_cuda(cudaGetLastError(), "octree build");
 }
 
