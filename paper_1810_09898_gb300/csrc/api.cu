@@ -220,16 +220,22 @@ __global__ void k_out_vel(int64_t n_act, const int32_t* __restrict__ active, int
     curlv[3 * i + 2] = v.w;
 }
 
-__global__ void k_counts_by_caller(int64_t n_act, const int32_t* __restrict__ active,
+// (active indices outside [0, n) were flagged by k_mark_active; the call reports EINVAL
+// and these kernels skip them: a count of 0, no write)
+__global__ void k_counts_by_caller(int64_t n_act, const int32_t* __restrict__ active, int64_t n,
                                    const int64_t* __restrict__ cnt, int64_t* __restrict__ out) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < n_act) out[k] = cnt[active[k]];
+    if (k >= n_act) return;
+    const int64_t i = active[k];
+    out[k] = (i >= 0 && i < n) ? cnt[i] : 0;
 }
 
-__global__ void k_offsets_by_orig(int64_t n_act, const int32_t* __restrict__ active,
+__global__ void k_offsets_by_orig(int64_t n_act, const int32_t* __restrict__ active, int64_t n,
                                   const int64_t* __restrict__ off, int64_t* __restrict__ out) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k < n_act) out[active[k]] = off[k];
+    if (k >= n_act) return;
+    const int64_t i = active[k];
+    if (i >= 0 && i < n) out[i] = off[k];
 }
 
 __global__ void k_group_first(int ng, int nu, int g, const int2* __restrict__ groups, int32_t* __restrict__ out) {
@@ -698,7 +704,7 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
     rc = launch_search(a, kind, kCount, grouped, c->sm_count, s);
     timer_end(c, s, a.nu);
     if (rc) return rc;
-    k_counts_by_caller<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->cnt64, offsets);
+    k_counts_by_caller<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->n, c->cnt64, offsets);
     note_launch();
     if ((rc = exclusive_scan_i64(c, offsets, offsets, n_act, offsets + n_act, s))) return rc;
     if (n_act == 0) cudaMemsetAsync(offsets, 0, sizeof(int64_t), s);
@@ -708,7 +714,7 @@ int sphgrp_ngb_search(sphgrp_ctx* ctx, int64_t n_act, const int32_t* active, con
     std::memcpy(&total, c->host_small + 32, sizeof(int64_t));
     *n_pairs = total;
     if (idx) {
-        k_offsets_by_orig<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, offsets, c->cnt64);
+        k_offsets_by_orig<<<blocks_for(n_act, 256), 256, 0, s>>>(n_act, active, c->n, offsets, c->cnt64);
         note_launch();
         a.x_idx = idx;
         timer_begin(c, s);

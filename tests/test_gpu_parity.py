@@ -283,6 +283,50 @@ def test_rejects_bad_input(cuda_device):
         ctx.density(act, torch.tensor([0.1], dtype=torch.float64, device="cuda"), 0, 1, 999, z, z, z, zi)
 
 
+def test_out_of_range_active_indices(cuda_device):
+    """Active indices outside [0, n) are reported as EINVAL by every call that takes an
+    active list; the kernels that read the list skip them (no access outside the
+    arrays), and the context stays usable: the next call with a valid list gives the
+    oracle's answer."""
+    import paper_1810_09898_gb300 as sg
+    import torch
+
+    n = 2000
+    d = dataset("uniform", n, 1)
+    pos_t = torch.as_tensor(d["pos"], device="cuda")
+    m_t = torch.as_tensor(d["m32"], device="cuda")
+    ctx = sg.Context(n)
+    ctx.sfc_keys_sort(pos_t)
+    ctx.tree_build(pos_t, m_t)
+    h = torch.full((n,), 2.0 * d["h0"], dtype=torch.float64, device="cuda")
+    f32 = dict(dtype=torch.float32, device="cuda")
+    rho, drho, f = (torch.ones(n, **f32) for _ in range(3))
+    nn = torch.zeros(n, dtype=torch.int32, device="cuda")
+    vel = torch.zeros((n, 3), **f32)
+    u = torch.ones(n, **f32)
+    acc, dudt = torch.zeros((n, 3), **f32), torch.zeros(n, **f32)
+    divv, curl = torch.zeros(n, **f32), torch.zeros((n, 3), **f32)
+    bad = torch.tensor([0, 7, n, -1, 1999], dtype=torch.int32, device="cuda")
+    calls = [
+        lambda: ctx.density(bad, h.clone(), 0, sg.GROUPED, 16, rho, drho, f, nn),
+        lambda: ctx.density(bad, h.clone(), 1, sg.INDIVIDUAL, 1, rho, drho, f, nn),
+        lambda: ctx.hydro_force(bad, h, rho, f, vel, u, sg.GROUPED, 16, acc, dudt),
+        lambda: ctx.velocity_derivs(bad, h, rho, vel, 16, divv, curl),
+        lambda: ctx.ngb_search(bad, h, 0, sg.GROUPED, 16,
+                               torch.zeros(len(bad) + 1, dtype=torch.int64, device="cuda")),
+    ]
+    for call in calls:
+        with pytest.raises(sg.SphgrpError, match="EINVAL"):
+            call()
+    # a valid call afterwards: counts and density as the oracle's at the same h
+    act = np.arange(n, dtype=np.int32)
+    ctx.density(torch.as_tensor(act, device="cuda"), h, 0, sg.GROUPED, 16, rho, drho, f, nn)
+    ref = oracle.density(d["pos"], d["m32"].astype(np.float64), h.cpu().numpy())
+    assert np.array_equal(nn.cpu().numpy(), ref["nngb"])
+    assert np.max(np.abs(rho.cpu().numpy() / ref["rho"] - 1.0)) <= RHO_TOL
+    ctx.close()
+
+
 # ---------------------------------------------------------------- radius grouping (Sec. 2.1)
 
 @pytest.fixture(scope="module", params=[(0.5, 1), (1.0, 0)], ids=["f0.5-box", "f1.0-first"])
