@@ -440,7 +440,9 @@ int sphgrp_domain_boxes(sphgrp_ctx* ctx, const double* h, int level, int cap, do
  * neighbour of i iff |x_j - x_i| < h_i) or below max(widen * hmax, h_j) (hydro: iff
  * below max(h_i, h_j)).  widen in [1, 4] covers the growth of h in a later
  * smoothing-length iteration.  counts (device, world int64) = particles per rank.
- * world <= 64.  Errors: EINVAL, ESTATE without a tree. */
+ * world <= 64.  The call synchronises the stream to read back the check of box_rank:
+ * a rank outside [0, world) is skipped and reported as EINVAL (the mask then leaves
+ * that box out).  Errors: EINVAL, ESTATE without a tree. */
 int sphgrp_halo_select(sphgrp_ctx* ctx, const double* h, int kind, double widen, int nbox,
                        const double* boxes, const int32_t* box_rank, int self_rank, int world,
                        uint64_t* mask, int64_t* counts, cudaStream_t stream);

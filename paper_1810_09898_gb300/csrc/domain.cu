@@ -115,8 +115,9 @@ __global__ void k_halo_select(int64_t n, const int32_t* __restrict__ perm, const
                               const double* __restrict__ yd, const double* __restrict__ zd,
                               const double* __restrict__ h, int kind, double widen, int nbox,
                               const double* __restrict__ boxes,
-                              const int32_t* __restrict__ box_rank, int self_rank, uint64_t* __restrict__ mask,
-                              unsigned long long* __restrict__ counts) {
+                              const int32_t* __restrict__ box_rank, int self_rank, int world,
+                              uint64_t* __restrict__ mask, unsigned long long* __restrict__ counts,
+                              unsigned* err) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= n) return;
     const int64_t i = perm[r];
@@ -124,6 +125,10 @@ __global__ void k_halo_select(int64_t n, const int32_t* __restrict__ perm, const
     uint64_t m = 0;
     for (int b = 0; b < nbox; ++b) {
         const int rk = box_rank[b];
+        if (rk < 0 || rk >= world) {   // the caller's rank array: skipped, reported
+            if (r == 0) atomicOr(err, kErrRank);
+            continue;
+        }
         if (rk == self_rank || ((m >> rk) & 1u)) continue;
         const double* B = boxes + 8 * (int64_t)b;
         const double reach = kind == SPHGRP_HYDRO ? fmax(widen * B[6], hj) : widen * B[6];
@@ -212,11 +217,18 @@ int sphgrp_halo_select(sphgrp_ctx* ctx, const double* h, int kind, double widen,
         (nbox > 0 && (!boxes || !box_rank)))
         return set_error(SPHGRP_EINVAL, "world outside [1, 64], bad rank or null array");
     cudaMemsetAsync(counts, 0, world * sizeof(int64_t), s);
+    cudaMemsetAsync(c->err, 0, sizeof(unsigned), s);
     k_halo_select<<<blocks_for(c->n, 128), 128, 0, s>>>(c->n, c->perm, c->xd, c->yd, c->zd, h, kind, widen, nbox, boxes,
-                                                        box_rank, self_rank, mask,
-                                                        reinterpret_cast<unsigned long long*>(counts));
+                                                        box_rank, self_rank, world, mask,
+                                                        reinterpret_cast<unsigned long long*>(counts), c->err);
     note_launch();
-    return check_cuda(cudaGetLastError(), "halo select");
+    // the box ranks are device data: their check is read back (one stream synchronisation)
+    int rc = check_cuda(cudaMemcpyAsync(c->host_small, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s),
+                        "halo select status");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(s), "halo select");
+    if (rc) return rc;
+    if ((unsigned)c->host_small[0] & kErrRank) return set_error(SPHGRP_EINVAL, "a box rank is outside [0, world)");
+    return SPHGRP_OK;
 }
 
 int sphgrp_mask_compact(sphgrp_ctx* ctx, int64_t n, const uint64_t* mask, int bit, int32_t* idx, int64_t* count,

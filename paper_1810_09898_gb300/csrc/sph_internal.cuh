@@ -84,6 +84,7 @@ enum ErrBits : unsigned {
     kErrCap = 8u,        // export capacity exceeded
     kErrH = 16u,         // smoothing length outside (0, 0.5)
     kErrTimeout = 64u,   // a bounded device-side wait gave up
+    kErrRank = 128u,     // a domain box's rank outside [0, world)
 };
 
 struct Ctx {

@@ -128,3 +128,31 @@ def test_two_domains_reproduce_the_single_domain(problem):
             G.ctx.close()
         # the halo is part of the other domain (at this N, h spans a good part of it)
         assert 0 < len(ghosts[(r, 0)]) < n - len(own)
+
+
+def test_halo_select_rejects_box_ranks_outside_the_world(problem):
+    """Box ranks are device data from the caller: a rank outside [0, world) is skipped by
+    the kernel (no count or mask bit beyond the world) and the call reports EINVAL."""
+    import torch
+
+    import paper_1810_09898_gb300 as sg
+    from paper_1810_09898_gb300.domain import LibOps
+
+    d, h, _ = problem
+    pos, m = d["pos"][:5000], d["m32"][:5000]
+    lib = LibOps()
+    B = lib.boxes(_t(pos), _t(m), _t(h[:5000]), 3)
+    for bad in (2, -1, 64):
+        R = np.zeros(len(B), np.int32)
+        R[len(B) // 2:] = 1
+        R[0] = bad
+        with pytest.raises(sg.SphgrpError, match="EINVAL"):
+            lib.halo_mask(_t(pos), _t(m), _t(h[:5000]), 0, 1.0, B.contiguous(), _t(R), 0, 2)
+    # valid ranks afterwards: the context still works and matches the CPU version
+    R = np.zeros(len(B), np.int32)
+    R[len(B) // 2:] = 1
+    mk = lib.halo_mask(_t(pos), _t(m), _t(h[:5000]), 0, 1.0, B.contiguous(), _t(R), 0, 2).cpu().numpy()
+    mc = CpuOps(oracle).halo_mask(torch.from_numpy(pos), None, torch.from_numpy(h[:5000]), 0, 1.0,
+                                  B.cpu(), torch.from_numpy(R), 0, 2).numpy()
+    assert np.array_equal(mk, mc)
+    lib.close()
