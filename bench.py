@@ -306,10 +306,16 @@ class Problem:
         self.h.copy_(self.h_init)
         c.density(self.act, self.h, 1, mode, g, self.rho, self.drho, self.f, self.nn)
         sd = c.stats() if collect is not None else None
+        passes = None
+        if collect is not None:
+            try:   # host-side record of the call's search launches (no device work)
+                passes = [{"members": e["members"], "ms": e["ms"]} for e in c.launch_log()]
+            except Exception:  # noqa: BLE001 - the per-pass record is optional
+                passes = None
         c.hydro_force(self.act, self.h, self.rho, self.f, self.vel, self.u, mode, g, self.acc, self.dudt,
                       self.nnh)
         if collect is not None:
-            collect.append({"density": sd, "hydro": c.stats()})
+            collect.append({"density": sd, "hydro": c.stats(), "density_passes": passes})
 
     def step_e2e(self, g: int):
         """The same step from host buffers: inputs copied in, results copied out.  Only
@@ -435,6 +441,11 @@ def roofline(collect, peak_gbs, clocks=None, form: str = "grouped"):
     alu = {"achieved_tflops": flops / per_launch_s / 1e12, "peak_tflops": alu_peak,
            "frac": flops / per_launch_s / 1e12 / alu_peak,
            "peak_source": "152 SMs x 128 FP32 lanes x 2 x sampled SM clock (derived)"}
+    # the smoothing-length iteration's density launches of the last step: active members
+    # and device time of every pass
+    last = collect[-1].get("density_passes") if collect else None
+    if last and "density" in detail:
+        detail["density"]["passes_of_last_step"] = last
     kernel = f"k_indiv ({dom})" if form == "individual" else f"k_group ({dom})"
     return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak_gbs,
             "unit": "GB/s", "frac": achieved / peak_gbs, "traffic": traffic,
