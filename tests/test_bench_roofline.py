@@ -39,6 +39,20 @@ def test_roofline_picks_the_slower_kernel_and_divides_bytes_by_time():
     assert detail["density"]["members_per_walk"] == pytest.approx(10.0)
 
 
+def test_density_passes_of_the_last_step_are_reported():
+    dens = _stats(10.0, 2, 1_000_000, 100_000, 50_000, 5_000_000, 800_000, 10_000)
+    hyd = _stats(3.0, 1, 2_000_000, 100_000, 40_000, 9_000_000, 1_600_000, 10_000)
+    first = [{"members": 100, "ms": 4.0}, {"members": 80, "ms": 3.0}]
+    last = [{"members": 100, "ms": 6.0}, {"members": 70, "ms": 4.0}]
+    recs = [{"density": dens, "hydro": hyd, "density_passes": first},
+            {"density": dens, "hydro": hyd, "density_passes": last}]
+    _, detail = bench.roofline(recs, 8000.0)
+    assert detail["density"]["passes_of_last_step"] == last
+    # records without the per-pass list (an optional field) leave it out
+    _, detail = bench.roofline([{"density": dens, "hydro": hyd}], 8000.0)
+    assert "passes_of_last_step" not in detail["density"]
+
+
 def test_launch_gbs_counts_candidates_members_and_nodes():
     e = {"candidates": 1000, "members": 10, "nodes": 5, "ms": 1e-3}
     assert bench.launch_gbs(e, 48, 92) == pytest.approx((1000 * 48 + 10 * 92 + 5 * bench.B_NODE) / 1e-6 / 1e9)
