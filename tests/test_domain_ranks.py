@@ -197,3 +197,28 @@ def test_two_ranks_reproduce_the_single_domain():
         # the halo is part of the other domain (at this small N, h spans much of it)
         assert 0 < res[r]["ghosts_0_1.0"] < N - len(g)
         assert res[r]["ghosts_0_1.0"] <= res[r]["ghosts_1_1.0"]
+
+
+def test_single_rank_needs_no_process_group():
+    """world = 1: the partition keeps every row, the halo is empty, and later columns
+    follow the (empty) plan; exchange_columns before any halo of that kind is an error."""
+    import pytest
+    import torch
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    import sphgen
+    from paper_1810_09898_gb300.domain import Decomposition
+
+    d, rows, dens = _problem(oracle, sphgen)
+    D = Decomposition(1, 0, ops=CpuOps(oracle), level=LEVEL)
+    with pytest.raises(RuntimeError):
+        D.exchange_columns(1, torch.zeros((len(rows), 2), dtype=torch.float64))
+    own = D.partition(torch.from_numpy(rows))
+    assert np.array_equal(np.sort(own[:, 9].numpy()), np.arange(N, dtype=np.float64))
+    assert D.splitters.numel() == 0
+    for kind in (0, 1):
+        ghosts = D.halo(own, kind)
+        assert ghosts.shape == (0, rows.shape[1])
+        cols = D.exchange_columns(kind, torch.ones((own.shape[0], 2), dtype=torch.float64))
+        assert cols.shape == (0, 2)
